@@ -1,0 +1,310 @@
+/*
+ * FP64 CPU oracle for the boundary-element electrostatics model of
+ * Yokota, Bardhan, Knepley, Barba & Hamada (arXiv:1007.4591).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * reference that the CUDA path is checked against.  Only the test suite,
+ * the smoke check and the benchmark's CPU-baseline leg may load it; the
+ * product library never links, calls or falls back to it.  It shares no
+ * code, header, table or constant with the CUDA sources.
+ *
+ * Everything here is the plain dense definition of the discrete operators:
+ * no tree, no expansions, no near/far split, no blocking.  Every pair of
+ * distinct panels uses the same quadrature rule.  OpenMP parallelises only
+ * the loop over targets (each target's sum is accumulated serially in the
+ * source order, so results do not depend on the thread count).
+ *
+ * Notation (Sec. 2.1, Eqs. ASC and reac):
+ *   panels j: vertices v0, v1, v2 (counter-clockwise seen from the solvent),
+ *   unit normal n_j = (v1-v0)x(v2-v0)/|.|, area A_j, centroid c_j,
+ *   quadrature points y_jq with weights w_q (sum w_q = 1),
+ *   Green's function G(r) = 1/(4 pi r),
+ *   K'_ij = A_j sum_q w_q [-(c_i - y_jq).n_i] / (4 pi |c_i - y_jq|^3), K'_ii = 0,
+ *   (B q)_i = sum_k q_k [-(c_i - x_k).n_i] / (4 pi |c_i - x_k|^3),
+ *   (C s)_k = sum_j s_j A_j sum_q w_q / (4 pi |x_k - y_jq|).
+ *
+ * K'_ii = 0: for a flat panel (c_i - y).n_i vanishes for every y in panel i,
+ * so the principal-value self integral of the normal derivative is exactly
+ * zero; the jump term of the interior limit is carried by the identity in
+ * A = I + Ehat K'.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define FOUR_PI 12.566370614359172953850573533118
+
+/* ------------------------------------------------------------------ */
+/* Quadrature on a triangle.                                           */
+/* nq = 1: the centroid (the paper's one-point rule, Sec. 2.1).        */
+/* nq = 7: Radon's degree-5 rule (Stroud, "Approximate Calculation of  */
+/*         Multiple Integrals", 1971, formula T2:5-1): the centroid    */
+/*         with weight 9/40, the three permutations of (a, a, 1-2a),   */
+/*         a = (6 - sqrt15)/21, weight (155 - sqrt15)/1200, and the    */
+/*         three permutations of (b, b, 1-2b), b = (6 + sqrt15)/21,    */
+/*         weight (155 + sqrt15)/1200.  Weights sum to one.            */
+/* ------------------------------------------------------------------ */
+int oracle_quad_rule(int nq, double *bary, double *w)
+{
+    if (nq == 1) {
+        bary[0] = bary[1] = bary[2] = 1.0 / 3.0;
+        w[0] = 1.0;
+        return 0;
+    }
+    if (nq != 7) return -1;
+    const double s15 = sqrt(15.0);
+    const double a = (6.0 - s15) / 21.0, b = (6.0 + s15) / 21.0;
+    const double wa = (155.0 - s15) / 1200.0, wb = (155.0 + s15) / 1200.0;
+    const double pts[7][3] = {
+        {1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0},
+        {a, a, 1.0 - 2.0 * a}, {a, 1.0 - 2.0 * a, a}, {1.0 - 2.0 * a, a, a},
+        {b, b, 1.0 - 2.0 * b}, {b, 1.0 - 2.0 * b, b}, {1.0 - 2.0 * b, b, b},
+    };
+    const double wt[7] = {9.0 / 40.0, wa, wa, wa, wb, wb, wb};
+    for (int q = 0; q < 7; ++q) {
+        for (int k = 0; k < 3; ++k) bary[3 * q + k] = pts[q][k];
+        w[q] = wt[q];
+    }
+    return 0;
+}
+
+/* Panel geometry: centroid, unit normal, area and quadrature points
+ * y_jq = sum_k bary_qk v_k with the weights A_j w_q (Sec. 2.1: flat
+ * triangular panels, piecewise-constant basis). */
+int oracle_geometry(const double *panels, int64_t n, int nq,
+                    double *cen, double *nrm, double *area,
+                    double *qp, double *qw)
+{
+    double bary[21], w[7];
+    if (oracle_quad_rule(nq, bary, w)) return -1;
+    for (int64_t j = 0; j < n; ++j) {
+        const double *v0 = panels + 9 * j, *v1 = v0 + 3, *v2 = v0 + 6;
+        double e1[3], e2[3], cr[3];
+        for (int k = 0; k < 3; ++k) { e1[k] = v1[k] - v0[k]; e2[k] = v2[k] - v0[k]; }
+        cr[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        cr[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        cr[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double len = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        if (!(len > 0.0)) return -2;
+        area[j] = 0.5 * len;
+        for (int k = 0; k < 3; ++k) {
+            nrm[3 * j + k] = cr[k] / len;
+            cen[3 * j + k] = (v0[k] + v1[k] + v2[k]) / 3.0;
+        }
+        for (int q = 0; q < nq; ++q) {
+            for (int k = 0; k < 3; ++k)
+                qp[(j * nq + q) * 3 + k] = bary[3 * q] * v0[k] + bary[3 * q + 1] * v1[k]
+                                          + bary[3 * q + 2] * v2[k];
+            qw[j * nq + q] = area[j] * w[q];
+        }
+    }
+    return 0;
+}
+
+/* Normal derivative at target t (normal n) of the potential of a unit
+ * source at s:  d/dn_t [1/(4 pi |t - s|)] = -(t - s).n / (4 pi |t - s|^3). */
+static inline double dn_green(const double *t, const double *n, const double *s)
+{
+    double d0 = t[0] - s[0], d1 = t[1] - s[1], d2 = t[2] - s[2];
+    double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    double r = sqrt(r2);
+    return -(d0 * n[0] + d1 * n[1] + d2 * n[2]) / (FOUR_PI * r2 * r);
+}
+
+static inline double green(const double *a, const double *b)
+{
+    double d0 = a[0] - b[0], d1 = a[1] - b[1], d2 = a[2] - b[2];
+    return 1.0 / (FOUR_PI * sqrt(d0 * d0 + d1 * d1 + d2 * d2));
+}
+
+/* K'_ij for one pair (i != j), Eq. ASC discretised by collocation at c_i. */
+static inline double kprime_entry(int64_t i, int64_t j, int nq, const double *cen,
+                                  const double *nrm, const double *qp, const double *qw)
+{
+    double acc = 0.0;
+    for (int q = 0; q < nq; ++q)
+        acc += qw[j * nq + q] * dn_green(cen + 3 * i, nrm + 3 * i, qp + 3 * (j * nq + q));
+    return acc;
+}
+
+/* y = K' x  (dense, O(n^2)). */
+void oracle_kprime(int64_t n, int nq, const double *cen, const double *nrm,
+                   const double *qp, const double *qw, const double *x, double *y)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            acc += kprime_entry(i, j, nq, cen, nrm, qp, qw) * x[j];
+        }
+        y[i] = acc;
+    }
+}
+
+/* y = K' x for a subset of target rows only (sampled parity at large n). */
+void oracle_kprime_rows(int64_t n, int nq, const double *cen, const double *nrm,
+                        const double *qp, const double *qw, const double *x,
+                        int64_t nrows, const int64_t *rows, double *y)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t i = rows[r];
+        double acc = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            acc += kprime_entry(i, j, nq, cen, nrm, qp, qw) * x[j];
+        }
+        y[r] = acc;
+    }
+}
+
+/* y = K'^T x, i.e. y_j = sum_{i != j} K'_ij x_i (each output its own serial sum). */
+void oracle_kprime_t(int64_t n, int nq, const double *cen, const double *nrm,
+                     const double *qp, const double *qw, const double *x, double *y)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (i == j) continue;
+            acc += kprime_entry(i, j, nq, cen, nrm, qp, qw) * x[i];
+        }
+        y[j] = acc;
+    }
+}
+
+/* Dense K' (row-major n x n), small n only. */
+void oracle_kprime_dense(int64_t n, int nq, const double *cen, const double *nrm,
+                         const double *qp, const double *qw, double *K)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j)
+            K[i * n + j] = (i == j) ? 0.0 : kprime_entry(i, j, nq, cen, nrm, qp, qw);
+}
+
+/* E = B q: normal field of the point charges at the collocation points. */
+void oracle_bq(int64_t n, const double *cen, const double *nrm, int64_t nc,
+               const double *xq /*[nc][3]*/, const double *q, double *E)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int64_t k = 0; k < nc; ++k)
+            acc += q[k] * dn_green(cen + 3 * i, nrm + 3 * i, xq + 3 * k);
+        E[i] = acc;
+    }
+}
+
+/* u = B^T v: u_k = sum_i v_i B_ik. */
+void oracle_bt(int64_t n, const double *cen, const double *nrm, int64_t nc,
+               const double *xq, const double *v, double *u)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nc; ++k) {
+        double acc = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            acc += v[i] * dn_green(cen + 3 * i, nrm + 3 * i, xq + 3 * k);
+        u[k] = acc;
+    }
+}
+
+/* phi = C s: potential at the charges of the surface charge s (Eq. reac). */
+void oracle_c(int64_t n, int nq, const double *qp, const double *qw, int64_t nc,
+              const double *xq, const double *s, double *phi)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nc; ++k) {
+        double acc = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double pj = 0.0;
+            for (int q = 0; q < nq; ++q)
+                pj += qw[j * nq + q] * green(xq + 3 * k, qp + 3 * (j * nq + q));
+            acc += s[j] * pj;
+        }
+        phi[k] = acc;
+    }
+}
+
+/* v = C^T u: v_j = sum_k u_k C_kj. */
+void oracle_ct(int64_t n, int nq, const double *qp, const double *qw, int64_t nc,
+               const double *xq, const double *u, double *v)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int64_t k = 0; k < nc; ++k) {
+            double pj = 0.0;
+            for (int q = 0; q < nq; ++q)
+                pj += qw[j * nq + q] * green(xq + 3 * k, qp + 3 * (j * nq + q));
+            acc += u[k] * pj;
+        }
+        v[j] = acc;
+    }
+}
+
+/* g_k = grad_{x_k} (C s)_k = sum_j s_j A_j sum_q w_q * (-(x_k - y)/(4 pi |x_k - y|^3)). */
+void oracle_grad_c(int64_t n, int nq, const double *qp, const double *qw, int64_t nc,
+                   const double *xq, const double *s, double *g /*[nc][3]*/)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nc; ++k) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            for (int q = 0; q < nq; ++q) {
+                const double *y = qp + 3 * (j * nq + q);
+                double d0 = xq[3 * k] - y[0], d1 = xq[3 * k + 1] - y[1], d2 = xq[3 * k + 2] - y[2];
+                double r2 = d0 * d0 + d1 * d1 + d2 * d2, r = sqrt(r2);
+                double f = -s[j] * qw[j * nq + q] / (FOUR_PI * r2 * r);
+                a0 += f * d0; a1 += f * d1; a2 += f * d2;
+            }
+        }
+        g[3 * k] = a0; g[3 * k + 1] = a1; g[3 * k + 2] = a2;
+    }
+}
+
+/* h_k = sum_i v_i grad_{x_k} B_ik, with B_ik = -(d.n_i)/(4 pi |d|^3), d = c_i - x_k:
+ * grad_{x_k} B_ik = [n_i/|d|^3 - 3 (d.n_i) d/|d|^5] / (4 pi). */
+void oracle_grad_bt(int64_t n, const double *cen, const double *nrm, int64_t nc,
+                    const double *xq, const double *v, double *h /*[nc][3]*/)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nc; ++k) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            const double *c = cen + 3 * i, *nn = nrm + 3 * i;
+            double d0 = c[0] - xq[3 * k], d1 = c[1] - xq[3 * k + 1], d2 = c[2] - xq[3 * k + 2];
+            double r2 = d0 * d0 + d1 * d1 + d2 * d2, r = sqrt(r2);
+            double ir3 = 1.0 / (r2 * r), ir5 = ir3 / r2;
+            double dn = d0 * nn[0] + d1 * nn[1] + d2 * nn[2];
+            double f = v[i] / FOUR_PI;
+            a0 += f * (nn[0] * ir3 - 3.0 * dn * d0 * ir5);
+            a1 += f * (nn[1] * ir3 - 3.0 * dn * d1 * ir5);
+            a2 += f * (nn[2] * ir3 - 3.0 * dn * d2 * ir5);
+        }
+        h[3 * k] = a0; h[3 * k + 1] = a1; h[3 * k + 2] = a2;
+    }
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void oracle_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}

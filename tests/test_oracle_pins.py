@@ -1,0 +1,303 @@
+"""Pins for the FP64 CPU oracle: closed forms, invariants and brute force.
+
+Each test ties the oracle to something other than itself, chosen so that a
+plausible slip (a dropped term, a wrong sign or normal direction, a swapped
+index, a transposed operand, a wrong quadrature weight) fails at least one:
+
+* quadrature: exact integrals of monomials (degree <= 5) and the published
+  table of the rule (tests/golden/stroud_t2_5_1.txt);
+* K' on a sphere: K' 1 -> -1/2 and K' Y_1 -> -1/6 Y_1 (eigenvalues
+  -1/(2(2l+1)) of the interior-limit operator), which fixes sign and scale;
+* Born ion (Sec. 2.1 model, one central charge): closed form energy;
+* Kirkwood series for off-centre charges (full solve) and its BIBEE
+  counterparts (Eq. CFA, lambda = -1/2 and 0), with the ordering
+  dG_P <= dG <= dG_CFA (CFA is an upper bound, Sec. 2.2);
+* Gauss's law for the total induced charge;
+* GMRES against dense LU (numpy.linalg.solve) on the assembled matrix;
+* adjoint: dot-product identities for K'^T, B^T, C^T and central finite
+  differences of the energy in the charge values and positions;
+* rigid-motion invariance of the energy.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import sphere_series as ss
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def small3():
+    m = synth.small_molecule(3)
+    return m, oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+
+
+@pytest.fixture(scope="module")
+def small4():
+    m = synth.small_molecule(4)
+    return m, oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+
+
+# ---------------------------------------------------------------- quadrature
+def test_quad_rule_matches_published_table():
+    rows = np.loadtxt(os.path.join(GOLDEN, "stroud_t2_5_1.txt"))
+    bary, w = oracle.quad_rule(7)
+    np.testing.assert_allclose(bary, rows[:, :3], atol=2e-15)
+    np.testing.assert_allclose(w, rows[:, 3], atol=2e-15)
+    assert abs(w.sum() - 1.0) < 1e-15
+
+
+def _monomial_integral_ref(a, b):
+    # int over {x>=0, y>=0, x+y<=1} of x^a y^b = a! b! / (a+b+2)!
+    from math import factorial
+    return factorial(a) * factorial(b) / factorial(a + b + 2)
+
+
+@pytest.mark.parametrize("nq,degree", [(7, 5), (1, 1)])
+def test_quad_rule_polynomial_exactness(nq, degree):
+    # reference triangle embedded in z = 0, counter-clockwise seen from +z
+    tri = np.array([[[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]]])
+    P = oracle.Problem(tri, np.array([[0.3, 0.3, -1.0, 1.0]]), 1.0, 80.0, nq=nq)
+    assert abs(P.area[0] - 0.5) < 1e-15
+    np.testing.assert_allclose(P.nrm[0], [0.0, 0.0, 1.0], atol=1e-15)
+    y = P.qp[0]
+    for a in range(degree + 1):
+        for b in range(degree + 1 - a):
+            got = float(np.sum(P.qw[0] * y[:, 0] ** a * y[:, 1] ** b))
+            assert abs(got - _monomial_integral_ref(a, b)) < 1e-14, (a, b)
+    if nq == 7:
+        # not exact one degree higher (so the table is not a higher-order rule)
+        got = float(np.sum(P.qw[0] * y[:, 0] ** 6))
+        assert abs(got - _monomial_integral_ref(6, 0)) > 1e-6
+
+
+def test_quad_rule_exact_on_skewed_triangle():
+    rng = np.random.default_rng(11)
+    v = rng.normal(size=(3, 3))
+    tri = v[None]
+    P = oracle.Problem(tri, np.array([[9.0, 9.0, 9.0, 1.0]]), 1.0, 80.0)
+    # barycentric monomials: int l1^a l2^b l3^c dA = 2 A a! b! c! / (a+b+c+2)!
+    from math import factorial
+    bary, _ = oracle.quad_rule(7)
+    for a in range(6):
+        for b in range(6 - a):
+            for c in range(6 - a - b):
+                exact = 2 * P.area[0] * factorial(a) * factorial(b) * factorial(c) / factorial(a + b + c + 2)
+                got = float(np.sum(P.qw[0] * bary[:, 0] ** a * bary[:, 1] ** b * bary[:, 2] ** c))
+                assert abs(got - exact) < 1e-13 * max(1.0, abs(exact))
+    # the quadrature points really are those barycentric combinations
+    np.testing.assert_allclose(P.qp[0], bary @ v, atol=1e-14)
+
+
+def test_geometry_outward_and_area():
+    m = synth.born(4)
+    P = oracle.Problem(m.panels, m.charges, 1.0, 80.0)
+    assert np.all(np.einsum("ij,ij->i", P.nrm, P.cen) > 0)  # normals point into the solvent
+    np.testing.assert_allclose(np.linalg.norm(P.nrm, axis=1), 1.0, atol=1e-14)
+    # inscribed polyhedron: area below, and close to, 4 pi R^2
+    tot = P.area.sum()
+    assert 0.99 * 4 * np.pi * 4.0 < tot < 4 * np.pi * 4.0
+
+
+def test_degenerate_panel_rejected():
+    tri = np.zeros((1, 3, 3))
+    with pytest.raises(ValueError):
+        oracle.Problem(tri, np.array([[0.0, 0.0, 1.0, 1.0]]), 1.0, 80.0)
+
+
+# -------------------------------------------------------------- K' on a sphere
+def test_kprime_sphere_eigenvalues(small3, small4):
+    e0, e1 = [], []
+    for m, P in (small3, small4):
+        k1 = P.kprime(np.ones(P.n))
+        e0.append(abs(k1.mean() + 0.5))          # eigenvalue -1/2 for l = 0
+        z = P.cen[:, 2] / np.linalg.norm(P.cen, axis=1)
+        kz = P.kprime(z)
+        lam = float(kz @ z / (z @ z))            # eigenvalue -1/6 for l = 1
+        e1.append(abs(lam + 1.0 / 6.0))
+        assert np.linalg.norm(kz - lam * z) / np.linalg.norm(kz) < 0.05
+    # first-order convergence (the fixed rule on near-singular neighbours)
+    assert e0[1] < 0.015 and e0[1] < 0.6 * e0[0]
+    assert e1[1] < 0.015 and e1[1] < 0.6 * e1[0]
+
+
+def test_kprime_self_term_vanishes_on_flat_panel():
+    # (c_i - y) . n_i = 0 for every y on a flat panel: refining the panel into
+    # sub-triangles and summing the interior-limit-free contributions gives 0.
+    tri = np.array([[0.0, 0.0, 0.0], [1.0, 0.1, 0.0], [0.2, 0.9, 0.0]])
+    c = tri.mean(0)
+    # the three corner children of the panel are coplanar with it: the
+    # collocation point's kernel vanishes on each of them identically
+    mids = [(tri[0] + tri[1]) / 2, (tri[1] + tri[2]) / 2, (tri[2] + tri[0]) / 2]
+    kids = np.array([[tri[0], mids[0], mids[2]], [tri[1], mids[1], mids[0]],
+                     [tri[2], mids[2], mids[1]]])
+    P = oracle.Problem(np.concatenate([tri[None], kids]), np.array([[0, 0, 5.0, 1.0]]), 1, 80)
+    K = P.kprime_dense()
+    assert np.all(np.abs(K[0, 1:]) < 1e-14)
+    assert K[0, 0] == 0.0
+
+
+# ---------------------------------------------------------------- Born ion
+def test_born_energy_converges_to_closed_form():
+    exact = ss.born_energy(1.0, 2.0, 1.0, 80.0)
+    assert abs(exact - (-81.97822593750)) < 1e-9
+    errs = []
+    for s in (2, 3, 4):
+        m = synth.born(s)
+        P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+        sig, info = P.solve(tol=1e-12)
+        assert info["converged"]
+        dg, _ = P.energy(sig)
+        errs.append(abs(dg - exact) / abs(exact))
+        # BIBEE/CFA is exact for a central charge (uniform normal field)
+        _, dcfa = P.bibee("cfa")
+        assert abs(dcfa - exact) / abs(exact) < 0.04 / 4 ** (s - 2)
+    assert errs[0] < 0.07 and errs[1] < 0.03 and errs[2] < 0.015
+    assert errs[1] / errs[0] < 0.6 and errs[2] / errs[1] < 0.6
+
+
+def test_series_reduce_to_born():
+    ch = np.array([[0.0, 0.0, 0.0, 1.3]])
+    b = ss.born_energy(1.3, 5.0, 4.0, 80.0)
+    for kind in ("full", "cfa"):
+        assert abs(ss.sphere_energy(ch, 5.0, 4.0, 80.0, kind) - b) < 1e-12 * abs(b)
+
+
+# ------------------------------------------------ Kirkwood and BIBEE series
+def test_kirkwood_and_bibee_series(small3, small4):
+    res = {}
+    for tag, (m, P) in (("s3", small3), ("s4", small4)):
+        sig, info = P.solve(tol=1e-11)
+        assert info["converged"]
+        dg, _ = P.energy(sig)
+        _, dc = P.bibee("cfa")
+        _, dp = P.bibee("p")
+        ex = ss.sphere_energy(m.charges, m.radius, m.eps_in, m.eps_out, "full")
+        exc = ss.sphere_energy(m.charges, m.radius, m.eps_in, m.eps_out, "cfa")
+        exp_ = ss.sphere_energy(m.charges, m.radius, m.eps_in, m.eps_out, "p")
+        res[tag] = (abs(dg - ex) / abs(ex), abs(dc - exc) / abs(exc), abs(dp - exp_) / abs(exp_))
+        # ordering of the approximations (CFA upper bound, Sec. 2.2)
+        assert dp < dg < dc
+        assert exp_ < ex < exc
+    assert res["s4"][0] < 0.025 and res["s4"][0] < 0.6 * res["s3"][0]
+    assert res["s4"][1] < 0.004 and res["s4"][1] < 0.35 * res["s3"][1]
+    assert res["s4"][2] < 0.004 and res["s4"][2] < 0.35 * res["s3"][2]
+
+
+def test_bibee_lambda_variants_closed_form():
+    e_in, e_out = 4.0, 80.0
+    # lambda = -1/2: sigma_hat = (1 - eps_in/eps_out) E_n
+    assert abs(oracle.bibee_factor(e_in, e_out, -0.5) - (1 - e_in / e_out)) < 1e-15
+    # lambda = +1/2: sigma_hat = (eps_out - eps_in)/eps_in E_n
+    assert abs(oracle.bibee_factor(e_in, e_out, 0.5) - (e_out - e_in) / e_in) < 1e-13
+
+
+def test_gauss_law_total_induced_charge(small3, small4):
+    errs = []
+    for m, P in (small3, small4):
+        sig, _ = P.solve(tol=1e-11)
+        total = float(P.area @ sig)
+        expect = -(1.0 - m.eps_in / m.eps_out) * m.charges[:, 3].sum()
+        errs.append(abs(total - expect) / abs(expect))
+    assert errs[1] < 0.02 and errs[1] < 0.6 * errs[0]
+
+
+# --------------------------------------------------------------- GMRES vs LU
+def test_gmres_matches_dense_lu():
+    m = synth.small_molecule(3)
+    P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+    A = np.eye(P.n) + P.ehat * P.kprime_dense()
+    b = P.rhs()
+    x_lu = np.linalg.solve(A, b)
+    x, info = P.solve(tol=1e-12, restart=10)   # small restart exercises restarts
+    assert info["converged"] and info["true_resid"] < 1e-11
+    assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) < 1e-10
+    # dense operator agrees with the matrix-free one
+    v = np.random.default_rng(3).normal(size=P.n)
+    np.testing.assert_allclose(A @ v, P.A(v), rtol=1e-12, atol=1e-12)
+
+
+def test_gmres_textbook_on_known_system():
+    rng = np.random.default_rng(0)
+    n = 60
+    M = np.eye(n) + 0.3 * rng.normal(size=(n, n)) / np.sqrt(n)
+    b = rng.normal(size=n)
+    x, info = oracle.gmres(lambda v: M @ v, b, tol=1e-13, restart=7, maxiter=2000)
+    assert info["converged"]
+    np.testing.assert_allclose(x, np.linalg.solve(M, b), rtol=1e-10, atol=1e-11)
+
+
+# ---------------------------------------------------------------- adjoint
+def test_transposes_by_dot_products(small3):
+    m, P = small3
+    rng = np.random.default_rng(5)
+    x, y = rng.normal(size=P.n), rng.normal(size=P.n)
+    assert abs(P.kprime(x) @ y - x @ P.kprime_t(y)) < 1e-12 * np.abs(P.kprime(x)).sum() * np.abs(y).max()
+    K = P.kprime_dense()
+    np.testing.assert_allclose(K @ x, P.kprime(x), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(K.T @ y, P.kprime_t(y), rtol=1e-12, atol=1e-14)
+    q, v = rng.normal(size=P.nc), rng.normal(size=P.n)
+    assert abs(P.bq(q) @ v - q @ P.bt(v)) < 1e-12 * np.linalg.norm(P.bq(q)) * np.linalg.norm(v)
+    s, u = rng.normal(size=P.n), rng.normal(size=P.nc)
+    assert abs(P.c(s) @ u - s @ P.ct(u)) < 1e-12 * np.linalg.norm(P.c(s)) * np.linalg.norm(u)
+
+
+def _energy_at(m, charges, tol=1e-13):
+    P = oracle.Problem(m.panels, charges, m.eps_in, m.eps_out)
+    sig, _ = P.solve(tol=tol, maxiter=2000)
+    return P.energy(sig)[0]
+
+
+def test_adjoint_gradients_match_central_differences():
+    m = synth.small_molecule(2, n_charges=12)
+    P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+    dg, dq, dx, _, _ = P.gradients(tol=1e-13)
+    hq, hx = 1e-4, 1e-4
+    for k in range(0, P.nc, 3):
+        cp, cm = m.charges.copy(), m.charges.copy()
+        cp[k, 3] += hq
+        cm[k, 3] -= hq
+        fd = (_energy_at(m, cp) - _energy_at(m, cm)) / (2 * hq)
+        assert abs(fd - dq[k]) < 1e-7 * max(1.0, abs(dq[k])), (k, fd, dq[k])
+        for d in range(3):
+            cp, cm = m.charges.copy(), m.charges.copy()
+            cp[k, d] += hx
+            cm[k, d] -= hx
+            fd = (_energy_at(m, cp) - _energy_at(m, cm)) / (2 * hx)
+            assert abs(fd - dx[k, d]) < 1e-6 * max(1.0, np.abs(dx).max()), (k, d, fd, dx[k, d])
+
+
+def test_energy_quadratic_in_charges(small3):
+    # dG(q) = 1/2 q^T R q  =>  q . d dG/dq = 2 dG
+    m, P = small3
+    dg, dq, _, _, _ = P.gradients(tol=1e-13)
+    assert abs(float(P.q @ dq) - 2.0 * dg) < 1e-9 * abs(dg)
+
+
+# --------------------------------------------------------------- invariance
+def test_energy_invariant_under_rigid_motion():
+    m = synth.small_molecule(3)
+    e0 = _energy_at(m, m.charges, tol=1e-12)
+    R = synth.random_rotation(np.random.default_rng(9))
+    t = np.array([3.0, -7.5, 12.25])
+    pan = m.panels @ R.T + t
+    ch = m.charges.copy()
+    ch[:, :3] = ch[:, :3] @ R.T + t
+    P = oracle.Problem(pan, ch, m.eps_in, m.eps_out)
+    sig, _ = P.solve(tol=1e-12)
+    e1 = P.energy(sig)[0]
+    assert abs(e1 - e0) < 1e-9 * abs(e0)
+
+
+def test_one_point_rule_variant_runs_and_converges():
+    # the paper's centroid rule (Sec. 2.1): same model, coarser panel integrals
+    m = synth.born(3)
+    P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out, nq=1)
+    sig, info = P.solve(tol=1e-10)
+    assert info["converged"]
+    dg, _ = P.energy(sig)
+    assert abs(dg - ss.born_energy(1.0, 2.0, 1.0, 80.0)) / 81.978 < 0.05
