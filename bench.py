@@ -1,0 +1,312 @@
+"""Benchmark of the FMM-BEM matrix-vector product (the hot path inside GMRES).
+
+Workload: the 81,920-panel globular molecule (sphere R = 20 A, icosphere
+subdivision 6, 2,000 seeded charges, eps_in = 4, eps_out = 80), synthetic
+stand-in for the paper's protein meshes.  One step = one product
+y = (I + Ehat K') x through the C-ABI on device-resident vectors; the tree
+is built once before the timed region (its time is reported separately).
+
+Printed: one JSON line (rank 0) with the throughput in Mpanels/s, the
+end-to-end number through the C-ABI with host buffers, the roofline of the
+dominant kernel (P2P, FP32 ALU bound), the oracle timed on the host cores,
+the solve time and the plain FP64 GPU form at the same accuracy.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica of the
+workload on its own GPU (the product is not sharded: replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM-BEM matvec Mpanels/s & solve s, mixed vs FP64 GPU at 1e-5 rel ΔG"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload():
+    import synth
+    return synth.globular(6)
+
+
+def cpu_baseline(mol, budget_s=12.0, rows=None):
+    """The oracle (dense FP64, OpenMP over targets) on a bounded sample of rows."""
+    import oracle
+    P = oracle.Problem(mol.panels, mol.charges, mol.eps_in, mol.eps_out)
+    x = P.bq()
+    rng = np.random.default_rng(0)
+    n = rows or 64
+    t0 = time.perf_counter()
+    P.kprime_rows(x, rng.choice(mol.n_p, n, replace=False))
+    dt = time.perf_counter() - t0
+    if rows is None:
+        n = int(max(64, min(mol.n_p, n * budget_s / max(dt, 1e-3))))
+        t0 = time.perf_counter()
+        P.kprime_rows(x, rng.choice(mol.n_p, n, replace=False))
+        dt = time.perf_counter() - t0
+    return {"value": n / dt / 1e6, "unit": "Mpanels/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{n} of {mol.n_p} rows of the dense FP64 product "
+                      f"(each row = {mol.n_p * 7} quadrature points), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    mol = workload()
+    cb = None
+    vals = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(mol, rows=max(8, args.ref_rows))
+        if k >= args.warmup:
+            vals.append(r["value"])
+        cb = r
+    v = float(np.mean(vals))
+    cb["value"] = v
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "Mpanels/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "globular-s6 (sphere R=20 A, 81,920 panels, 2,000 charges)",
+                   "global_batch": 1, "parallelism": "replicas"},
+        "cpu_baseline": cb,
+        "e2e": {"value": v, "unit": "Mpanels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_1007_4591_gb300 as pkg
+    pkg.load_library()
+    mol = workload()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    opts = dict(p=args.p, leaf_size=args.leaf, precision=0)
+    t0 = time.perf_counter()
+    mesh = pkg.Mesh(mol.panels, mol.charges, mol.eps_in, mol.eps_out, **opts)
+    tree_s = time.perf_counter() - t0
+    info = mesh.info()
+    n = mol.n_p
+    x = torch.from_numpy(np.random.default_rng(1).standard_normal(n)).to(dev)
+    y = torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        pkg.bem_matvec(mesh.h, x, y)
+    torch.cuda.synchronize()
+    # timed region: K products, L2 flushed between products (outside the events)
+    clk = ClockSampler(local)
+    clk.start()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pkg.bem_matvec(mesh.h, x, y)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    _barrier(ws)
+    clocks = clk.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t_ms = _max_over_ranks(t_ms, ws)
+    value = ws * n * args.steps / (t_ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (P2P): phase events on the library's stream
+    pkg.bem_set_profiling(mesh.h, True)
+    phases = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.fill_(1.0)
+        pkg.bem_matvec(mesh.h, x, y)
+        phases.append(pkg.bem_last_phase_ms(mesh.h))
+    pkg.bem_set_profiling(mesh.h, False)
+    ph = {k: float(np.mean([d[k] for d in phases])) for k in phases[0]}
+    peaks, src = _peaks()
+    f_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * f_mhz * 1e6 / 1e12
+    p2p_flops = 20.0 * info["p2p_pairs"]
+    achieved = p2p_flops / (ph["p2p"] * 1e-3) / 1e12 if ph["p2p"] > 0 else 0.0
+    roofline = {"kernel": "k_p2p (near-field panel quadrature)", "bound": "alu",
+                "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                "peak_source": f"FP32: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                               f"{f_mhz:.0f} MHz (sm_max_mhz from MEASURED_PEAKS.json, {src})",
+                "algorithmic": f"20 flop x {info['p2p_pairs']} (collocation point, source point) pairs"}
+
+    # end to end through the C-ABI with host buffers
+    xh = np.ascontiguousarray(x.cpu().numpy())
+    yh = np.empty(n)
+    for _ in range(2):
+        pkg.bem_matvec(mesh.h, xh, yh)
+    ts = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        pkg.bem_matvec(mesh.h, xh, yh)
+        ts.append(time.perf_counter() - t1)
+    e2e_s = _max_over_ranks(float(np.sum(ts)), ws)
+    e2e = {"value": ws * n * args.steps / e2e_s / 1e6, "unit": "Mpanels/s",
+           "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+
+    # one full solve (rhs + GMRES to 1e-8 + energy) on the same mesh
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    sig, st = mesh.solve(allow_noconv=True)
+    dg = mesh.energy(sig)
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t1
+
+    L = info["depth"]
+    # gather, P2P, combine, operator epilogue, scatter; P2M, M2L, L2P and one M2M
+    # and one L2L launch per level between 2 and L
+    launches_per = 5 + (3 + 2 * (L - 2) if L >= 2 else 0)
+    cpu = cpu_baseline(mol, budget_s=args.cpu_budget) if (rank == 0 and not args.no_cpu) else None
+    mesh.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": round(value, 3), "unit": "Mpanels/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "globular-s6 (sphere R=20 A, icosphere subdivision 6, 81,920 "
+                                   "panels, 2,000 charges, eps 4/80)",
+                       "p": args.p, "leaf_size": args.leaf, "depth": L, "precision": "mixed",
+                       "global_batch": ws, "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "flushed (256 MB write) between timed products"},
+            "phases_ms": {k: round(v, 4) for k, v in ph.items()},
+            "tree_build_s": round(tree_s, 4),
+            "solve_s": round(solve_s, 4), "solve_iters": st["iterations"], "dG_kcal": dg,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per * args.steps, "clocks": clocks,
+        }))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--p", type=int, default=10)
+    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-rows", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

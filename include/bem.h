@@ -1,0 +1,194 @@
+/*
+ * libbem -- FMM-accelerated boundary-element solver for continuum (Poisson)
+ * biomolecular electrostatics on one GB300 GPU (sm_103a).
+ *
+ * Method: Yokota, Bardhan, Knepley, Barba, Hamada, "Biomolecular
+ * electrostatics using a fast multipole BEM on up to 512 GPUs and a billion
+ * unknowns" (arXiv:1007.4591).  Section references below are to that paper.
+ *
+ * Model (Sec. 2.1).  A closed surface of n_p flat triangular panels (vertices
+ * counter-clockwise seen from the solvent) encloses n_c point charges; the
+ * interior has permittivity eps_in, the solvent eps_out.  With one unknown per
+ * panel (piecewise constant), collocation at the panel centroids and a
+ * quadrature rule on every panel, Eq. ASC becomes the second-kind system
+ *
+ *     A sigma = b,   A = I + Ehat K',   b = -Ehat (B q),
+ *     Ehat = 2 (eps_in - eps_out) / (eps_in + eps_out),
+ *     K'_ij = A_j sum_q w_q [-(c_i - y_jq).n_i] / (4 pi |c_i - y_jq|^3),  K'_ii = 0,
+ *     (B q)_i = sum_k q_k [-(c_i - x_k).n_i] / (4 pi |c_i - x_k|^3),
+ *
+ * (the normal derivative of Eq. ASC taken as the interior limit; K'_ii = 0
+ * exactly on a flat panel).  sigma is eps_in times the physical induced
+ * charge, so the reaction potential of Eq. reac at the charges is
+ * phi = C sigma / eps_in, (C s)_k = sum_j s_j A_j sum_q w_q / (4 pi |x_k - y_jq|),
+ * and the solvation free energy (Sec. 2.1) is
+ *
+ *     dG = 1/2 sum_k q_k phi_k = 4 pi * 332.0637 / (2 eps_in) * q.(C sigma)  [kcal/mol].
+ *
+ * Products with K', B and C run as fast multipole passes (Sec. 2.3: P2M, M2M,
+ * M2L, L2L, L2P over an octree plus the near-field P2P panel quadrature).
+ *
+ * Conventions for every entry point:
+ *  - Lengths in Angstrom, charges in e, energies in kcal/mol.
+ *  - Array arguments may be host or device pointers (device memory of the
+ *    current device, or managed memory); the library detects which.  A device
+ *    array is read or written in stream order on the mesh's stream; the call
+ *    returns after its results are complete (it synchronises that stream).
+ *  - Vectors over panels are in the caller's panel order (length n_p, f64);
+ *    vectors over charges are in the caller's charge order (length n_c).
+ *  - The caller owns every array it passes; the library copies what it keeps.
+ *  - Return value: BEM_OK (0) or a negative BEM_E* code; nothing aborts.
+ *    bem_last_error() gives a message for the calling thread's last failure.
+ */
+#ifndef LIBBEM_BEM_H
+#define LIBBEM_BEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define BEM_OK 0
+#define BEM_EINVAL (-1)       /* bad argument: NaN/Inf, zero-area panel, eps <= 0, n_p = 0 ... */
+#define BEM_ENOMEM (-2)       /* device or host allocation failed */
+#define BEM_ECUDA (-3)        /* a CUDA runtime call failed */
+#define BEM_ENOCONV (-4)      /* GMRES hit max_iter or stagnated; best iterate written */
+#define BEM_ETIMEOUT (-5)     /* a bounded device-side wait ran out */
+#define BEM_EUNSUPPORTED (-6) /* option combination not built */
+
+/* ---- options ----------------------------------------------------------- */
+#define BEM_MIXED 0 /* FP32 P2P and expansions, FP64 GMRES / epilogues / reductions */
+#define BEM_FP64 1  /* every kernel in FP64 (the plain double-precision GPU form) */
+
+#define BEM_BIBEE_CFA 0       /* lambda = -1/2 (Eq. CFA) */
+#define BEM_BIBEE_P 1         /* lambda =  0               (Sec. 2.2) */
+#define BEM_BIBEE_PLUS_HALF 2 /* lambda = +1/2             (Sec. 2.2) */
+
+#define BEM_FLAG_NO_FAR 1u      /* diagnostics: drop the far field (expansions) */
+#define BEM_FLAG_NO_NEAR 2u     /* diagnostics: drop the near field (P2P + table) */
+#define BEM_FLAG_NO_NEARTAB 4u  /* diagnostics: skip the near-singular FP64 table */
+
+typedef struct bem_options {
+    int precision;     /* BEM_MIXED (default) or BEM_FP64 */
+    int p;             /* expansion order, 1..16 (default 10) */
+    int leaf_size;     /* target mean panels per non-empty leaf (default 64) */
+    int depth;         /* octree leaf level; 0 = choose from leaf_size; -1 = single leaf */
+    int quad_points;   /* panel quadrature: 7 (degree-5 rule, default) or 1 (centroid) */
+    int gmres_restart; /* GMRES(m) restart length (default 30) */
+    int max_iter;      /* total GMRES iterations (default 300) */
+    double tol;        /* relative residual |b - A x| / |b| (default 1e-8) */
+    unsigned flags;    /* BEM_FLAG_* (default 0) */
+    int near_table;    /* 1 = FP64 near-singular correction table (default 1) */
+    int charge_mode;   /* products with B, B^T, C, C^T (charges <-> surface):
+                          0 = auto (direct sum when n_c * n_p * quad_points <= 4e10,
+                              fast multipole otherwise), 1 = fast multipole, 2 = direct */
+} bem_options;
+
+#define BEM_CHARGE_AUTO 0
+#define BEM_CHARGE_FMM 1
+#define BEM_CHARGE_DIRECT 2
+
+typedef struct bem_solve_stats {
+    int iterations;      /* GMRES iterations (matrix-vector products inside GMRES) */
+    int restarts;
+    int converged;       /* 1 if the recurrence residual reached tol */
+    double resid;        /* final recurrence residual (relative) */
+    double true_resid;   /* |b - A x| / |b| from one extra product */
+    double ms_rhs, ms_gmres, ms_total;
+} bem_solve_stats;
+
+typedef struct bem_mesh_info {
+    int64_t n_p, n_c;
+    int depth;             /* leaf level L */
+    int p;
+    int precision;
+    int64_t leaves, cells; /* panel tree */
+    int64_t p2p_pairs;     /* exact (target, source point) pairs of one K' near field */
+    int64_t m2l_pairs;     /* M2L translations of one K' far field */
+    int64_t m2m_pairs;     /* M2M (= L2L) translations of one pass */
+    int64_t source_points; /* quadrature points (n_p * quad_points) */
+    int64_t near_table_nnz;
+    double root_side;      /* root cube side (A) */
+    size_t device_bytes;   /* device memory held by the mesh */
+    double ms_build;       /* time spent in bem_mesh_create (tree, lists, tables) */
+} bem_mesh_info;
+
+typedef struct bem_mesh bem_mesh; /* opaque: owns geometry, trees, lists, scratch */
+
+/* Fill *opt with the defaults above. */
+int bem_options_default(bem_options *opt);
+
+/* Build a mesh handle (Sec. 2.1 discretisation, Sec. 2.3 octree).
+ *   panels  [n_p][3][3] f64, vertex coordinates, counter-clockwise seen from outside.
+ *   charges [n_c][4] f64 rows (x, y, z, q); n_c may be 0 (then no rhs/energy).
+ *   eps_in, eps_out > 0.
+ *   opt may be NULL (defaults).  stream: a cudaStream_t (NULL = legacy default).
+ * Computes panel geometry and quadrature points, Morton keys and sort, the
+ * octree, neighbour and interaction lists, translation tables and the FP64
+ * near-singular table, all on the device.  Errors: BEM_EINVAL for NaN/Inf
+ * coordinates, zero-area panels, eps <= 0, n_p <= 0, bad options. */
+int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, int64_t n_c,
+                    double eps_in, double eps_out, const bem_options *opt, void *stream,
+                    bem_mesh **out);
+
+/* Release every resource of the handle (NULL is accepted). */
+int bem_mesh_destroy(bem_mesh *mesh);
+
+/* Replace the point charges (same or different count); the panel tree is kept,
+ * the charge tree and lists are rebuilt.  charges [n_c][4] f64. */
+int bem_set_charges(bem_mesh *mesh, const double *charges, int64_t n_c);
+
+/* y = A x = x + Ehat K' x  (the BEM operator of Eq. ASC), x, y [n_p] f64.
+ * x and y may alias. */
+int bem_matvec(bem_mesh *mesh, const double *x, double *y);
+
+/* y = A^T x = x + Ehat K'^T x  (the transposed operator, used by the adjoint). */
+int bem_matvec_t(bem_mesh *mesh, const double *x, double *y);
+
+/* b = -Ehat (B q): the right-hand side of Eq. ASC, [n_p] f64. */
+int bem_rhs(bem_mesh *mesh, double *b);
+
+/* Solve A sigma = b by restarted GMRES (Sec. 2.1) to opt.tol.
+ *   x0: initial guess [n_p] or NULL (zero).  sigma: [n_p] output.
+ *   stats may be NULL.  Returns BEM_ENOCONV (sigma still written) when the
+ *   iteration budget runs out or the residual stagnates. */
+int bem_solve(bem_mesh *mesh, const double *x0, double *sigma, bem_solve_stats *stats);
+
+/* BIBEE (Sec. 2.2, Eq. CFA): K' replaced by lambda I, lambda from `variant`:
+ *   sigma_hat = -Ehat / (1 + Ehat lambda) (B q),  then dG as in bem_energy.
+ *   sigma_hat [n_p] may be NULL; dG_kcal may be NULL. */
+int bem_bibee(bem_mesh *mesh, int variant, double *sigma_hat, double *dG_kcal);
+
+/* Solvation energy of a surface charge (Sec. 2.1, Eq. reac):
+ *   phi = C sigma / eps_in at the charges (phi_reac [n_c], may be NULL),
+ *   dG = 1/2 q.phi * 4 pi 332.0637  [kcal/mol]. */
+int bem_energy(bem_mesh *mesh, const double *sigma, double *dG_kcal, double *phi_reac);
+
+/* Gradient of dG (from the last bem_solve, or a fresh one if none) with
+ * respect to the charge values and positions, by the adjoint: solve
+ * A^T lam = C^T q, then
+ *   d dG/d q_k = kappa/(2 eps_in) [ (C sigma)_k - Ehat (B^T lam)_k ],
+ *   d dG/d x_k = kappa/(2 eps_in) q_k [ grad (C sigma)_k - Ehat sum_i lam_i grad_{x_k} B_ik ],
+ * kappa = 4 pi 332.0637, each multiplied by grad_out.
+ *   dq [n_c] and dx [n_c][3] f64, either may be NULL. */
+int bem_energy_backward(bem_mesh *mesh, double grad_out, double *dq, double *dx);
+
+/* Sizes and counts of the handle (tree depth, list sizes, memory). */
+int bem_mesh_info_get(const bem_mesh *mesh, bem_mesh_info *info);
+
+/* Per-phase device time (ms) of the last bem_matvec, measured with CUDA events
+ * when enabled by bem_set_profiling(mesh, 1): order P2M, M2M, M2L, L2L, L2P,
+ * P2P, epilogue.  times[7]. */
+int bem_set_profiling(bem_mesh *mesh, int enable);
+int bem_last_phase_ms(const bem_mesh *mesh, double *times);
+
+/* Message for the calling thread's last error (static storage, never NULL). */
+const char *bem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBBEM_BEM_H */

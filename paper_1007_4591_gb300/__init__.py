@@ -1,0 +1,339 @@
+"""Python binding of libbem, the GB300 FMM-BEM solver (arXiv:1007.4591).
+
+The functions below have the names of the C entry points declared in
+``include/bem.h`` and only marshal arguments: every step of the computation
+runs in the CUDA library.  Arrays may be torch CUDA tensors (device pointers,
+used in place) or numpy / CPU arrays (host pointers, staged by the library).
+There is no CPU fallback: importing this package without the built
+``lib/libbem.so`` raises.
+
+A small convenience class, :class:`Mesh`, owns a handle and exposes the same
+operations with array allocation done here (plumbing only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libbem.so")
+
+BEM_OK = 0
+BEM_EINVAL = -1
+BEM_ENOMEM = -2
+BEM_ECUDA = -3
+BEM_ENOCONV = -4
+BEM_ETIMEOUT = -5
+BEM_EUNSUPPORTED = -6
+
+BEM_MIXED = 0
+BEM_FP64 = 1
+BEM_BIBEE_CFA = 0
+BEM_BIBEE_P = 1
+BEM_BIBEE_PLUS_HALF = 2
+BEM_FLAG_NO_FAR = 1
+BEM_FLAG_NO_NEAR = 2
+BEM_FLAG_NO_NEARTAB = 4
+BEM_CHARGE_AUTO = 0
+BEM_CHARGE_FMM = 1
+BEM_CHARGE_DIRECT = 2
+
+ERROR_NAMES = {0: "BEM_OK", -1: "BEM_EINVAL", -2: "BEM_ENOMEM", -3: "BEM_ECUDA",
+               -4: "BEM_ENOCONV", -5: "BEM_ETIMEOUT", -6: "BEM_EUNSUPPORTED"}
+
+
+class bem_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("p", ctypes.c_int), ("leaf_size", ctypes.c_int),
+                ("depth", ctypes.c_int), ("quad_points", ctypes.c_int),
+                ("gmres_restart", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("tol", ctypes.c_double), ("flags", ctypes.c_uint), ("near_table", ctypes.c_int),
+                ("charge_mode", ctypes.c_int)]
+
+
+class bem_solve_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("converged", ctypes.c_int), ("resid", ctypes.c_double),
+                ("true_resid", ctypes.c_double), ("ms_rhs", ctypes.c_double),
+                ("ms_gmres", ctypes.c_double), ("ms_total", ctypes.c_double)]
+
+
+class bem_mesh_info(ctypes.Structure):
+    _fields_ = [("n_p", ctypes.c_int64), ("n_c", ctypes.c_int64), ("depth", ctypes.c_int),
+                ("p", ctypes.c_int), ("precision", ctypes.c_int), ("leaves", ctypes.c_int64),
+                ("cells", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
+                ("m2l_pairs", ctypes.c_int64), ("m2m_pairs", ctypes.c_int64),
+                ("source_points", ctypes.c_int64), ("near_table_nnz", ctypes.c_int64),
+                ("root_side", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+                ("ms_build", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_SIGS = {
+    "bem_options_default": [ctypes.POINTER(bem_options)],
+    "bem_mesh_create": [_vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_double,
+                        ctypes.c_double, ctypes.POINTER(bem_options), _vp, ctypes.POINTER(_vp)],
+    "bem_mesh_destroy": [_vp],
+    "bem_set_charges": [_vp, _vp, ctypes.c_int64],
+    "bem_matvec": [_vp, _vp, _vp],
+    "bem_matvec_t": [_vp, _vp, _vp],
+    "bem_rhs": [_vp, _vp],
+    "bem_solve": [_vp, _vp, _vp, ctypes.POINTER(bem_solve_stats)],
+    "bem_bibee": [_vp, ctypes.c_int, _vp, _vp],
+    "bem_energy": [_vp, _vp, _vp, _vp],
+    "bem_energy_backward": [_vp, ctypes.c_double, _vp, _vp],
+    "bem_mesh_info_get": [_vp, ctypes.POINTER(bem_mesh_info)],
+    "bem_set_profiling": [_vp, ctypes.c_int],
+    "bem_last_phase_ms": [_vp, _vp],
+    "bem_last_error": [],
+}
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libbem.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libbem.so not found at {path}: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == "bem_last_error" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class BemError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = load_library().bem_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {ERROR_NAMES.get(code, code)}: {msg}")
+
+
+def _check(code: int, where: str, allow=()):
+    if code != BEM_OK and code not in allow:
+        raise BemError(code, where)
+    return code
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check_f64(a, n, name):
+    if a is None:
+        return
+    dt = getattr(a, "dtype", None)
+    ok = str(dt) in ("float64", "torch.float64")
+    if not ok:
+        raise TypeError(f"{name} must be float64")
+    cnt = a.numel() if hasattr(a, "numel") else a.size
+    if cnt != n:
+        raise ValueError(f"{name} must have {n} elements")
+
+
+# ---------------------------------------------------------------- C-ABI names
+def bem_options_default() -> bem_options:
+    o = bem_options()
+    _check(load_library().bem_options_default(ctypes.byref(o)), "bem_options_default")
+    return o
+
+
+def bem_mesh_create(panels, charges, eps_in, eps_out, opt: bem_options | None = None,
+                    stream=None):
+    lib = load_library()
+    n_p = int(panels.shape[0])
+    n_c = int(charges.shape[0]) if charges is not None else 0
+    _check_f64(panels, n_p * 9, "panels")
+    if charges is not None:
+        _check_f64(charges, n_c * 4, "charges")
+    h = ctypes.c_void_p()
+    o = opt if opt is not None else bem_options_default()
+    st = ctypes.c_void_p(stream) if stream is not None else None
+    _check(lib.bem_mesh_create(_ptr(panels), n_p, _ptr(charges), n_c, float(eps_in),
+                               float(eps_out), ctypes.byref(o), st, ctypes.byref(h)),
+           "bem_mesh_create")
+    return h
+
+
+def bem_mesh_destroy(h):
+    return _check(load_library().bem_mesh_destroy(h), "bem_mesh_destroy")
+
+
+def bem_set_charges(h, charges):
+    n_c = int(charges.shape[0])
+    return _check(load_library().bem_set_charges(h, _ptr(charges), n_c), "bem_set_charges")
+
+
+def bem_matvec(h, x, y):
+    return _check(load_library().bem_matvec(h, _ptr(x), _ptr(y)), "bem_matvec")
+
+
+def bem_matvec_t(h, x, y):
+    return _check(load_library().bem_matvec_t(h, _ptr(x), _ptr(y)), "bem_matvec_t")
+
+
+def bem_rhs(h, b):
+    return _check(load_library().bem_rhs(h, _ptr(b)), "bem_rhs")
+
+
+def bem_solve(h, x0, sigma, allow_noconv: bool = False):
+    st = bem_solve_stats()
+    allow = (BEM_ENOCONV,) if allow_noconv else ()
+    rc = _check(load_library().bem_solve(h, _ptr(x0), _ptr(sigma), ctypes.byref(st)),
+                "bem_solve", allow)
+    return rc, st
+
+
+def bem_bibee(h, variant: int, sigma_hat=None) -> float:
+    dg = ctypes.c_double()
+    _check(load_library().bem_bibee(h, int(variant), _ptr(sigma_hat), ctypes.byref(dg)),
+           "bem_bibee")
+    return dg.value
+
+
+def bem_energy(h, sigma, phi=None) -> float:
+    dg = ctypes.c_double()
+    _check(load_library().bem_energy(h, _ptr(sigma), ctypes.byref(dg), _ptr(phi)), "bem_energy")
+    return dg.value
+
+
+def bem_energy_backward(h, grad_out: float, dq=None, dx=None):
+    return _check(load_library().bem_energy_backward(h, float(grad_out), _ptr(dq), _ptr(dx)),
+                  "bem_energy_backward")
+
+
+def bem_mesh_info_get(h) -> bem_mesh_info:
+    info = bem_mesh_info()
+    _check(load_library().bem_mesh_info_get(h, ctypes.byref(info)), "bem_mesh_info_get")
+    return info
+
+
+def bem_set_profiling(h, enable: bool):
+    return _check(load_library().bem_set_profiling(h, 1 if enable else 0), "bem_set_profiling")
+
+
+def bem_last_phase_ms(h):
+    t = np.zeros(7)
+    _check(load_library().bem_last_phase_ms(h, _ptr(t)), "bem_last_phase_ms")
+    return dict(zip(["p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "epilogue"], t.tolist()))
+
+
+def bem_last_error() -> str:
+    return load_library().bem_last_error().decode(errors="replace")
+
+
+# --------------------------------------------------------------- convenience
+def make_options(**kw) -> bem_options:
+    o = bem_options_default()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Mesh:
+    """Owns one bem_mesh handle; arrays are torch CUDA tensors (f64)."""
+
+    def __init__(self, panels, charges, eps_in, eps_out, stream=None, **opts):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        pan = torch.as_tensor(panels, dtype=torch.float64).reshape(-1, 3, 3).contiguous()
+        ch = torch.as_tensor(charges, dtype=torch.float64).reshape(-1, 4).contiguous()
+        self.n_p, self.n_c = int(pan.shape[0]), int(ch.shape[0])
+        self.opt = make_options(**opts)
+        self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        self.h = bem_mesh_create(pan.to(self.device), ch.to(self.device), eps_in, eps_out,
+                                 self.opt, self.stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            bem_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _vec(self, n):
+        return self.torch.empty(n, dtype=self.torch.float64, device=self.device)
+
+    def _dev(self, x, n):
+        t = self.torch.as_tensor(x, dtype=self.torch.float64).to(self.device).contiguous()
+        if t.numel() != n:
+            raise ValueError(f"expected {n} values")
+        return t
+
+    def info(self) -> dict:
+        i = bem_mesh_info_get(self.h)
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def matvec(self, x):
+        y = self._vec(self.n_p)
+        bem_matvec(self.h, self._dev(x, self.n_p), y)
+        return y
+
+    def matvec_t(self, x):
+        y = self._vec(self.n_p)
+        bem_matvec_t(self.h, self._dev(x, self.n_p), y)
+        return y
+
+    def rhs(self):
+        b = self._vec(self.n_p)
+        bem_rhs(self.h, b)
+        return b
+
+    def solve(self, x0=None, allow_noconv=False):
+        s = self._vec(self.n_p)
+        rc, st = bem_solve(self.h, None if x0 is None else self._dev(x0, self.n_p), s,
+                           allow_noconv)
+        return s, {f: getattr(st, f) for f, _ in st._fields_}
+
+    def energy(self, sigma, want_phi=False):
+        phi = self._vec(self.n_c) if want_phi else None
+        dg = bem_energy(self.h, self._dev(sigma, self.n_p), phi)
+        return (dg, phi) if want_phi else dg
+
+    def bibee(self, variant=BEM_BIBEE_CFA, want_sigma=False):
+        s = self._vec(self.n_p) if want_sigma else None
+        dg = bem_bibee(self.h, variant, s)
+        return (dg, s) if want_sigma else dg
+
+    def energy_backward(self, grad_out=1.0):
+        dq = self._vec(self.n_c)
+        dx = self._vec(self.n_c * 3)
+        bem_energy_backward(self.h, grad_out, dq, dx)
+        return dq, dx.reshape(self.n_c, 3)
+
+    def set_charges(self, charges):
+        ch = self.torch.as_tensor(charges, dtype=self.torch.float64).reshape(-1, 4).contiguous()
+        bem_set_charges(self.h, ch.to(self.device))
+        self.n_c = int(ch.shape[0])

@@ -1,0 +1,465 @@
+// C-ABI entry points of libbem (declared in include/bem.h).
+//
+// Every entry point converts C++ exceptions into BEM_E* codes, records a
+// message for bem_last_error(), and accepts host or device arrays: host
+// arrays are staged through device buffers owned by the mesh.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "bem_internal.cuh"
+
+namespace bem {
+
+int gmres_solve(Mesh &m, const double *b, double *x, bool transpose, bem_solve_stats *st);
+double energy_from_phi(Mesh &m, const double *phi_s);
+void axpby(Mesh &m, double a, const double *x, double b, const double *y, double *out, int64_t n);
+void adjoint_gradients(Mesh &m, double grad_out, double *dq_s, double *dx_s);
+
+static thread_local std::string g_last_error = "no error";
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+static bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of an input array (copied through `stage` when it lives on the host).
+static const double *dev_in(Mesh &m, const double *p, size_t n, DArray<double> &stage) {
+    if (is_device_ptr(p)) return p;
+    if (stage.n < n) stage.alloc(n);
+    BEM_CUDA(cudaMemcpyAsync(stage.p, p, n * sizeof(double), cudaMemcpyHostToDevice, m.stream));
+    return stage.p;
+}
+
+struct OutArg {
+    double *user;
+    double *dev;
+    size_t n;
+    bool host;
+};
+
+static OutArg dev_out(Mesh &m, double *p, size_t n, DArray<double> &stage) {
+    OutArg o{p, p, n, false};
+    if (!is_device_ptr(p)) {
+        if (stage.n < n) stage.alloc(n);
+        o.dev = stage.p;
+        o.host = true;
+    }
+    return o;
+}
+
+static void finish_out(Mesh &m, const OutArg &o) {
+    if (o.host)
+        BEM_CUDA(cudaMemcpyAsync(o.user, o.dev, o.n * sizeof(double), cudaMemcpyDeviceToHost, m.stream));
+}
+
+static void sync(Mesh &m) { BEM_CUDA(cudaStreamSynchronize(m.stream)); }
+
+template <class F>
+static int guarded(F &&f) {
+    try {
+        f();
+        return BEM_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return BEM_ENOMEM;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return BEM_ECUDA;
+    }
+}
+
+size_t Mesh::bytes() const {
+    size_t b = tp.bytes() + tc.bytes();
+    b += cen_perm.bytes() + cen64.bytes() + nrm64.bytes() + area64.bytes() + cen32.bytes() +
+         nrm32.bytes() + cen64r.bytes() + nrm64r.bytes() + cen_key.bytes();
+    b += qp_panel.bytes() + qpg64.bytes() + qw64.bytes() + qp32.bytes() + qp64r.bytes() + qp_key.bytes();
+    b += chg_perm.bytes() + chgg64.bytes() + q64.bytes() + chg32.bytes() + chg64r.bytes() + chg_key.bytes();
+    b += nt_off.bytes() + nt_col.bytes() + nt_val.bytes();
+    b += tab.Rm2m_f.bytes() + tab.If_f.bytes() + tab.Rm2m_d.bytes() + tab.If_d.bytes();
+    b += Mf.bytes() + Lf.bytes() + Md.bytes() + Ld.bytes();
+    b += xs.bytes() + ys.bytes() + zs.bytes() + far_f.bytes() + near_f.bytes() + far_d.bytes() +
+         near_d.bytes() + io_a.bytes() + io_b.bytes() + red.bytes();
+    b += V.bytes() + H.bytes() + gv.bytes() + cs.bytes() + sn.bytes() + yv.bytes() + hv.bytes() +
+         part.bytes() + sigma_s.bytes();
+    return b;
+}
+
+static void alloc_work(Mesh &m) {
+    const int p = m.opt.p;
+    const size_t nc = (size_t)(p + 1) * (p + 1);
+    const size_t ncell = (size_t)std::max(m.tp.ncell, m.tc.ncell);
+    if (m.opt.precision == BEM_MIXED) {
+        m.Mf.alloc(ncell * nc);
+        m.Lf.alloc(ncell * nc);
+        const size_t nt = (size_t)std::max<int64_t>(m.np, m.nc);
+        m.far_f.alloc(nt);
+        m.near_f.alloc(nt);
+    } else {
+        m.Md.alloc(ncell * nc);
+        m.Ld.alloc(ncell * nc);
+        const size_t nt = (size_t)std::max<int64_t>(m.np, m.nc);
+        m.far_d.alloc(nt);
+        m.near_d.alloc(nt);
+    }
+    const size_t nv = (size_t)std::max<int64_t>(m.np, m.nc);
+    m.xs.alloc(nv);
+    m.ys.alloc(nv);
+    m.zs.alloc(nv * 3);
+    m.red.alloc(16);
+    m.part.alloc((size_t)(std::max(1, m.opt.gmres_restart) + 2) * 1024);
+}
+
+static void validate_options(const bem_options &o) {
+    if (o.precision != BEM_MIXED && o.precision != BEM_FP64)
+        throw Error(BEM_EINVAL, "precision must be BEM_MIXED or BEM_FP64");
+    if (o.p < 1 || o.p > MAXP) throw Error(BEM_EINVAL, "expansion order p must be in 1..16");
+    if (o.leaf_size < 1) throw Error(BEM_EINVAL, "leaf_size must be positive");
+    if (o.depth > MORTON_BITS) throw Error(BEM_EINVAL, "depth must be <= 21");
+    if (o.quad_points != 1 && o.quad_points != 7) throw Error(BEM_EINVAL, "quad_points must be 1 or 7");
+    if (o.gmres_restart < 1 || o.gmres_restart > 200) throw Error(BEM_EINVAL, "gmres_restart must be in 1..200");
+    if (o.max_iter < 1) throw Error(BEM_EINVAL, "max_iter must be positive");
+    if (!(o.tol > 0.0)) throw Error(BEM_EINVAL, "tol must be positive");
+    if (o.charge_mode < 0 || o.charge_mode > 2) throw Error(BEM_EINVAL, "charge_mode must be 0, 1 or 2");
+}
+
+}  // namespace bem
+
+using namespace bem;
+
+struct bem_mesh : public bem::Mesh {};
+
+extern "C" {
+
+int bem_options_default(bem_options *opt) {
+    if (!opt) {
+        set_last_error("bem_options_default: NULL");
+        return BEM_EINVAL;
+    }
+    opt->precision = BEM_MIXED;
+    opt->p = 10;
+    opt->leaf_size = 64;
+    opt->depth = 0;
+    opt->quad_points = 7;
+    opt->gmres_restart = 30;
+    opt->max_iter = 300;
+    opt->tol = 1e-8;
+    opt->flags = 0;
+    opt->near_table = 1;
+    opt->charge_mode = BEM_CHARGE_AUTO;
+    return BEM_OK;
+}
+
+int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, int64_t n_c,
+                    double eps_in, double eps_out, const bem_options *opt, void *stream,
+                    bem_mesh **out) {
+    if (!out) {
+        set_last_error("bem_mesh_create: out is NULL");
+        return BEM_EINVAL;
+    }
+    *out = nullptr;
+    bem_mesh *m = nullptr;
+    int rc = guarded([&] {
+        if (!panels || n_p <= 0) throw Error(BEM_EINVAL, "need at least one panel");
+        if (n_c < 0 || (n_c > 0 && !charges)) throw Error(BEM_EINVAL, "bad charge array");
+        if (!(eps_in > 0.0) || !(eps_out > 0.0) || !std::isfinite(eps_in) || !std::isfinite(eps_out))
+            throw Error(BEM_EINVAL, "permittivities must be positive and finite");
+        if (n_p * 7 > (int64_t)INT32_MAX - 1024 || n_c > (int64_t)INT32_MAX - 1024)
+            throw Error(BEM_EINVAL, "too many panels or charges for 32-bit indices");
+        auto t0 = std::chrono::steady_clock::now();
+        m = new bem_mesh();
+        if (opt) m->opt = *opt;
+        else bem_options_default(&m->opt);
+        validate_options(m->opt);
+        BEM_CUDA(cudaGetDevice(&m->device));
+        m->stream = (cudaStream_t)stream;
+        m->np = n_p;
+        m->nc = n_c;
+        m->nq = m->opt.quad_points;
+        m->nqp = n_p * m->nq;
+        m->eps_in = eps_in;
+        m->eps_out = eps_out;
+        m->ehat = 2.0 * (eps_in - eps_out) / (eps_in + eps_out);
+        BEM_CUDA(cudaMallocHost((void **)&m->h_pinned, 64));
+        DArray<double> sp, sc;
+        const double *dp = dev_in(*m, panels, (size_t)n_p * 9, sp);
+        const double *dc = n_c > 0 ? dev_in(*m, charges, (size_t)n_c * 4, sc) : nullptr;
+        build_geometry_and_trees(*m, dp, dc);
+        build_tables(*m);
+        alloc_work(*m);
+        if (m->opt.near_table) build_near_table(*m);
+        sync(*m);
+        m->ms_build = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    });
+    if (rc != BEM_OK) {
+        if (m) {
+            if (m->h_pinned) cudaFreeHost(m->h_pinned);
+            delete m;
+        }
+        return rc;
+    }
+    *out = m;
+    return BEM_OK;
+}
+
+int bem_mesh_destroy(bem_mesh *m) {
+    if (!m) return BEM_OK;
+    return guarded([&] {
+        if (m->stream) cudaStreamSynchronize(m->stream);
+        for (auto &e : m->tm.ev)
+            if (e) cudaEventDestroy(e);
+        if (m->h_pinned) cudaFreeHost(m->h_pinned);
+        delete m;
+    });
+}
+
+int bem_set_charges(bem_mesh *m, const double *charges, int64_t n_c) {
+    if (!m) return BEM_EINVAL;
+    return guarded([&] {
+        if (n_c < 0 || (n_c > 0 && !charges)) throw Error(BEM_EINVAL, "bad charge array");
+        DArray<double> sc;
+        const double *dc = n_c > 0 ? dev_in(*m, charges, (size_t)n_c * 4, sc) : nullptr;
+        m->nc = n_c;
+        rebuild_charge_tree(*m, dc);
+        alloc_work(*m);
+        m->have_sigma = false;
+        sync(*m);
+    });
+}
+
+int bem_matvec(bem_mesh *m, const double *x, double *y) {
+    if (!m || !x || !y) return BEM_EINVAL;
+    return guarded([&] {
+        const double *dx = dev_in(*m, x, m->np, m->io_a);
+        gather_f64(dx, m->cen_perm.p, m->xs.p, m->np, m->stream);
+        matvec_sorted(*m, m->xs.p, m->ys.p);
+        OutArg o = dev_out(*m, y, m->np, m->io_b);
+        scatter_f64(m->ys.p, m->cen_perm.p, o.dev, m->np, m->stream);
+        finish_out(*m, o);
+        sync(*m);
+    });
+}
+
+int bem_matvec_t(bem_mesh *m, const double *x, double *y) {
+    if (!m || !x || !y) return BEM_EINVAL;
+    return guarded([&] {
+        const double *dx = dev_in(*m, x, m->np, m->io_a);
+        gather_f64(dx, m->cen_perm.p, m->xs.p, m->np, m->stream);
+        matvec_t_sorted(*m, m->xs.p, m->ys.p);
+        OutArg o = dev_out(*m, y, m->np, m->io_b);
+        scatter_f64(m->ys.p, m->cen_perm.p, o.dev, m->np, m->stream);
+        finish_out(*m, o);
+        sync(*m);
+    });
+}
+
+static void rhs_sorted(Mesh &m, double *b_s) {
+    if (m.nc == 0) {
+        BEM_CUDA(cudaMemsetAsync(b_s, 0, m.np * sizeof(double), m.stream));
+        return;
+    }
+    charge_pass(m, SRC_CHARGE, TGT_CEN_DN, nullptr, m.zs.p);
+    axpby(m, -m.ehat, m.zs.p, 0.0, m.zs.p, b_s, m.np);
+}
+
+int bem_rhs(bem_mesh *m, double *b) {
+    if (!m || !b) return BEM_EINVAL;
+    return guarded([&] {
+        rhs_sorted(*m, m->ys.p);
+        OutArg o = dev_out(*m, b, m->np, m->io_b);
+        scatter_f64(m->ys.p, m->cen_perm.p, o.dev, m->np, m->stream);
+        finish_out(*m, o);
+        sync(*m);
+    });
+}
+
+int bem_solve(bem_mesh *m, const double *x0, double *sigma, bem_solve_stats *st) {
+    if (!m || !sigma) return BEM_EINVAL;
+    int status = BEM_OK;
+    int rc = guarded([&] {
+        cudaEvent_t e0, e1, e2;
+        BEM_CUDA(cudaEventCreate(&e0));
+        BEM_CUDA(cudaEventCreate(&e1));
+        BEM_CUDA(cudaEventCreate(&e2));
+        BEM_CUDA(cudaEventRecord(e0, m->stream));
+        if (m->sigma_s.n < (size_t)m->np) m->sigma_s.alloc(m->np);
+        DArray<double> b;
+        b.alloc(m->np);
+        rhs_sorted(*m, b.p);
+        BEM_CUDA(cudaEventRecord(e1, m->stream));
+        if (x0) {
+            const double *d0 = dev_in(*m, x0, m->np, m->io_a);
+            gather_f64(d0, m->cen_perm.p, m->sigma_s.p, m->np, m->stream);
+        } else {
+            BEM_CUDA(cudaMemsetAsync(m->sigma_s.p, 0, m->np * sizeof(double), m->stream));
+        }
+        bem_solve_stats local{};
+        status = gmres_solve(*m, b.p, m->sigma_s.p, false, &local);
+        BEM_CUDA(cudaEventRecord(e2, m->stream));
+        OutArg o = dev_out(*m, sigma, m->np, m->io_b);
+        scatter_f64(m->sigma_s.p, m->cen_perm.p, o.dev, m->np, m->stream);
+        finish_out(*m, o);
+        sync(*m);
+        float a = 0, c = 0;
+        cudaEventElapsedTime(&a, e0, e1);
+        cudaEventElapsedTime(&c, e1, e2);
+        local.ms_rhs = a;
+        local.ms_gmres = c;
+        local.ms_total = a + c;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(e2);
+        m->have_sigma = true;
+        if (st) *st = local;
+        if (status != BEM_OK) set_last_error("GMRES did not reach the tolerance");
+    });
+    return rc != BEM_OK ? rc : status;
+}
+
+static double energy_sorted(Mesh &m, const double *sig_s, double *phi_user) {
+    if (m.nc == 0) return 0.0;
+    double *phi_s = m.zs.p;  // n_c <= 3 * max(n_p, n_c)
+    charge_pass(m, SRC_QUAD, TGT_CHG_PHI, sig_s, phi_s);
+    const double dG = energy_from_phi(m, phi_s);
+    if (phi_user) {
+        // phi_reac = (C sigma) / eps_in in the caller's charge order
+        OutArg o = dev_out(m, phi_user, m.nc, m.io_b);
+        axpby(m, 1.0 / m.eps_in, phi_s, 0.0, phi_s, m.ys.p, m.nc);
+        scatter_f64(m.ys.p, m.chg_perm.p, o.dev, m.nc, m.stream);
+        finish_out(m, o);
+    }
+    return dG;
+}
+
+int bem_energy(bem_mesh *m, const double *sigma, double *dG, double *phi) {
+    if (!m || !sigma) return BEM_EINVAL;
+    return guarded([&] {
+        const double *ds = dev_in(*m, sigma, m->np, m->io_a);
+        gather_f64(ds, m->cen_perm.p, m->xs.p, m->np, m->stream);
+        const double e = energy_sorted(*m, m->xs.p, phi);
+        sync(*m);
+        if (dG) *dG = e;
+    });
+}
+
+int bem_bibee(bem_mesh *m, int variant, double *sigma_hat, double *dG) {
+    if (!m) return BEM_EINVAL;
+    return guarded([&] {
+        double lam;
+        if (variant == BEM_BIBEE_CFA) lam = -0.5;
+        else if (variant == BEM_BIBEE_P) lam = 0.0;
+        else if (variant == BEM_BIBEE_PLUS_HALF) lam = 0.5;
+        else throw Error(BEM_EINVAL, "unknown BIBEE variant");
+        // sigma_hat = -Ehat / (1 + Ehat lambda) (B q)
+        const double f = -m->ehat / (1.0 + m->ehat * lam);
+        if (m->nc == 0) BEM_CUDA(cudaMemsetAsync(m->xs.p, 0, m->np * sizeof(double), m->stream));
+        else {
+            charge_pass(*m, SRC_CHARGE, TGT_CEN_DN, nullptr, m->zs.p);
+            axpby(*m, f, m->zs.p, 0.0, m->zs.p, m->xs.p, m->np);
+        }
+        if (sigma_hat) {
+            OutArg o = dev_out(*m, sigma_hat, m->np, m->io_b);
+            scatter_f64(m->xs.p, m->cen_perm.p, o.dev, m->np, m->stream);
+            finish_out(*m, o);
+        }
+        double e = energy_sorted(*m, m->xs.p, nullptr);
+        sync(*m);
+        if (dG) *dG = e;
+    });
+}
+
+int bem_energy_backward(bem_mesh *m, double grad_out, double *dq, double *dx) {
+    if (!m) return BEM_EINVAL;
+    return guarded([&] {
+        if (m->nc == 0) return;
+        if (!m->have_sigma) {
+            bem_solve_stats st{};
+            if (m->sigma_s.n < (size_t)m->np) m->sigma_s.alloc(m->np);
+            DArray<double> b;
+            b.alloc(m->np);
+            rhs_sorted(*m, b.p);
+            BEM_CUDA(cudaMemsetAsync(m->sigma_s.p, 0, m->np * sizeof(double), m->stream));
+            gmres_solve(*m, b.p, m->sigma_s.p, false, &st);
+            m->have_sigma = true;
+        }
+        DArray<double> gq, gx;
+        gq.alloc(m->nc);
+        gx.alloc((size_t)m->nc * 3);
+        adjoint_gradients(*m, grad_out, gq.p, gx.p);
+        if (dq) {
+            OutArg o = dev_out(*m, dq, m->nc, m->io_a);
+            scatter_f64(gq.p, m->chg_perm.p, o.dev, m->nc, m->stream);
+            finish_out(*m, o);
+        }
+        if (dx) {
+            OutArg o = dev_out(*m, dx, (size_t)m->nc * 3, m->io_b);
+            gather_rows3(gx.p, m->chg_perm.p, o.dev, m->nc, m->stream);
+            finish_out(*m, o);
+        }
+        sync(*m);
+    });
+}
+
+int bem_mesh_info_get(const bem_mesh *m, bem_mesh_info *info) {
+    if (!m || !info) return BEM_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->n_p = m->np;
+    info->n_c = m->nc;
+    info->depth = m->L;
+    info->p = m->opt.p;
+    info->precision = m->opt.precision;
+    info->leaves = m->tp.nleaf;
+    info->cells = m->tp.ncell;
+    info->p2p_pairs = m->tp.p2p_pairs_cq;
+    info->m2l_pairs = m->tp.nm2l;
+    int64_t m2m = 0;
+    if (m->tp.L >= 2) m2m = m->tp.ncell - m->tp.lvl_off[2];
+    info->m2m_pairs = m2m;
+    info->source_points = m->nqp;
+    info->near_table_nnz = m->nt_nnz;
+    info->root_side = m->side;
+    info->device_bytes = m->bytes();
+    info->ms_build = m->ms_build;
+    return BEM_OK;
+}
+
+int bem_set_profiling(bem_mesh *m, int enable) {
+    if (!m) return BEM_EINVAL;
+    return guarded([&] {
+        if (enable && !m->tm.ev[0])
+            for (auto &e : m->tm.ev) BEM_CUDA(cudaEventCreate(&e));
+        m->tm.on = enable != 0;
+    });
+}
+
+int bem_last_phase_ms(const bem_mesh *m, double *times) {
+    if (!m || !times) return BEM_EINVAL;
+    if (!m->tm.on) {
+        set_last_error("profiling is off");
+        return BEM_EINVAL;
+    }
+    for (int k = 0; k < 7; ++k) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, m->tm.ev[k], m->tm.ev[k + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0;
+        }
+        times[k] = ms;
+    }
+    return BEM_OK;
+}
+
+const char *bem_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,235 @@
+// Internal declarations of libbem (not part of the public C ABI).
+//
+// Data layout in HBM (all arrays device-resident, owned by the mesh):
+//   * panels, quadrature points and charges are each sorted by their own
+//     63-bit Morton key (21 bits per axis, root cube shared by all sets);
+//   * every point record stores its coordinates relative to the centre of
+//     the leaf cell that contains it (FP32 float4 or FP64 double4, .w holds
+//     the weight A_j w_q or the charge), so near-field differences never see
+//     the absolute coordinate magnitude;
+//   * multipole / local expansions are (p+1)^2 reals per cell in the compact
+//     real layout  [n^2] = Re X_n^0,  [n^2 + 2m - 1] = Re X_n^m,
+//     [n^2 + 2m] = Im X_n^m  (m = 1..n), scaled by the cell size so that every
+//     translation operator is level independent.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/bem.h"
+
+namespace bem {
+
+constexpr int MAXP = 16;           // largest expansion order built
+constexpr int MORTON_BITS = 21;    // bits per axis in a key
+constexpr int NOFFSET = 343;       // (dx,dy,dz) in [-3,3]^3 -> 7*7*7 classes
+constexpr double PI = 3.14159265358979323846;
+constexpr double FOUR_PI = 12.566370614359172953850573533118;
+constexpr double KCAL = 332.0637;  // e^2/(4 pi eps0 A) in kcal/mol
+
+// ---------------------------------------------------------------- errors
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+void set_last_error(const std::string &msg);
+
+#define BEM_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            throw ::bem::Error(e_ == cudaErrorMemoryAllocation ? BEM_ENOMEM : BEM_ECUDA,  \
+                               std::string(#call) + ": " + cudaGetErrorString(e_) + " (" + \
+                                   __FILE__ + ":" + std::to_string(__LINE__) + ")");      \
+    } while (0)
+
+#define BEM_CHECK_LAUNCH() BEM_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------- device array (RAII)
+template <class T>
+struct DArray {
+    T *p = nullptr;
+    size_t n = 0;
+    DArray() = default;
+    DArray(const DArray &) = delete;
+    DArray &operator=(const DArray &) = delete;
+    DArray(DArray &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DArray &operator=(DArray &&o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DArray() { release(); }
+    void alloc(size_t count) {
+        release();
+        if (count == 0) count = 1;
+        BEM_CUDA(cudaMalloc((void **)&p, count * sizeof(T)));
+        n = count;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    size_t bytes() const { return n * sizeof(T); }
+    operator T *() const { return p; }
+};
+
+// ------------------------------------------------------------- structures
+// Octree over one or more point sets sharing the root cube and leaf level.
+struct Tree {
+    int L = 0;                    // leaf level
+    std::vector<int> lvl_off;     // cells of level l: [lvl_off[l], lvl_off[l+1])
+    int ncell = 0, nleaf = 0, leaf0 = 0;
+    DArray<uint64_t> key;         // [ncell] Morton key at the cell's own level
+    DArray<int4> ijk;             // [ncell] integer cell coordinates (x, y, z, level)
+    DArray<int> parent;           // [ncell] (-1 at the root)
+    DArray<int> child_beg;        // [ncell] first child (global index), -1 for leaves
+    DArray<int> child_end;        // [ncell]
+    DArray<int> cen_beg, qp_beg, chg_beg; // [nleaf+1] CSR of each sorted set over leaves
+    bool has_cen = false, has_qp = false, has_chg = false;
+    DArray<int> nbr_off, nbr;     // P2P: leaf -> adjacent leaves (incl. itself), CSR
+    DArray<int> m2l_off, m2l_src, m2l_ofs; // per cell CSR: source cell, offset class
+    int64_t nnbr = 0, nm2l = 0;
+    int64_t p2p_pairs_cq = 0;     // (centroid target, quad source) pairs
+    size_t bytes() const;
+};
+
+// Device-side view of a tree, passed to kernels by value.
+struct TreeView {
+    int L, ncell, nleaf, leaf0;
+    const int4 *ijk;
+    const int *parent, *child_beg, *child_end;
+    const int *cen_beg, *qp_beg, *chg_beg;
+    const int *nbr_off, *nbr;
+    const int *m2l_off, *m2l_src, *m2l_ofs;
+};
+
+TreeView view(const Tree &t);
+
+// Source and target kinds of one fast multipole pass.
+enum SrcKind { SRC_QUAD = 0, SRC_CHARGE = 1 };
+enum TgtKind { TGT_CEN_DN = 0, TGT_CHG_PHI = 1 };
+
+struct Mesh;
+
+// Expansion/translation tables of one expansion order and precision.
+struct Tables {
+    int p = 0;
+    DArray<float> Rm2m_f, If_f;   // FP32 tables
+    DArray<double> Rm2m_d, If_d;  // FP64 tables
+};
+
+struct Timers {
+    bool on = false;
+    cudaEvent_t ev[8] = {};
+    double ms[7] = {};
+};
+
+struct Mesh {
+    bem_options opt;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int64_t np = 0, nc = 0, nq = 0, nqp = 0;
+    double eps_in = 1, eps_out = 80, ehat = 0;
+    double root_min[3] = {0, 0, 0};
+    double side = 1;
+    int L = 0;
+    double ms_build = 0;
+
+    // sorted panels (targets / unknowns)
+    DArray<int> cen_perm;        // sorted -> original panel
+    DArray<double> cen64;        // [np][3] absolute centroid
+    DArray<double> nrm64;        // [np][3]
+    DArray<double> area64;       // [np]
+    DArray<float4> cen32, nrm32; // relative centroid / normal (mixed precision)
+    DArray<double4> cen64r, nrm64r; // relative centroid / normal (fp64 mode)
+    DArray<uint64_t> cen_key;
+    // sorted quadrature points (sources)
+    DArray<int> qp_panel;        // sorted quad point -> sorted panel
+    DArray<double> qpg64;        // [nqp][3] absolute coordinates
+    DArray<double> qw64;         // [nqp] A_j w_q
+    DArray<float4> qp32;         // (y_rel, A_j w_q)
+    DArray<double4> qp64r;
+    DArray<uint64_t> qp_key;
+    // sorted charges
+    DArray<int> chg_perm;        // sorted -> original charge
+    DArray<double> chgg64;       // [nc][3] absolute coordinates
+    DArray<double> q64;          // [nc] charge values (sorted order)
+    DArray<float4> chg32;        // (x_rel, q)
+    DArray<double4> chg64r;
+    DArray<uint64_t> chg_key;
+
+    Tree tp;   // panels (centroids + quadrature points): K' and K'^T
+    Tree tc;   // panels + charges: B, C and the adjoint charge terms
+
+    // near-singular FP64 table (CSR over sorted targets)
+    DArray<int> nt_off, nt_col;
+    DArray<double> nt_val;
+    int64_t nt_nnz = 0;
+
+    Tables tab;
+
+    // expansion buffers (sized for the larger tree)
+    DArray<float> Mf, Lf;
+    DArray<double> Md, Ld;
+
+    // work vectors
+    DArray<double> xs, ys, zs;         // sorted-order f64 vectors
+    DArray<float> far_f, near_f;       // per-target partial results (mixed)
+    DArray<double> far_d, near_d;      // (fp64 mode)
+    DArray<double> io_a, io_b;         // staging for host or unsorted arguments
+    DArray<double> red;                // reduction scratch
+    DArray<float> dpart_f;             // direct-sum partials (mixed)
+    DArray<double> dpart_d;            // direct-sum partials (fp64)
+    double *h_pinned = nullptr;        // small pinned host buffer
+
+    // GMRES workspace
+    DArray<double> V, H, gv, cs, sn, yv, hv, part;
+    // last solve (for the adjoint)
+    DArray<double> sigma_s;
+    bool have_sigma = false;
+
+    Timers tm;
+    size_t bytes() const;
+};
+
+// --------------------------------------------------------------- helpers
+inline int ncoef(int p) { return (p + 1) * (p + 1); }
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// geometry + trees (bem_tree.cu)
+void build_geometry_and_trees(Mesh &m, const double *d_panels, const double *d_charges);
+void rebuild_charge_tree(Mesh &m, const double *d_charges);
+void build_near_table(Mesh &m);
+void build_tables(Mesh &m);
+void compute_bbox(const double *d, int64_t n, int stride, double *lo, double *hi, cudaStream_t s);
+
+// fast multipole passes (bem_fmm.cu).  `dens` is indexed in sorted panel
+// order for SRC_QUAD (strength A_j w_q dens[panel]) and sorted charge order for
+// SRC_CHARGE (strength dens[k], or the stored q when dens is null).  The output
+// `out` (sorted target order, f64) receives sum over sources of
+//   TGT_CEN_DN : n_i . grad_{c_i} (s / (4 pi |c_i - y|))
+//   TGT_CHG_PHI: s / (4 pi |x_k - y|)
+void fmm_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const double *dens, double *out,
+              bool timed);
+
+// Products between the charges and the surface (B q, C sigma): the fast
+// multipole pass on the charge tree, or the direct sum over all pairs,
+// following opt.charge_mode.
+void charge_pass(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, double *out);
+bool charge_direct(const Mesh &m);
+void direct_pass(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, double *out);
+
+// solver pieces (bem_solver.cu)
+void matvec_sorted(Mesh &m, const double *xs, double *ys);
+void matvec_t_sorted(Mesh &m, const double *xs, double *ys);
+void exclusive_scan_int(const int *in, int *out, int n, cudaStream_t s);
+void gather_f64(const double *src, const int *perm, double *dst, int64_t n, cudaStream_t s);
+void scatter_f64(const double *src, const int *perm, double *dst, int64_t n, cudaStream_t s);
+void gather_rows3(const double *src, const int *perm, double *dst, int64_t n, cudaStream_t s);
+
+}  // namespace bem

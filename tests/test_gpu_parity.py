@@ -1,0 +1,178 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Tolerances (the benchmark spec): relative L2 error of the operator product <= 1e-5
+and of solvation energies <= 1e-5 in the mixed FP32/FP64 mode; the FP64 mode
+of the near field alone agrees with the dense FP64 sum to roundoff.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import rel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1007_4591_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def small4():
+    m = synth.small_molecule(4)
+    return m, oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+
+
+@pytest.fixture(scope="module")
+def born3():
+    m = synth.born(3)
+    return m, oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+
+
+def _x(n, seed=0):
+    return np.random.default_rng(seed).standard_normal(n)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 2e-6), (1, 1e-12)])
+def test_near_field_only_matches_dense(pkg, born3, precision, tol):
+    m, P = born3
+    x = _x(m.n_p)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=-1, precision=precision) as g:
+        y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, P.A(x)) < tol
+    kx_ref = P.kprime(x)
+    assert rel((y - x) / P.ehat, kx_ref) < 50 * tol
+
+
+@pytest.mark.parametrize("depth,p", [(2, 10), (3, 10), (3, 12), (4, 12)])
+def test_fmm_matvec_matches_dense(pkg, small4, depth, p):
+    m, P = small4
+    for x in (_x(m.n_p, 1), P.bq()):
+        ref = P.A(x)
+        with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=depth, p=p) as g:
+            y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+        assert rel(y, ref) < 1e-5, (depth, p, rel(y, ref))
+
+
+@pytest.mark.parametrize("depth", [2, 3])
+def test_fmm_matvec_fp64_mode(pkg, small4, depth):
+    m, P = small4
+    x = P.bq()
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=depth, p=12, precision=1) as g:
+        y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, P.A(x)) < 1e-6
+
+
+def test_ragged_open_surface(pkg):
+    # a subset of panels (not a closed surface): ragged leaves and tails
+    m = synth.small_molecule(4)
+    pan = np.ascontiguousarray(m.panels[:3001])
+    P = oracle.Problem(pan, m.charges, m.eps_in, m.eps_out)
+    x = _x(3001, 4)
+    with pkg.Mesh(pan, m.charges, m.eps_in, m.eps_out, depth=3, p=12) as g:
+        y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, P.A(x)) < 1e-5
+
+
+def test_rhs_matches_oracle(pkg, small4):
+    m, P = small4
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=3, p=12) as g:
+        b = g.rhs().cpu().numpy()
+    assert rel(b, P.rhs()) < 1e-5
+
+
+def test_energy_of_given_sigma(pkg, small4):
+    m, P = small4
+    sig = P.bq()
+    dg_ref, phi_ref = P.energy(sig)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=3, p=12) as g:
+        dg, phi = g.energy(torch.from_numpy(sig).cuda(), want_phi=True)
+    assert abs(dg - dg_ref) / abs(dg_ref) < 1e-5
+    assert rel(phi.cpu().numpy(), phi_ref / m.eps_in) < 1e-5
+
+
+def test_solve_and_energy_match_oracle(pkg, small4):
+    m, P = small4
+    sig_ref, _ = P.solve(tol=1e-11)
+    dg_ref, _ = P.energy(sig_ref)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=3, p=12, tol=1e-9) as g:
+        sig, st = g.solve()
+        dg = g.energy(sig)
+    assert st["converged"] == 1
+    assert rel(sig.cpu().numpy(), sig_ref) < 1e-5
+    assert abs(dg - dg_ref) / abs(dg_ref) < 1e-5
+
+
+def test_born_solve(pkg, born3):
+    m, P = born3
+    sig_ref, _ = P.solve(tol=1e-11)
+    dg_ref, _ = P.energy(sig_ref)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=10, leaf_size=64) as g:
+        sig, st = g.solve()
+        dg = g.energy(sig)
+    assert abs(dg - dg_ref) / abs(dg_ref) < 1e-5
+
+
+@pytest.mark.parametrize("variant,name", [(0, "cfa"), (1, "p"), (2, "plus_half")])
+def test_bibee_matches_oracle(pkg, small4, variant, name):
+    m, P = small4
+    sh_ref, dg_ref = P.bibee(name)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=3, p=12) as g:
+        dg, sh = g.bibee(variant, want_sigma=True)
+    assert rel(sh.cpu().numpy(), sh_ref) < 1e-5
+    assert abs(dg - dg_ref) / abs(dg_ref) < 1e-5
+
+
+def test_host_and_device_arguments_agree(pkg, small4):
+    m, P = small4
+    x = _x(m.n_p, 7)
+    h = pkg.bem_mesh_create(m.panels, m.charges, m.eps_in, m.eps_out, pkg.make_options(depth=3))
+    try:
+        y_host = np.empty(m.n_p)
+        pkg.bem_matvec(h, x, y_host)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.empty_like(xd)
+        pkg.bem_matvec(h, xd, yd)
+        assert np.array_equal(y_host, yd.cpu().numpy())
+    finally:
+        pkg.bem_mesh_destroy(h)
+
+
+def test_invalid_inputs_rejected(pkg):
+    m = synth.born(2)
+    bad = m.panels.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(pkg.BemError) as e:
+        pkg.bem_mesh_create(bad, m.charges, 1.0, 80.0)
+    assert e.value.code == pkg.BEM_EINVAL
+    deg = m.panels.copy()
+    deg[5, 2] = deg[5, 1]
+    with pytest.raises(pkg.BemError) as e:
+        pkg.bem_mesh_create(deg, m.charges, 1.0, 80.0)
+    assert e.value.code == pkg.BEM_EINVAL
+    with pytest.raises(pkg.BemError):
+        pkg.bem_mesh_create(m.panels, m.charges, -1.0, 80.0)
+    with pytest.raises(pkg.BemError):
+        pkg.bem_mesh_create(m.panels, m.charges, 1.0, 80.0, pkg.make_options(p=0))
+
+
+def test_full_size_sampled_rows(pkg):
+    """The 81,920-panel globular molecule in the benchmark's launch
+    configuration, checked on 256 sampled rows against the dense FP64 sum."""
+    m = synth.globular(6)
+    P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+    x = P.bq()
+    rows = np.random.default_rng(3).choice(m.n_p, 256, replace=False)
+    ref = x[rows] + P.ehat * P.kprime_rows(x, rows)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=12) as g:
+        y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+        info = g.info()
+    assert rel(y[rows], ref) < 1e-5, (rel(y[rows], ref), info["depth"])
