@@ -39,6 +39,9 @@ BEM_FLAG_NO_NEARTAB = 4
 BEM_CHARGE_AUTO = 0
 BEM_CHARGE_FMM = 1
 BEM_CHARGE_DIRECT = 2
+BEM_M2L_AUTO = 0
+BEM_M2L_DENSE = 1
+BEM_M2L_DIRECT = 2
 
 ERROR_NAMES = {0: "BEM_OK", -1: "BEM_EINVAL", -2: "BEM_ENOMEM", -3: "BEM_ECUDA",
                -4: "BEM_ENOCONV", -5: "BEM_ETIMEOUT", -6: "BEM_EUNSUPPORTED"}
@@ -49,7 +52,7 @@ class bem_options(ctypes.Structure):
                 ("depth", ctypes.c_int), ("quad_points", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("flags", ctypes.c_uint), ("near_table", ctypes.c_int),
-                ("charge_mode", ctypes.c_int)]
+                ("charge_mode", ctypes.c_int), ("m2l_mode", ctypes.c_int)]
 
 
 class bem_solve_stats(ctypes.Structure):
@@ -337,3 +340,44 @@ class Mesh:
         ch = self.torch.as_tensor(charges, dtype=self.torch.float64).reshape(-1, 4).contiguous()
         bem_set_charges(self.h, ch.to(self.device))
         self.n_c = int(ch.shape[0])
+
+
+# ------------------------------------------------------------------ autograd
+def _energy_function():
+    import torch
+
+    class SolvationEnergy(torch.autograd.Function):
+        """dG(charges) with the adjoint gradient (bem_energy_backward).
+
+        charges: [n_c, 4] float64 tensor (x, y, z, q).  Forward: the charge
+        tree is rebuilt for the new charges (the panel tree and near-field
+        tables are the mesh's), the BEM system is solved and dG returned in
+        kcal/mol.  Backward: one transposed solve, then d dG/dq and d dG/dx.
+        """
+
+        @staticmethod
+        def forward(ctx, charges, mesh):
+            mesh.set_charges(charges.detach().to(torch.float64).contiguous())
+            sig, st = mesh.solve()
+            dg = mesh.energy(sig)
+            ctx.mesh = mesh
+            return charges.new_tensor(dg)
+
+        @staticmethod
+        def backward(ctx, g):
+            dq, dx = ctx.mesh.energy_backward(float(g))
+            grad = torch.cat([dx, dq[:, None]], dim=1)
+            return grad, None
+
+    return SolvationEnergy
+
+
+_SE = None
+
+
+def solvation_energy(mesh: "Mesh", charges):
+    """Differentiable electrostatic solvation energy (kcal/mol) of `charges`."""
+    global _SE
+    if _SE is None:
+        _SE = _energy_function()
+    return _SE.apply(charges, mesh)

@@ -86,9 +86,11 @@ size_t Mesh::bytes() const {
          nrm32.bytes() + cen64r.bytes() + nrm64r.bytes() + cen_key.bytes();
     b += qp_panel.bytes() + qpg64.bytes() + qw64.bytes() + qp32.bytes() + qp64r.bytes() + qp_key.bytes();
     b += chg_perm.bytes() + chgg64.bytes() + q64.bytes() + chg32.bytes() + chg64r.bytes() + chg_key.bytes();
-    b += nt_off.bytes() + nt_col.bytes() + nt_val.bytes();
-    b += tab.Rm2m_f.bytes() + tab.If_f.bytes() + tab.Rm2m_d.bytes() + tab.If_d.bytes();
+    b += nt_off.bytes() + nt_col.bytes() + nt_val.bytes() + ntT_off.bytes() + ntT_col.bytes() +
+         ntT_val.bytes() + qp_of_panel.bytes();
+    if (tab) b += tab->bytes();
     b += Mf.bytes() + Lf.bytes() + Md.bytes() + Ld.bytes();
+    b += str32.bytes() + str64.bytes() + dpart_f.bytes() + dpart_d.bytes();
     b += xs.bytes() + ys.bytes() + zs.bytes() + far_f.bytes() + near_f.bytes() + far_d.bytes() +
          near_d.bytes() + io_a.bytes() + io_b.bytes() + red.bytes();
     b += V.bytes() + H.bytes() + gv.bytes() + cs.bytes() + sn.bytes() + yv.bytes() + hv.bytes() +
@@ -97,22 +99,24 @@ size_t Mesh::bytes() const {
 }
 
 static void alloc_work(Mesh &m) {
-    const int p = m.opt.p;
-    const size_t nc = (size_t)(p + 1) * (p + 1);
+    const size_t nc = (size_t)cell_stride(m.opt.p);
     const size_t ncell = (size_t)std::max(m.tp.ncell, m.tc.ncell);
     if (m.opt.precision == BEM_MIXED) {
         m.Mf.alloc(ncell * nc);
         m.Lf.alloc(ncell * nc);
-        const size_t nt = (size_t)std::max<int64_t>(m.np, m.nc);
+        const size_t nt = (size_t)std::max<int64_t>(std::max<int64_t>(m.np, m.nc), m.nqp);
         m.far_f.alloc(nt);
         m.near_f.alloc(nt);
     } else {
         m.Md.alloc(ncell * nc);
         m.Ld.alloc(ncell * nc);
-        const size_t nt = (size_t)std::max<int64_t>(m.np, m.nc);
+        const size_t nt = (size_t)std::max<int64_t>(std::max<int64_t>(m.np, m.nc), m.nqp);
         m.far_d.alloc(nt);
         m.near_d.alloc(nt);
     }
+    const size_t nsrc = (size_t)std::max<int64_t>(m.nqp, m.nc);
+    if (m.opt.precision == BEM_MIXED) m.str32.alloc(nsrc);
+    else m.str64.alloc(nsrc);
     const size_t nv = (size_t)std::max<int64_t>(m.np, m.nc);
     m.xs.alloc(nv);
     m.ys.alloc(nv);
@@ -132,6 +136,7 @@ static void validate_options(const bem_options &o) {
     if (o.max_iter < 1) throw Error(BEM_EINVAL, "max_iter must be positive");
     if (!(o.tol > 0.0)) throw Error(BEM_EINVAL, "tol must be positive");
     if (o.charge_mode < 0 || o.charge_mode > 2) throw Error(BEM_EINVAL, "charge_mode must be 0, 1 or 2");
+    if (o.m2l_mode < 0 || o.m2l_mode > 2) throw Error(BEM_EINVAL, "m2l_mode must be 0, 1 or 2");
 }
 
 }  // namespace bem
@@ -158,6 +163,7 @@ int bem_options_default(bem_options *opt) {
     opt->flags = 0;
     opt->near_table = 1;
     opt->charge_mode = BEM_CHARGE_AUTO;
+    opt->m2l_mode = BEM_M2L_AUTO;
     return BEM_OK;
 }
 
@@ -197,6 +203,8 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
         const double *dc = n_c > 0 ? dev_in(*m, charges, (size_t)n_c * 4, sc) : nullptr;
         build_geometry_and_trees(*m, dp, dc);
         build_tables(*m);
+        build_translation_groups(*m, m->tp);
+        build_translation_groups(*m, m->tc);
         alloc_work(*m);
         if (m->opt.near_table) build_near_table(*m);
         sync(*m);
@@ -232,6 +240,7 @@ int bem_set_charges(bem_mesh *m, const double *charges, int64_t n_c) {
         const double *dc = n_c > 0 ? dev_in(*m, charges, (size_t)n_c * 4, sc) : nullptr;
         m->nc = n_c;
         rebuild_charge_tree(*m, dc);
+        build_translation_groups(*m, m->tc);
         alloc_work(*m);
         m->have_sigma = false;
         sync(*m);
@@ -404,7 +413,7 @@ int bem_energy_backward(bem_mesh *m, double grad_out, double *dq, double *dx) {
         }
         if (dx) {
             OutArg o = dev_out(*m, dx, (size_t)m->nc * 3, m->io_b);
-            gather_rows3(gx.p, m->chg_perm.p, o.dev, m->nc, m->stream);
+            scatter_rows3(gx.p, m->chg_perm.p, o.dev, m->nc, m->stream);
             finish_out(*m, o);
         }
         sync(*m);

@@ -21,8 +21,11 @@
 // the offsets are (+-1/4)^3 for parent/child and integer vectors in
 // [-3,3]^3 for M2L.  The paper rotates every expansion before an axial
 // translation (Sec. 4.3); here the 343 offset classes are tabulated once.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "bem_internal.cuh"
 
@@ -131,8 +134,7 @@ __device__ __forceinline__ void load_full(const T *src, int p, cpx<T> *dst) {
 
 // ------------------------------------------------------------------- P2M
 template <class T, int SRC>
-__global__ void k_p2m(TreeView tv, const typename V4T<T>::t *rec, const int *qpanel,
-                      const double *dens, int p, T inv_h, T *M) {
+__global__ void k_p2m(TreeView tv, const typename V4T<T>::t *rec, int p, int cs, T inv_h, T *M) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sh = reinterpret_cast<T *>(smraw);
     const int leaf = blockIdx.x;
@@ -148,9 +150,7 @@ __global__ void k_p2m(TreeView tv, const typename V4T<T>::t *rec, const int *qpa
         T *row = sh + threadIdx.x * nc;
         if (i < e) {
             const typename V4T<T>::t r = rec[i];
-            T s;
-            if (SRC == SRC_QUAD) s = r.w * (T)dens[qpanel[i]];
-            else s = dens ? (T)dens[i] : r.w;
+            const T s = r.w;  // strength record
             regular_solid<T>(r.x * inv_h, r.y * inv_h, r.z * inv_h, p,
                              [&](int n, int m, T re, T im) {
                                  if (m == 0) row[n * n] = s * re;
@@ -172,7 +172,7 @@ __global__ void k_p2m(TreeView tv, const typename V4T<T>::t *rec, const int *qpa
         }
         __syncthreads();
     }
-    T *out = M + (size_t)(tv.leaf0 + leaf) * nc;
+    T *out = M + (size_t)(tv.leaf0 + leaf) * cs;
     int k = 0;
     for (int c = threadIdx.x; c < nc; c += blockDim.x, ++k) {
 #pragma unroll
@@ -184,7 +184,7 @@ __global__ void k_p2m(TreeView tv, const typename V4T<T>::t *rec, const int *qpa
 // ------------------------------------------------------------------- M2M
 // Parents [first, last) gather their children's multipoles.
 template <class T>
-__global__ void k_m2m(TreeView tv, int first, const cpx<T> *Rtab, int p, T *M) {
+__global__ void k_m2m(TreeView tv, int first, const cpx<T> *Rtab, int p, int cs, T *M) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int W = 2 * p + 1;
     cpx<T> *Mc = reinterpret_cast<cpx<T> *>(smraw);
@@ -204,7 +204,7 @@ __global__ void k_m2m(TreeView tv, int first, const cpx<T> *Rtab, int p, T *M) {
     const int cb = tv.child_beg[cell], ce = tv.child_end[cell];
     for (int c = cb; c < ce; ++c) {
         __syncthreads();
-        load_full<T>(M + (size_t)c * nc, p, Mc);
+        load_full<T>(M + (size_t)c * cs, p, Mc);
         const int4 q = tv.ijk[c];
         const int oct = (q.x & 1) | ((q.y & 1) << 1) | ((q.z & 1) << 2);
         const cpx<T> *R = Rtab + (size_t)oct * (p + 1) * W;
@@ -225,7 +225,7 @@ __global__ void k_m2m(TreeView tv, int first, const cpx<T> *Rtab, int p, T *M) {
         }
     }
     if (t < ntri) {
-        T *out = M + (size_t)cell * nc;
+        T *out = M + (size_t)cell * cs;
         if (m == 0) out[n * n] = acc.x;
         else {
             out[n * n + 2 * m - 1] = acc.x;
@@ -238,7 +238,7 @@ __global__ void k_m2m(TreeView tv, int first, const cpx<T> *Rtab, int p, T *M) {
 // Cells [first, first + gridDim.x) receive their interaction lists; the local
 // expansion is overwritten (L2L adds the parent's part afterwards).
 template <class T>
-__global__ void k_m2l(TreeView tv, int first, const cpx<T> *Itab, int p, const T *M, T *L) {
+__global__ void k_m2l(TreeView tv, int first, const cpx<T> *Itab, int p, int cs, const T *M, T *L) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int W = 2 * p + 1, W2 = 4 * p + 1;
     cpx<T> *Ms = reinterpret_cast<cpx<T> *>(smraw);
@@ -259,7 +259,7 @@ __global__ void k_m2l(TreeView tv, int first, const cpx<T> *Itab, int p, const T
     const int itot = (2 * p + 1) * W2;
     for (int e = eb; e < ee; ++e) {
         __syncthreads();
-        load_full<T>(M + (size_t)tv.m2l_src[e] * nc, p, Ms);
+        load_full<T>(M + (size_t)tv.m2l_src[e] * cs, p, Ms);
         const cpx<T> *I = Itab + (size_t)tv.m2l_ofs[e] * itot;
         for (int idx = t; idx < itot; idx += blockDim.x) It[idx] = I[idx];
         __syncthreads();
@@ -273,7 +273,7 @@ __global__ void k_m2l(TreeView tv, int first, const cpx<T> *Itab, int p, const T
     }
     if (t < ntri) {
         const T sg = (k & 1) ? (T)-1 : (T)1;
-        T *out = L + (size_t)cell * nc;
+        T *out = L + (size_t)cell * cs;
         if (l == 0) out[k * k] = sg * acc.x;
         else {
             out[k * k + 2 * l - 1] = sg * acc.x;
@@ -285,7 +285,7 @@ __global__ void k_m2l(TreeView tv, int first, const cpx<T> *Itab, int p, const T
 // ------------------------------------------------------------------- L2L
 // Children [first, first + gridDim.x) add their parent's local expansion.
 template <class T>
-__global__ void k_l2l(TreeView tv, int first, const cpx<T> *Rtab, int p, T *L) {
+__global__ void k_l2l(TreeView tv, int first, const cpx<T> *Rtab, int p, int cs, T *L) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int W = 2 * p + 1;
     cpx<T> *Lp = reinterpret_cast<cpx<T> *>(smraw);
@@ -295,7 +295,7 @@ __global__ void k_l2l(TreeView tv, int first, const cpx<T> *Rtab, int p, T *L) {
     const int ntri = (p + 1) * (p + 2) / 2;
     const int t = threadIdx.x;
     const int P = tv.parent[cell];
-    load_full<T>(L + (size_t)P * nc, p, Lp);
+    load_full<T>(L + (size_t)P * cs, p, Lp);
     const int4 q = tv.ijk[cell];
     const int oct = (q.x & 1) | ((q.y & 1) << 1) | ((q.z & 1) << 2);
     const cpx<T> *R = Rtab + (size_t)oct * (p + 1) * W;
@@ -313,7 +313,7 @@ __global__ void k_l2l(TreeView tv, int first, const cpx<T> *Rtab, int p, T *L) {
                 cmac_conjb<T>(acc, Lp[n * W + mm + p], Rd[j * W + (mm - l) + p]);
         }
         const T s = K<T>::pow2n(k + 1);
-        T *out = L + (size_t)cell * nc;
+        T *out = L + (size_t)cell * cs;
         if (l == 0) out[k * k] += s * acc.x;
         else {
             out[k * k + 2 * l - 1] += s * acc.x;
@@ -325,15 +325,15 @@ __global__ void k_l2l(TreeView tv, int first, const cpx<T> *Rtab, int p, T *L) {
 // ------------------------------------------------------------------- L2P
 template <class T, int TGT>
 __global__ void k_l2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
-                      int p, T inv_h, const T *L, T *out) {
+                      int p, int cs, T inv_h, const T *L, T *out) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int W = 2 * p + 1;
     cpx<T> *Lf = reinterpret_cast<cpx<T> *>(smraw);
     const int leaf = blockIdx.x;
-    const int *beg = TGT == TGT_CEN_DN ? tv.cen_beg : tv.chg_beg;
+    const int *beg = TGT == TGT_CEN_DN ? tv.cen_beg : (TGT == TGT_QUAD_PHI ? tv.qp_beg : tv.chg_beg);
     const int b = beg[leaf], e = beg[leaf + 1];
     if (b == e) return;
-    load_full<T>(L + (size_t)(tv.leaf0 + leaf) * (p + 1) * (p + 1), p, Lf);
+    load_full<T>(L + (size_t)(tv.leaf0 + leaf) * cs, p, Lf);
     __syncthreads();
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
         const typename V4T<T>::t r = tgt[i];
@@ -406,15 +406,70 @@ __device__ __forceinline__ void dn_pair(T dx, T dy, T dz, T nx, T ny, T nz, T &n
     ri3 = ri * ri * ri;
 }
 
+// Source strengths of one pass, s = A_j w_q dens[panel] for quadrature
+// points or s = q_k (or dens[k]) for charges, written next to the
+// leaf-relative coordinates so that P2M and P2P read one record per source.
+template <class T, int SRC>
+__global__ void k_strength(const typename V4T<T>::t *rec, const int *qpanel, const double *dens,
+                           int64_t n, typename V4T<T>::t *out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    typename V4T<T>::t r = rec[i];
+    if (SRC == SRC_QUAD) r.w = r.w * (T)dens[qpanel[i]];
+    else if (dens) r.w = (T)dens[i];
+    out[i] = r;
+}
+
+// Two lanes of T: packed FP32 instructions on sm_100+ (per component the
+// same rounding as the scalar fmaf / fadd / fmul), plain pairs for FP64.
+template <class T> struct Pk;
+template <> struct Pk<float> {
+    using v = float2;
+    __device__ static v mk(float a, float b) { return make_float2(a, b); }
+    __device__ static v add(v a, v b) { return __fadd2_rn(a, b); }
+    __device__ static v sub(v a, v b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+    __device__ static v mul(v a, v b) { return __fmul2_rn(a, b); }
+    __device__ static v fma(v a, v b, v c) { return __ffma2_rn(a, b, c); }
+};
+template <> struct Pk<double> {
+    using v = double2;
+    __device__ static v mk(double a, double b) { return make_double2(a, b); }
+    __device__ static v add(v a, v b) { return make_double2(a.x + b.x, a.y + b.y); }
+    __device__ static v sub(v a, v b) { return make_double2(a.x - b.x, a.y - b.y); }
+    __device__ static v mul(v a, v b) { return make_double2(a.x * b.x, a.y * b.y); }
+    __device__ static v fma(v a, v b, v c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
+};
+
+// Near field of one target leaf: every source point of the adjacent leaves
+// (and the leaf itself), staged through shared memory in tiles of
+// P2P_TILE sources, coordinates moved into the target leaf's frame.  Sources
+// are stored in pairs, (x0,x1,y0,y1) and (z0,z1,w0,w1), so that one packed
+// instruction evaluates a target against two sources.
+// Thread mapping: targets are taken P2P_TPT at a time into groups; the
+// threads split into ngroups x G (G = threads / ngroups, any integer), each
+// thread owning P2P_TPT targets and a 1/G share of the source pairs of each
+// tile.  Tile sums go into a second accumulator; the G partial sums of a
+// target are added in a fixed order at the end.  A pair of coincident points
+// (a collocation point and its own panel's centroid node) gives d = 0,
+// n.d = 0 and r^2 = eps, a finite zero.
+template <class T> struct P2PTpt;
+template <> struct P2PTpt<float> { static constexpr int v = 4; };
+template <> struct P2PTpt<double> { static constexpr int v = 2; };
+constexpr int P2P_TILE = 2 * P2P_THREADS;
+
 template <class T, int SRC, int TGT>
 __global__ void __launch_bounds__(P2P_THREADS)
 k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
-      const typename V4T<T>::t *src, const int *qpanel, const double *dens, T h, T *out) {
+      const typename V4T<T>::t *src, T h, T *out) {
     using V4 = typename V4T<T>::t;
-    __shared__ V4 sh[P2P_THREADS];
+    using P = Pk<T>;
+    using v2 = typename P::v;
+    constexpr int P2P_TPT = P2PTpt<T>::v;
+    __shared__ V4 shA[P2P_THREADS], shB[P2P_THREADS];
     __shared__ int s_beg[28], s_cum[28];
     __shared__ T s_off[27][3];
-    const int leaf = blockIdx.x;
+    __shared__ T s_part[P2P_THREADS * 4];
+    const int leaf = tv.p2p_order[blockIdx.x];  // heaviest leaves first
     const int *tb_ = TGT == TGT_CEN_DN ? tv.cen_beg : tv.chg_beg;
     const int *sb_ = SRC == SRC_QUAD ? tv.qp_beg : tv.chg_beg;
     const int tb = tb_[leaf], te = tb_[leaf + 1];
@@ -438,74 +493,268 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
     __syncthreads();
     const int total = s_cum[nn];
     const int ntgt = te - tb;
-    int G = 1;
-    while (G < 8 && ntgt * G * 2 <= P2P_THREADS) G *= 2;
-    const int per = P2P_THREADS / G;
-    const int g = threadIdx.x & (G - 1);
-    const T EPS = P2PEps<T>::v;
-    for (int t0 = 0; t0 < ntgt; t0 += per) {
-        const int ti = t0 + threadIdx.x / G;
-        const bool valid = ti < ntgt;
-        T cx = 0, cy = 0, cz = 0, nx = 0, ny = 0, nz = 0;
-        if (valid) {
-            const V4 c = tgt[tb + ti];
-            cx = c.x;
-            cy = c.y;
-            cz = c.z;
-            if (TGT == TGT_CEN_DN) {
-                const V4 nv = nrm[tb + ti];
-                nx = nv.x;
-                ny = nv.y;
-                nz = nv.z;
+    const v2 EPS2 = P::mk(P2PEps<T>::v, P2PEps<T>::v);
+    constexpr int MAXT = (P2P_THREADS / 4) * P2P_TPT;  // targets per pass (G >= 4)
+    // staged source v (0 <= v < total) in the target leaf's frame, or a zero-weight dummy
+    auto fetch = [&](int v, T &x, T &y, T &z, T &w) {
+        x = y = z = w = 0;
+        if (v < total) {
+            int lo = 0, hi = nn;  // segment k with s_cum[k] <= v < s_cum[k+1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_cum[mid] <= v) lo = mid;
+                else hi = mid;
             }
+            const V4 r = src[s_beg[lo] + (v - s_cum[lo])];
+            x = r.x + s_off[lo][0];
+            y = r.y + s_off[lo][1];
+            z = r.z + s_off[lo][2];
+            w = r.w;
         }
-        T outer = 0;  // sum of per-tile sums (short FP32 accumulations)
-        for (int vb = 0; vb < total; vb += P2P_THREADS) {
-            __syncthreads();
-            const int v = vb + threadIdx.x;
-            if (v < total) {
-                int lo = 0, hi = nn;  // segment k with s_cum[k] <= v < s_cum[k+1]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s_cum[mid] <= v) lo = mid;
-                    else hi = mid;
+    };
+    for (int t0 = 0; t0 < ntgt; t0 += MAXT) {
+        const int nt = min(ntgt - t0, MAXT);
+        const int ngroups = (nt + P2P_TPT - 1) / P2P_TPT;
+        const int G = P2P_THREADS / ngroups;
+        const int grp = threadIdx.x / G, g = threadIdx.x - grp * G;
+        const bool active = grp < ngroups;
+        v2 cx[P2P_TPT], cy[P2P_TPT], cz[P2P_TPT], nx[P2P_TPT], ny[P2P_TPT], nz[P2P_TPT];
+        T outer[P2P_TPT];
+#pragma unroll
+        for (int q = 0; q < P2P_TPT; ++q) {
+            const int ti = grp * P2P_TPT + q;
+            T a = 0, b = 0, c = 0, d = 0, e = 0, f = 0;
+            if (active && ti < nt) {
+                const V4 cv = tgt[tb + t0 + ti];
+                a = cv.x;
+                b = cv.y;
+                c = cv.z;
+                if (TGT == TGT_CEN_DN) {
+                    const V4 nv = nrm[tb + t0 + ti];
+                    d = nv.x;
+                    e = nv.y;
+                    f = nv.z;
                 }
-                const int si = s_beg[lo] + (v - s_cum[lo]);
-                V4 r = src[si];
-                T s;
-                if (SRC == SRC_QUAD) s = r.w * (T)dens[qpanel[si]];
-                else s = dens ? (T)dens[si] : r.w;
-                r.x += s_off[lo][0];
-                r.y += s_off[lo][1];
-                r.z += s_off[lo][2];
-                r.w = s;
-                sh[threadIdx.x] = r;
+            }
+            cx[q] = P::mk(a, a);
+            cy[q] = P::mk(b, b);
+            cz[q] = P::mk(c, c);
+            nx[q] = P::mk(d, d);
+            ny[q] = P::mk(e, e);
+            nz[q] = P::mk(f, f);
+            outer[q] = 0;
+        }
+        for (int vb = 0; vb < total; vb += P2P_TILE) {
+            __syncthreads();
+            {
+                T x0, y0, z0, w0, x1, y1, z1, w1;
+                fetch(vb + 2 * threadIdx.x, x0, y0, z0, w0);
+                fetch(vb + 2 * threadIdx.x + 1, x1, y1, z1, w1);
+                V4 a, b;
+                a.x = x0; a.y = x1; a.z = y0; a.w = y1;
+                b.x = z0; b.y = z1; b.z = w0; b.w = w1;
+                shA[threadIdx.x] = a;
+                shB[threadIdx.x] = b;
             }
             __syncthreads();
-            const int cnt = min(P2P_THREADS, total - vb);
-            T acc = 0;
-            if (valid) {
-#pragma unroll 4
-                for (int j = g; j < cnt; j += G) {
-                    const V4 y = sh[j];
-                    const T dx = cx - y.x, dy = cy - y.y, dz = cz - y.z;
-                    if (TGT == TGT_CEN_DN) {
-                        T nd, ri3;
-                        dn_pair<T>(dx, dy, dz, nx, ny, nz, nd, ri3);
-                        acc = fma(y.w * nd, ri3, acc);
-                    } else {
-                        const T r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, EPS)));
-                        acc = fma(y.w, rsq(r2), acc);
+            const int npair = min(P2P_THREADS, (total - vb + 1) >> 1);
+            if (active) {
+                v2 acc[P2P_TPT];
+#pragma unroll
+                for (int q = 0; q < P2P_TPT; ++q) acc[q] = P::mk(0, 0);
+#pragma unroll 2
+                for (int j = g; j < npair; j += G) {
+                    const V4 a = shA[j], b = shB[j];
+                    const v2 yx = P::mk(a.x, a.y), yy = P::mk(a.z, a.w);
+                    const v2 yz = P::mk(b.x, b.y), yw = P::mk(b.z, b.w);
+#pragma unroll
+                    for (int q = 0; q < P2P_TPT; ++q) {
+                        const v2 dx = P::sub(cx[q], yx), dy = P::sub(cy[q], yy), dz = P::sub(cz[q], yz);
+                        const v2 r2 = P::fma(dx, dx, P::fma(dy, dy, P::fma(dz, dz, EPS2)));
+                        const v2 ri = P::mk(rsq(r2.x), rsq(r2.y));
+                        if (TGT == TGT_CEN_DN) {
+                            const v2 nd = P::fma(nx[q], dx, P::fma(ny[q], dy, P::mul(nz[q], dz)));
+                            const v2 ri3 = P::mul(P::mul(ri, ri), ri);
+                            acc[q] = P::fma(P::mul(yw, nd), ri3, acc[q]);
+                        } else {
+                            acc[q] = P::fma(yw, ri, acc[q]);
+                        }
                     }
                 }
+#pragma unroll
+                for (int q = 0; q < P2P_TPT; ++q) outer[q] += acc[q].x + acc[q].y;
             }
-            outer += acc;
         }
-        for (int o = G >> 1; o > 0; o >>= 1) outer += __shfl_xor_sync(0xffffffffu, outer, o);
-        if (valid && g == 0) out[tb + ti] = (TGT == TGT_CEN_DN) ? -outer : outer;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < P2P_TPT; ++q) s_part[threadIdx.x * P2P_TPT + q] = outer[q];
+        __syncthreads();
+        if (threadIdx.x < nt) {
+            const int gr = threadIdx.x / P2P_TPT, q = threadIdx.x - gr * P2P_TPT;
+            T a = 0;
+            for (int k = 0; k < G; ++k) a += s_part[(gr * G + k) * P2P_TPT + q];
+            out[tb + t0 + threadIdx.x] = (TGT == TGT_CEN_DN) ? -a : a;
+        }
     }
 }
 
+// ------------------------------------------------------ transposed K' pass
+// Dipole sources p_i = lam_i n_i at the collocation points.  The multipole
+// of a dipole is its own degree-1 expansion D_1^0 = p_z,
+// D_1^{+-1} = -+ (p_x -+ i p_y)/2 translated like an M2M:
+//   M_n^m = sum_{l=-1..1} conj(R_{n-1}^{m-l}(c - z)) D_1^l,
+// accumulated here while the recurrence emits R_k^l (scaled by 1/h).
+template <class T>
+__global__ void k_p2m_dipole(TreeView tv, const typename V4T<T>::t *rec,
+                             const typename V4T<T>::t *nrm, const double *lam, int p, int cs,
+                             T inv_h, T *M) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sh = reinterpret_cast<T *>(smraw);
+    const int leaf = blockIdx.x;
+    const int b = tv.cen_beg[leaf], e = tv.cen_beg[leaf + 1];
+    const int nc = (p + 1) * (p + 1);
+    constexpr int MAXACC = 10;
+    T acc[MAXACC];
+#pragma unroll
+    for (int k = 0; k < MAXACC; ++k) acc[k] = 0;
+    for (int base = b; base < e; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        T *row = sh + threadIdx.x * nc;
+        for (int c = 0; c < nc; ++c) row[c] = 0;
+        if (i < e) {
+            const typename V4T<T>::t r = rec[i], nv = nrm[i];
+            const T l = (T)lam[i] * inv_h;
+            const T px = l * nv.x, py = l * nv.y, pz = l * nv.z;
+            // D_1^0 = pz, D_1^1 = -(px - i py)/2, D_1^-1 = (px + i py)/2
+            const T d1r = -px / 2, d1i = py / 2, dmr = px / 2, dmi = py / 2;
+            regular_solid<T>(r.x * inv_h, r.y * inv_h, r.z * inv_h, p - 1, [&](int k, int l, T re, T im) {
+                const int n = k + 1;
+                // conj(R) = (re, -im); add conj(R) * D to M_n^m
+                auto add = [&](int m, T dr, T di) {  // m >= 0
+                    const T vr = re * dr + im * di, vi = re * di - im * dr;
+                    if (m == 0) row[n * n] += vr;
+                    else {
+                        row[n * n + 2 * m - 1] += vr;
+                        row[n * n + 2 * m] += vi;
+                    }
+                };
+                add(l, pz, 0);
+                add(l + 1, d1r, d1i);
+                if (l >= 1) add(l - 1, dmr, dmi);
+                if (l == 1) {
+                    // R_k^{-1} = -conj(R_k^1): conj(R_k^{-1}) D_1^1 = -(re + i im)(d1r + i d1i)
+                    row[n * n] += -(re * d1r - im * d1i);
+                }
+            });
+        }
+        __syncthreads();
+        const int cnt = min((int)blockDim.x, e - base);
+        int k = 0;
+        for (int c = threadIdx.x; c < nc; c += blockDim.x, ++k) {
+            T a = 0;
+            for (int j = 0; j < cnt; ++j) a += sh[j * nc + c];
+#pragma unroll
+            for (int q = 0; q < MAXACC; ++q)
+                if (q == k) acc[q] += a;
+        }
+        __syncthreads();
+    }
+    T *out = M + (size_t)(tv.leaf0 + leaf) * cs;
+    int k = 0;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x, ++k) {
+#pragma unroll
+        for (int q = 0; q < MAXACC; ++q)
+            if (q == k) out[c] = acc[q];
+    }
+}
+
+// Near field of the transposed product, organised like the forward kernel:
+// one CTA per leaf T of collocation points; the quadrature points of the
+// adjacent leaves are moved into T's frame exactly as the forward kernel
+// moves them, so every pair value n.d |d|^-3 is bit-identical to the
+// forward one (the transposed near-singular table then replaces it exactly).
+// Each thread owns quadrature points and loops over T's collocation points
+// (staged with their lam_i and normals); results go out with one atomic add
+// per point and CTA.
+template <class T>
+__global__ void __launch_bounds__(P2P_THREADS)
+k_p2p_t(TreeView tv, const typename V4T<T>::t *cen, const typename V4T<T>::t *nrm,
+        const double *lam, const typename V4T<T>::t *qrec, T h, T *outq) {
+    using V4 = typename V4T<T>::t;
+    __shared__ V4 sc[P2P_THREADS], sn[P2P_THREADS];
+    __shared__ int s_beg[28], s_cum[28];
+    __shared__ T s_off[27][3];
+    const int leaf = tv.p2p_order[blockIdx.x];
+    const int tb = tv.cen_beg[leaf], te = tv.cen_beg[leaf + 1];
+    if (tb == te) return;
+    const int nb0 = tv.nbr_off[leaf], nn = tv.nbr_off[leaf + 1] - nb0;
+    const int4 ct = tv.ijk[tv.leaf0 + leaf];
+    if (threadIdx.x < nn) {
+        const int S = tv.nbr[nb0 + threadIdx.x];
+        const int4 cs = tv.ijk[tv.leaf0 + S];
+        s_beg[threadIdx.x] = tv.qp_beg[S];
+        s_cum[threadIdx.x + 1] = tv.qp_beg[S + 1] - tv.qp_beg[S];
+        s_off[threadIdx.x][0] = (T)((double)(cs.x - ct.x) * (double)h);
+        s_off[threadIdx.x][1] = (T)((double)(cs.y - ct.y) * (double)h);
+        s_off[threadIdx.x][2] = (T)((double)(cs.z - ct.z) * (double)h);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_cum[0] = 0;
+        for (int k = 0; k < nn; ++k) s_cum[k + 1] += s_cum[k];
+    }
+    __syncthreads();
+    const int total = s_cum[nn];
+    const int ntgt = te - tb;
+    for (int t0 = 0; t0 < ntgt; t0 += P2P_THREADS) {
+        const int nt = min(ntgt - t0, P2P_THREADS);
+        __syncthreads();
+        if (threadIdx.x < nt) {
+            V4 c = cen[tb + t0 + threadIdx.x];
+            c.w = (T)lam[tb + t0 + threadIdx.x];
+            sc[threadIdx.x] = c;
+            sn[threadIdx.x] = nrm[tb + t0 + threadIdx.x];
+        }
+        __syncthreads();
+        for (int v = threadIdx.x; v < total; v += P2P_THREADS) {
+            int lo = 0, hi = nn;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_cum[mid] <= v) lo = mid;
+                else hi = mid;
+            }
+            const int qi = s_beg[lo] + (v - s_cum[lo]);
+            V4 y = qrec[qi];
+            y.x += s_off[lo][0];
+            y.y += s_off[lo][1];
+            y.z += s_off[lo][2];
+            T acc = 0;
+            for (int i = 0; i < nt; ++i) {
+                const V4 c = sc[i], nv = sn[i];
+                T nd, ri3;
+                dn_pair<T>(c.x - y.x, c.y - y.y, c.z - y.z, nv.x, nv.y, nv.z, nd, ri3);
+                acc = fma(c.w * nd, ri3, acc);
+            }
+            atomicAdd(outq + qi, -acc);
+        }
+    }
+}
+
+// z_j = 1/(4 pi) sum_q A_j w_q (far_q + near_q) over the points of panel j
+template <class T>
+__global__ void k_panel_reduce(const T *far, const T *near, const int *qp_of_panel,
+                               const double *qw, int nq, int64_t np, double *out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    double a = 0.0;
+    for (int q = 0; q < nq; ++q) {
+        const int k = qp_of_panel[j * nq + q];
+        double v = near ? (double)near[k] : 0.0;
+        if (far) v += (double)far[k];
+        a += qw[k] * v;
+    }
+    out[j] = a / FOUR_PI;
+}
 
 // ------------------------------------------------------ near-singular table
 // For each collocation point i, the panels j close to it (centroid distance
@@ -597,14 +846,6 @@ __global__ void k_leaf_of(const int *beg, int nleaf, int *leaf_of) {
     for (int i = beg[l] + threadIdx.x; i < beg[l + 1]; i += blockDim.x) leaf_of[i] = l;
 }
 
-__global__ void k_qp_of_panel(const int *qp_panel, const uint64_t *dummy, int64_t nqp, int nq,
-                              int *slot_cnt, int *qp_of_panel) {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= nqp) return;
-    const int j = qp_panel[k];
-    const int s = atomicAdd(&slot_cnt[j], 1);
-    qp_of_panel[(int64_t)j * nq + s] = (int)k;
-}
 
 // ---------------------------------------------------------------- combine
 template <class T>
@@ -740,40 +981,359 @@ static void upload_constants(int dev) {
     if (dev >= 0 && dev < 64) g_consts_up[dev] = true;
 }
 
-void build_tables(Mesh &m) {
-    upload_constants(m.device);
-    const int p = m.opt.p;
+// Real (p+1)^2 x (p+1)^2 matrix of a complex translation
+//   out_k^l = sum_{n, m=-n..n} coef(k, l, n, m) in_n^m
+// acting on the compact real layout (both sides real fields, so
+// in_n^{-m} = (-1)^m conj(in_n^m)).  With P = coef(k,l,n,mu) and
+// Q = (-1)^mu coef(k,l,n,-mu), an input a + ib at (n, mu) contributes
+// a (P + Q) + i b (P - Q).  Stored column-major: Tt[in * nc + out].
+template <class F>
+static void real_operator(int p, F coef, double *Tt) {
+    const int nc = (p + 1) * (p + 1);
+    std::fill(Tt, Tt + (size_t)nc * nc, 0.0);
+    for (int k = 0; k <= p; ++k)
+        for (int l = 0; l <= k; ++l) {
+            const int ro = k * k + (l == 0 ? 0 : 2 * l - 1), io = l > 0 ? k * k + 2 * l : -1;
+            for (int n = 0; n <= p; ++n)
+                for (int mu = 0; mu <= n; ++mu) {
+                    double Pr, Pi, Qr = 0, Qi = 0;
+                    coef(k, l, n, mu, Pr, Pi);
+                    if (mu > 0) {
+                        coef(k, l, n, -mu, Qr, Qi);
+                        if (mu & 1) { Qr = -Qr; Qi = -Qi; }
+                    }
+                    const int ri = n * n + (mu == 0 ? 0 : 2 * mu - 1), ii = mu > 0 ? n * n + 2 * mu : -1;
+                    Tt[(size_t)ri * nc + ro] += Pr + Qr;
+                    if (ii >= 0) Tt[(size_t)ii * nc + ro] += -(Pi - Qi);
+                    if (io >= 0) Tt[(size_t)ri * nc + io] += Pi + Qi;
+                    if (io >= 0 && ii >= 0) Tt[(size_t)ii * nc + io] += Pr - Qr;
+                }
+        }
+}
+
+struct TabKey {
+    int dev, p, prec;
+    bool operator<(const TabKey &o) const {
+        return dev != o.dev ? dev < o.dev : (p != o.p ? p < o.p : prec < o.prec);
+    }
+};
+static std::mutex g_tab_mu;
+static std::map<TabKey, std::weak_ptr<Tables>> g_tab_cache;
+
+template <class T>
+static void upload(DArray<T> &d, const std::vector<double> &h) {
+    std::vector<T> v(h.begin(), h.end());
+    d.alloc(v.size());
+    BEM_CUDA(cudaMemcpy(d.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+static std::shared_ptr<Tables> make_tables(int p, int prec) {
+    auto t = std::make_shared<Tables>();
     const int W = 2 * p + 1, W2 = 4 * p + 1;
-    m.tab.p = p;
+    const int nc = (p + 1) * (p + 1);
+    t->p = p;
     // parent/child offsets: child centre minus parent centre over the parent size
-    std::vector<double> r8((size_t)8 * (p + 1) * W * 2), tmp;
+    std::vector<std::vector<double>> r8(8);
+    std::vector<double> rtab((size_t)8 * (p + 1) * W * 2);
     for (int o = 0; o < 8; ++o) {
         double d[3];
         for (int k = 0; k < 3; ++k) d[k] = ((o >> k) & 1) ? 0.25 : -0.25;
-        host_regular_full(d[0], d[1], d[2], p, tmp);
-        std::memcpy(&r8[(size_t)o * (p + 1) * W * 2], tmp.data(), tmp.size() * sizeof(double));
+        host_regular_full(d[0], d[1], d[2], p, r8[o]);
+        std::memcpy(&rtab[(size_t)o * (p + 1) * W * 2], r8[o].data(), r8[o].size() * sizeof(double));
     }
     // M2L offsets: target centre minus source centre over the cell size = -(dx,dy,dz)
     const size_t itot = (size_t)(2 * p + 1) * W2 * 2;
-    std::vector<double> it((size_t)NOFFSET * itot, 0.0);
+    std::vector<double> it((size_t)NOFFSET * itot, 0.0), tmp;
     for (int o = 0; o < NOFFSET; ++o) {
         int dx = o / 49 - 3, dy = (o / 7) % 7 - 3, dz = o % 7 - 3;
         if (std::abs(dx) <= 1 && std::abs(dy) <= 1 && std::abs(dz) <= 1) continue;
         host_irregular_full(-dx, -dy, -dz, 2 * p, tmp);
         std::memcpy(&it[(size_t)o * itot], tmp.data(), tmp.size() * sizeof(double));
     }
-    if (m.opt.precision == BEM_MIXED) {
-        std::vector<float> a(r8.begin(), r8.end()), b(it.begin(), it.end());
-        m.tab.Rm2m_f.alloc(a.size());
-        m.tab.If_f.alloc(b.size());
-        BEM_CUDA(cudaMemcpy(m.tab.Rm2m_f.p, a.data(), a.size() * sizeof(float), cudaMemcpyHostToDevice));
-        BEM_CUDA(cudaMemcpy(m.tab.If_f.p, b.data(), b.size() * sizeof(float), cudaMemcpyHostToDevice));
-    } else {
-        m.tab.Rm2m_d.alloc(r8.size());
-        m.tab.If_d.alloc(it.size());
-        BEM_CUDA(cudaMemcpy(m.tab.Rm2m_d.p, r8.data(), r8.size() * sizeof(double), cudaMemcpyHostToDevice));
-        BEM_CUDA(cudaMemcpy(m.tab.If_d.p, it.data(), it.size() * sizeof(double), cudaMemcpyHostToDevice));
+    // dense real operators
+    const size_t osz = (size_t)nc * nc;
+    std::vector<double> om2l((size_t)NOFFSET * osz, 0.0), om2m(8 * osz), ol2l(8 * osz);
+    for (int o = 0; o < NOFFSET; ++o) {
+        int dx = o / 49 - 3, dy = (o / 7) % 7 - 3, dz = o % 7 - 3;
+        if (std::abs(dx) <= 1 && std::abs(dy) <= 1 && std::abs(dz) <= 1) continue;
+        const double *I = &it[(size_t)o * itot];
+        // L_k^l = (-1)^k sum M_n^m I_{n+k}^{m+l}
+        real_operator(p, [&](int k, int l, int n, int m, double &re, double &im) {
+            const double sg = (k & 1) ? -1.0 : 1.0;
+            const size_t q = ((size_t)(n + k) * W2 + (m + l) + 2 * p) * 2;
+            re = sg * I[q];
+            im = sg * I[q + 1];
+        }, &om2l[(size_t)o * osz]);
     }
+    for (int o = 0; o < 8; ++o) {
+        const std::vector<double> &R = r8[o];
+        auto Rc = [&](int n, int m, double &re, double &im) {  // conj(R_n^m), 0 outside
+            if (n < 0 || m < -n || m > n) { re = im = 0; return; }
+            const size_t q = ((size_t)n * W + m + p) * 2;
+            re = R[q];
+            im = -R[q + 1];
+        };
+        // M2M: M'_N^Mo = sum_{j,mu} 2^-j conj(R_{N-j}^{Mo-mu}) M_j^mu
+        real_operator(p, [&](int N, int Mo, int j, int mu, double &re, double &im) {
+            if (j > N) { re = im = 0; return; }
+            Rc(N - j, Mo - mu, re, im);
+            const double s = std::ldexp(1.0, -j);
+            re *= s;
+            im *= s;
+        }, &om2m[(size_t)o * osz]);
+        // L2L: L'_k^l = 2^-(k+1) sum_{n,m} conj(R_{n-k}^{m-l}) L_n^m
+        real_operator(p, [&](int k, int l, int n, int m, double &re, double &im) {
+            if (n < k) { re = im = 0; return; }
+            Rc(n - k, m - l, re, im);
+            const double s = std::ldexp(1.0, -(k + 1));
+            re *= s;
+            im *= s;
+        }, &ol2l[(size_t)o * osz]);
+    }
+    if (prec == BEM_MIXED) {
+        upload(t->Rm2m_f, rtab);
+        upload(t->If_f, it);
+        upload(t->Om2l_f, om2l);
+        upload(t->Om2m_f, om2m);
+        upload(t->Ol2l_f, ol2l);
+    } else {
+        upload(t->Rm2m_d, rtab);
+        upload(t->If_d, it);
+        upload(t->Om2l_d, om2l);
+        upload(t->Om2m_d, om2m);
+        upload(t->Ol2l_d, ol2l);
+    }
+    return t;
+}
+
+void build_tables(Mesh &m) {
+    upload_constants(m.device);
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    TabKey key{m.device, m.opt.p, m.opt.precision};
+    auto it = g_tab_cache.find(key);
+    if (it != g_tab_cache.end()) {
+        if (auto sp = it->second.lock()) {
+            m.tab = sp;
+            return;
+        }
+    }
+    m.tab = make_tables(m.opt.p, m.opt.precision);
+    g_tab_cache[key] = m.tab;
+}
+
+// ------------------------------------------------- batched dense translations
+// out[pair_out[j]] += Op[op] . in[pair_in[j]] for the pairs of one chunk: a
+// (p+1)^2 x (p+1)^2 by (p+1)^2 x 64 product tiled 128 x 64 x BK through
+// shared memory, 8 x 4 outputs per thread, then scattered with coalesced
+// atomic adds (a warp adds 32 consecutive coefficients of one cell).
+constexpr int TR_BM = 128, TR_THREADS = 256;
+constexpr int TR_BN_M2L = 64;  // pairs per chunk for M2L (many pairs per offset class)
+constexpr int TR_BN_TREE = 16; // pairs per chunk for M2M / L2L (8 operators per level)
+template <class T> struct TrBK;
+template <> struct TrBK<float> { static constexpr int v = 32; };
+template <> struct TrBK<double> { static constexpr int v = 16; };
+
+template <class T, int BN>
+__global__ void __launch_bounds__(TR_THREADS)
+k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ chunks,
+            const int *__restrict__ p_out, const int *__restrict__ p_in, const T *__restrict__ in,
+            T *__restrict__ out) {
+    constexpr int BK = TrBK<T>::v;
+    constexpr int CPT = BN / 16;            // columns per thread
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *As = reinterpret_cast<T *>(smraw);   // [BK][BM]
+    T *Bs = As + BK * TR_BM;                // [BK][BN]
+    T *Cs = As;                             // [BN][BM+1] (epilogue)
+    __shared__ int s_in[BN], s_out[BN];
+    const int4 ch = chunks[blockIdx.x];
+    const T *Tt = ops + (size_t)ch.x * nc * nc;
+    const int rb = blockIdx.y * TR_BM;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    if (tid < BN) {
+        s_in[tid] = tid < ch.z ? p_in[ch.y + tid] : -1;
+        s_out[tid] = tid < ch.z ? p_out[ch.y + tid] : -1;
+    }
+    T acc[8][CPT];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) acc[r][c] = 0;
+    __syncthreads();
+    for (int k0 = 0; k0 < nc; k0 += BK) {
+        for (int e = tid; e < BK * TR_BM; e += TR_THREADS) {
+            const int k = e / TR_BM, r = e - k * TR_BM;
+            T v = 0;
+            if (k0 + k < nc && rb + r < nc) v = Tt[(size_t)(k0 + k) * nc + rb + r];
+            As[k * TR_BM + r] = v;
+        }
+        for (int e = tid; e < BK * BN; e += TR_THREADS) {
+            const int j = e / BK, k = e - j * BK;
+            const int src = s_in[j];
+            T v = 0;
+            if (src >= 0 && k0 + k < nc) v = in[(size_t)src * cs + k0 + k];
+            Bs[k * BN + j] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < BK; ++k) {
+            T a[8], b[CPT];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) a[r] = As[k * TR_BM + ty * 8 + r];
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) b[c] = Bs[k * BN + tx * CPT + c];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) Cs[(tx * CPT + c) * (TR_BM + 1) + ty * 8 + r] = acc[r][c];
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    const int rows = min(TR_BM, nc - rb);
+    for (int j = warp; j < ch.z; j += TR_THREADS / 32) {
+        T *o = out + (size_t)s_out[j] * cs + rb;
+        const T *cj = Cs + j * (TR_BM + 1);
+        for (int r = lane; r < rows; r += 32) atomicAdd(o + r, cj[r]);
+    }
+}
+
+template <class T, int BN>
+static size_t translate_smem() {
+    constexpr int BK = TrBK<T>::v;
+    const size_t a = (size_t)(BK * TR_BM + BK * BN) * sizeof(T);
+    const size_t c = (size_t)BN * (TR_BM + 1) * sizeof(T);
+    return std::max(a, c);
+}
+
+// Group the translations of a tree by operator and cut them into chunks.
+__global__ void k_m2l_pairs(const int *m2l_off, int first, int last, const int *m2l_src,
+                            const int *m2l_ofs, int *out, int *in, int *key) {
+    const int t = first + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= last) return;
+    for (int e = m2l_off[t]; e < m2l_off[t + 1]; ++e) {
+        out[e] = t;
+        in[e] = m2l_src[e];
+        key[e] = m2l_ofs[e];
+    }
+}
+
+// Launch order of the near-field kernel: leaves by decreasing work
+// (targets x sources of the adjacent leaves), so that the last wave of
+// CTAs holds the small ones.
+static void build_p2p_order(Mesh &m, Tree &t) {
+    cudaStream_t s = m.stream;
+    const int n = t.nleaf;
+    std::vector<int> tb(n + 1), qb(n + 1), cb(n + 1), no(n + 1), nb(t.nnbr > 0 ? t.nnbr : 1);
+    BEM_CUDA(cudaMemcpyAsync(tb.data(), t.cen_beg.p, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(qb.data(), t.qp_beg.p, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(cb.data(), t.chg_beg.p, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(no.data(), t.nbr_off.p, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (t.nnbr > 0)
+        BEM_CUDA(cudaMemcpyAsync(nb.data(), t.nbr.p, t.nnbr * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    std::vector<std::pair<int64_t, int>> w(n);
+    for (int l = 0; l < n; ++l) {
+        int64_t src = 0;
+        for (int e = no[l]; e < no[l + 1]; ++e) {
+            const int S = nb[e];
+            src += (qb[S + 1] - qb[S]) + (cb[S + 1] - cb[S]);
+        }
+        const int64_t tg = (tb[l + 1] - tb[l]) + (cb[l + 1] - cb[l]);
+        w[l] = {-(tg * src), l};
+    }
+    std::stable_sort(w.begin(), w.end());
+    std::vector<int> ord(n);
+    for (int l = 0; l < n; ++l) ord[l] = w[l].second;
+    t.p2p_order.alloc(n);
+    BEM_CUDA(cudaMemcpyAsync(t.p2p_order.p, ord.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+}
+
+void build_translation_groups(Mesh &m, Tree &t) {
+    cudaStream_t s = m.stream;
+    const int L = t.L;
+    build_p2p_order(m, t);
+    t.m2m_chunk0.assign(L + 2, 0);
+    t.m2m_nchunk.assign(L + 2, 0);
+    t.l2l_chunk0.assign(L + 2, 0);
+    t.l2l_nchunk.assign(L + 2, 0);
+    t.m2l_chunk0 = t.m2l_nchunk = 0;
+    if (L < 2) return;
+    // host copies of the cell structure (parents, coordinates)
+    std::vector<int4> ijk(t.ncell);
+    std::vector<int> parent(t.ncell);
+    BEM_CUDA(cudaMemcpyAsync(ijk.data(), t.ijk.p, t.ncell * sizeof(int4), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(parent.data(), t.parent.p, t.ncell * sizeof(int), cudaMemcpyDeviceToHost, s));
+    // M2L pairs sorted by offset class (device radix sort, stable)
+    const int64_t nm = t.nm2l;
+    std::vector<int> h_out, h_in;
+    std::vector<int4> chunks;
+    std::vector<int> cnt(NOFFSET, 0);
+    {
+        DArray<int> po, pi, key;
+        po.alloc(nm);
+        pi.alloc(nm);
+        key.alloc(nm);
+        const int first = t.lvl_off[2], last = t.ncell;
+        k_m2l_pairs<<<cdiv(last - first, 256), 256, 0, s>>>(t.m2l_off.p, first, last, t.m2l_src.p,
+                                                          t.m2l_ofs.p, po.p, pi.p, key.p);
+        BEM_CHECK_LAUNCH();
+        std::vector<int> hk(nm), ho(nm), hi(nm);
+        BEM_CUDA(cudaMemcpyAsync(hk.data(), key.p, nm * sizeof(int), cudaMemcpyDeviceToHost, s));
+        BEM_CUDA(cudaMemcpyAsync(ho.data(), po.p, nm * sizeof(int), cudaMemcpyDeviceToHost, s));
+        BEM_CUDA(cudaMemcpyAsync(hi.data(), pi.p, nm * sizeof(int), cudaMemcpyDeviceToHost, s));
+        BEM_CUDA(cudaStreamSynchronize(s));
+        for (int64_t e = 0; e < nm; ++e) cnt[hk[e]]++;
+        std::vector<int64_t> start(NOFFSET + 1, 0);
+        for (int o = 0; o < NOFFSET; ++o) start[o + 1] = start[o] + cnt[o];
+        h_out.resize(nm);
+        h_in.resize(nm);
+        std::vector<int64_t> fill(start.begin(), start.end() - 1);
+        for (int64_t e = 0; e < nm; ++e) {
+            const int64_t d = fill[hk[e]]++;
+            h_out[d] = ho[e];
+            h_in[d] = hi[e];
+        }
+        for (int o = 0; o < NOFFSET; ++o)
+            for (int64_t b = start[o]; b < start[o + 1]; b += TR_BN_M2L)
+                chunks.push_back(make_int4(o, (int)b, (int)std::min<int64_t>(TR_BN_M2L, start[o + 1] - b), 0));
+        t.m2l_nchunk = (int)chunks.size();
+    }
+    // M2M (out parent, in child) and L2L (out child, in parent) per child level
+    for (int c = 3; c <= L; ++c) {
+        std::vector<std::vector<int>> byoct(8);
+        for (int e = t.lvl_off[c]; e < t.lvl_off[c + 1]; ++e) {
+            const int4 q = ijk[e];
+            byoct[(q.x & 1) | ((q.y & 1) << 1) | ((q.z & 1) << 2)].push_back(e);
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+            const int c0 = (int)chunks.size();
+            for (int o = 0; o < 8; ++o) {
+                const int64_t b0 = (int64_t)h_out.size();
+                for (int e : byoct[o]) {
+                    if (pass == 0) { h_out.push_back(parent[e]); h_in.push_back(e); }
+                    else { h_out.push_back(e); h_in.push_back(parent[e]); }
+                }
+                const int64_t b1 = (int64_t)h_out.size();
+                for (int64_t b = b0; b < b1; b += TR_BN_TREE)
+                    chunks.push_back(make_int4(o, (int)b, (int)std::min<int64_t>(TR_BN_TREE, b1 - b), 0));
+            }
+            if (pass == 0) { t.m2m_chunk0[c] = c0; t.m2m_nchunk[c] = (int)chunks.size() - c0; }
+            else { t.l2l_chunk0[c] = c0; t.l2l_nchunk[c] = (int)chunks.size() - c0; }
+        }
+    }
+    t.g_out.alloc(h_out.size());
+    t.g_in.alloc(h_in.size());
+    t.g_chunk.alloc(chunks.size());
+    BEM_CUDA(cudaMemcpyAsync(t.g_out.p, h_out.data(), h_out.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(t.g_in.p, h_in.data(), h_in.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(t.g_chunk.p, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
 }
 
 // ---------------------------------------------------------------- driver
@@ -785,12 +1345,16 @@ struct PassBufs<float> {
     static float *L(Mesh &m) { return m.Lf.p; }
     static float *far(Mesh &m) { return m.far_f.p; }
     static float *near(Mesh &m) { return m.near_f.p; }
-    static const cpx<float> *R(Mesh &m) { return reinterpret_cast<const cpx<float> *>(m.tab.Rm2m_f.p); }
-    static const cpx<float> *I(Mesh &m) { return reinterpret_cast<const cpx<float> *>(m.tab.If_f.p); }
+    static const cpx<float> *R(Mesh &m) { return reinterpret_cast<const cpx<float> *>(m.tab->Rm2m_f.p); }
+    static const cpx<float> *I(Mesh &m) { return reinterpret_cast<const cpx<float> *>(m.tab->If_f.p); }
+    static const float *Om2l(Mesh &m) { return m.tab->Om2l_f.p; }
+    static const float *Om2m(Mesh &m) { return m.tab->Om2m_f.p; }
+    static const float *Ol2l(Mesh &m) { return m.tab->Ol2l_f.p; }
     static const float4 *cen(Mesh &m) { return m.cen32.p; }
     static const float4 *nrm(Mesh &m) { return m.nrm32.p; }
     static const float4 *qp(Mesh &m) { return m.qp32.p; }
     static const float4 *chg(Mesh &m) { return m.chg32.p; }
+    static float4 *str(Mesh &m) { return m.str32.p; }
 };
 template <>
 struct PassBufs<double> {
@@ -798,12 +1362,16 @@ struct PassBufs<double> {
     static double *L(Mesh &m) { return m.Ld.p; }
     static double *far(Mesh &m) { return m.far_d.p; }
     static double *near(Mesh &m) { return m.near_d.p; }
-    static const cpx<double> *R(Mesh &m) { return reinterpret_cast<const cpx<double> *>(m.tab.Rm2m_d.p); }
-    static const cpx<double> *I(Mesh &m) { return reinterpret_cast<const cpx<double> *>(m.tab.If_d.p); }
+    static const cpx<double> *R(Mesh &m) { return reinterpret_cast<const cpx<double> *>(m.tab->Rm2m_d.p); }
+    static const cpx<double> *I(Mesh &m) { return reinterpret_cast<const cpx<double> *>(m.tab->If_d.p); }
+    static const double *Om2l(Mesh &m) { return m.tab->Om2l_d.p; }
+    static const double *Om2m(Mesh &m) { return m.tab->Om2m_d.p; }
+    static const double *Ol2l(Mesh &m) { return m.tab->Ol2l_d.p; }
     static const double4 *cen(Mesh &m) { return m.cen64r.p; }
     static const double4 *nrm(Mesh &m) { return m.nrm64r.p; }
     static const double4 *qp(Mesh &m) { return m.qp64r.p; }
     static const double4 *chg(Mesh &m) { return m.chg64r.p; }
+    static double4 *str(Mesh &m) { return m.str64.p; }
 };
 
 static int p2m_threads(int p, size_t elt) {
@@ -842,8 +1410,27 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
     const typename V4T<T>::t *nrec = B::nrm(m);
     T *far_b = B::far(m), *near_b = B::near(m);
     ev_rec(m, timed, 0);
+    // strength records of this pass
+    typename V4T<T>::t *strec = B::str(m);
+    {
+        const int64_t ns = (sk == SRC_QUAD) ? m.nqp : m.nc;
+        if (sk == SRC_QUAD)
+            k_strength<T, SRC_QUAD><<<cdiv(ns, 256), 256, 0, s>>>(srec, m.qp_panel.p, dens, ns, strec);
+        else
+            k_strength<T, SRC_CHARGE><<<cdiv(ns, 256), 256, 0, s>>>(srec, nullptr, dens, ns, strec);
+        BEM_CHECK_LAUNCH();
+    }
     if (far) {
         T *M = B::M(m), *L = B::L(m);
+        const int cs = cell_stride(p);
+        const bool dense = m.opt.m2l_mode != BEM_M2L_DIRECT;
+        const int rblocks = cdiv(nc, TR_BM);
+        const size_t trsm = translate_smem<T, TR_BN_M2L>();
+        const size_t trsm_t = translate_smem<T, TR_BN_TREE>();
+        if (dense) {
+            set_smem<T>(k_translate<T, TR_BN_M2L>, trsm);
+            set_smem<T>(k_translate<T, TR_BN_TREE>, trsm_t);
+        }
         // P2M
         {
             const int th = p2m_threads(p, sizeof(T));
@@ -851,43 +1438,71 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             if (sk == SRC_QUAD) {
                 auto kern = k_p2m<T, SRC_QUAD>;
                 set_smem<T>(kern, sm);
-                kern<<<t.nleaf, th, sm, s>>>(tv, srec, m.qp_panel.p, dens, p, inv_h, M);
+                kern<<<t.nleaf, th, sm, s>>>(tv, strec, p, cs, inv_h, M);
             } else {
                 auto kern = k_p2m<T, SRC_CHARGE>;
                 set_smem<T>(kern, sm);
-                kern<<<t.nleaf, th, sm, s>>>(tv, srec, nullptr, dens, p, inv_h, M);
+                kern<<<t.nleaf, th, sm, s>>>(tv, strec, p, cs, inv_h, M);
             }
             BEM_CHECK_LAUNCH();
         }
         ev_rec(m, timed, 1);
         // M2M: parents at levels L-1 .. 2
-        {
+        if (dense) {
+            if (t.L >= 3)
+                BEM_CUDA(cudaMemsetAsync(M + (size_t)t.lvl_off[2] * cs, 0,
+                                         (size_t)(t.lvl_off[t.L] - t.lvl_off[2]) * cs * sizeof(T), s));
+            for (int c = t.L; c >= 3; --c) {
+                if (t.m2m_nchunk[c] == 0) continue;
+                dim3 g(t.m2m_nchunk[c], rblocks);
+                k_translate<T, TR_BN_TREE><<<g, TR_THREADS, trsm_t, s>>>(B::Om2m(m), nc, cs, t.g_chunk.p + t.m2m_chunk0[c],
+                                                            t.g_out.p, t.g_in.p, M, M);
+                BEM_CHECK_LAUNCH();
+            }
+        } else {
             const size_t sm = 2 * (size_t)(p + 1) * W * sizeof(cpx<T>);
             set_smem<T>(k_m2m<T>, sm);
             for (int l = t.L - 1; l >= 2; --l) {
                 const int cnt = t.lvl_off[l + 1] - t.lvl_off[l];
-                if (cnt > 0) k_m2m<T><<<cnt, 160, sm, s>>>(tv, t.lvl_off[l], B::R(m), p, M);
+                if (cnt > 0) k_m2m<T><<<cnt, 160, sm, s>>>(tv, t.lvl_off[l], B::R(m), p, cs, M);
                 BEM_CHECK_LAUNCH();
             }
         }
         ev_rec(m, timed, 2);
         // M2L: every cell at levels 2..L
-        {
+        if (dense) {
+            BEM_CUDA(cudaMemsetAsync(L + (size_t)t.lvl_off[2] * cs, 0,
+                                     (size_t)(t.ncell - t.lvl_off[2]) * cs * sizeof(T), s));
+            if (t.m2l_nchunk > 0) {
+                dim3 g(t.m2l_nchunk, rblocks);
+                k_translate<T, TR_BN_M2L><<<g, TR_THREADS, trsm, s>>>(B::Om2l(m), nc, cs, t.g_chunk.p + t.m2l_chunk0,
+                                                            t.g_out.p, t.g_in.p, M, L);
+                BEM_CHECK_LAUNCH();
+            }
+        } else {
             const size_t sm = ((size_t)(p + 1) * W + (size_t)(2 * p + 1) * W2) * sizeof(cpx<T>);
             set_smem<T>(k_m2l<T>, sm);
             const int first = t.lvl_off[2];
             const int cnt = t.ncell - first;
-            if (cnt > 0) k_m2l<T><<<cnt, 160, sm, s>>>(tv, first, B::I(m), p, M, L);
+            if (cnt > 0) k_m2l<T><<<cnt, 160, sm, s>>>(tv, first, B::I(m), p, cs, M, L);
             BEM_CHECK_LAUNCH();
         }
         ev_rec(m, timed, 3);
         // L2L: children at levels 3..L
-        {
+        if (dense) {
+            for (int c = 3; c <= t.L; ++c) {
+                if (t.l2l_nchunk[c] == 0) continue;
+                dim3 g(t.l2l_nchunk[c], rblocks);
+                k_translate<T, TR_BN_TREE><<<g, TR_THREADS, trsm_t, s>>>(B::Ol2l(m), nc, cs, t.g_chunk.p + t.l2l_chunk0[c],
+                                                            t.g_out.p, t.g_in.p, L, L);
+                BEM_CHECK_LAUNCH();
+            }
+        } else {
             const size_t sm = 2 * (size_t)(p + 1) * W * sizeof(cpx<T>);
             set_smem<T>(k_l2l<T>, sm);
             for (int l = 3; l <= t.L; ++l) {
                 const int cnt = t.lvl_off[l + 1] - t.lvl_off[l];
-                if (cnt > 0) k_l2l<T><<<cnt, 160, sm, s>>>(tv, t.lvl_off[l], B::R(m), p, L);
+                if (cnt > 0) k_l2l<T><<<cnt, 160, sm, s>>>(tv, t.lvl_off[l], B::R(m), p, cs, L);
                 BEM_CHECK_LAUNCH();
             }
         }
@@ -898,11 +1513,11 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             if (tk == TGT_CEN_DN) {
                 auto kern = k_l2p<T, TGT_CEN_DN>;
                 set_smem<T>(kern, sm);
-                kern<<<t.nleaf, 128, sm, s>>>(tv, trec, nrec, p, inv_h, L, far_b);
+                kern<<<t.nleaf, 128, sm, s>>>(tv, trec, nrec, p, cs, inv_h, L, far_b);
             } else {
                 auto kern = k_l2p<T, TGT_CHG_PHI>;
                 set_smem<T>(kern, sm);
-                kern<<<t.nleaf, 128, sm, s>>>(tv, trec, nrec, p, inv_h, L, far_b);
+                kern<<<t.nleaf, 128, sm, s>>>(tv, trec, nrec, p, cs, inv_h, L, far_b);
             }
             BEM_CHECK_LAUNCH();
         }
@@ -913,13 +1528,13 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
     if (near) {
         const T hh = (T)h;
         if (sk == SRC_QUAD && tk == TGT_CEN_DN)
-            k_p2p<T, SRC_QUAD, TGT_CEN_DN><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, trec, nrec, srec, m.qp_panel.p, dens, hh, near_b);
+            k_p2p<T, SRC_QUAD, TGT_CEN_DN><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, trec, nrec, strec, hh, near_b);
         else if (sk == SRC_CHARGE && tk == TGT_CEN_DN)
-            k_p2p<T, SRC_CHARGE, TGT_CEN_DN><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, trec, nrec, srec, nullptr, dens, hh, near_b);
+            k_p2p<T, SRC_CHARGE, TGT_CEN_DN><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, trec, nrec, strec, hh, near_b);
         else if (sk == SRC_QUAD && tk == TGT_CHG_PHI)
-            k_p2p<T, SRC_QUAD, TGT_CHG_PHI><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, trec, nrec, srec, m.qp_panel.p, dens, hh, near_b);
+            k_p2p<T, SRC_QUAD, TGT_CHG_PHI><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, trec, nrec, strec, hh, near_b);
         else
-            k_p2p<T, SRC_CHARGE, TGT_CHG_PHI><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, trec, nrec, srec, nullptr, dens, hh, near_b);
+            k_p2p<T, SRC_CHARGE, TGT_CHG_PHI><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, trec, nrec, strec, hh, near_b);
         BEM_CHECK_LAUNCH();
     }
     ev_rec(m, timed, 6);
@@ -929,6 +1544,8 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
 }
 
 
+void build_qp_of_panel(Mesh &m);
+
 template <class T>
 static void near_table_impl(Mesh &m) {
     using B = PassBufs<T>;
@@ -936,16 +1553,14 @@ static void near_table_impl(Mesh &m) {
     const Tree &t = m.tp;
     const int64_t np = m.np;
     const int nq = (int)m.nq;
-    DArray<int> leaf_of, slot, qop, cnt;
+    DArray<int> leaf_of, slot, cnt;
+    DArray<int> &qop = m.qp_of_panel;
     leaf_of.alloc(np);
     slot.alloc(np);
-    qop.alloc(m.nqp);
     cnt.alloc(np + 1);
     k_leaf_of<<<t.nleaf, 128, 0, s>>>(t.cen_beg.p, t.nleaf, leaf_of.p);
     BEM_CHECK_LAUNCH();
-    BEM_CUDA(cudaMemsetAsync(slot.p, 0, np * sizeof(int), s));
-    k_qp_of_panel<<<cdiv(m.nqp, 256), 256, 0, s>>>(m.qp_panel.p, nullptr, m.nqp, nq, slot.p, qop.p);
-    BEM_CHECK_LAUNCH();
+    build_qp_of_panel(m);
     BEM_CUDA(cudaMemsetAsync(cnt.p, 0, (np + 1) * sizeof(int), s));
     const int shift = 3 * (MORTON_BITS - t.L);
     const double h = m.side / (double)(1 << t.L);
@@ -970,9 +1585,132 @@ static void near_table_impl(Mesh &m) {
     BEM_CUDA(cudaStreamSynchronize(s));
 }
 
+void build_qp_of_panel(Mesh &m) {
+    if (m.qp_of_panel.n >= (size_t)m.nqp && m.nqp > 0) return;
+    // the points of each panel in the order of the sorted quadrature array
+    std::vector<int> qpanel(m.nqp), fill(m.np, 0), qop(m.nqp);
+    BEM_CUDA(cudaMemcpyAsync(qpanel.data(), m.qp_panel.p, m.nqp * sizeof(int), cudaMemcpyDeviceToHost, m.stream));
+    BEM_CUDA(cudaStreamSynchronize(m.stream));
+    for (int64_t k = 0; k < m.nqp; ++k) {
+        const int j = qpanel[k];
+        qop[(int64_t)j * m.nq + fill[j]++] = (int)k;
+    }
+    m.qp_of_panel.alloc(m.nqp);
+    BEM_CUDA(cudaMemcpyAsync(m.qp_of_panel.p, qop.data(), m.nqp * sizeof(int), cudaMemcpyHostToDevice, m.stream));
+    BEM_CUDA(cudaStreamSynchronize(m.stream));
+}
+
+// CSR transpose of the near-singular table (for K'^T).
+static void transpose_near_table(Mesh &m) {
+    const int64_t np = m.np, nnz = m.nt_nnz;
+    std::vector<int> off(np + 1), col(nnz > 0 ? nnz : 1), toff(np + 1, 0), tcol(nnz > 0 ? nnz : 1);
+    std::vector<double> val(nnz > 0 ? nnz : 1), tval(nnz > 0 ? nnz : 1);
+    BEM_CUDA(cudaMemcpyAsync(off.data(), m.nt_off.p, (np + 1) * sizeof(int), cudaMemcpyDeviceToHost, m.stream));
+    if (nnz > 0) {
+        BEM_CUDA(cudaMemcpyAsync(col.data(), m.nt_col.p, nnz * sizeof(int), cudaMemcpyDeviceToHost, m.stream));
+        BEM_CUDA(cudaMemcpyAsync(val.data(), m.nt_val.p, nnz * sizeof(double), cudaMemcpyDeviceToHost, m.stream));
+    }
+    BEM_CUDA(cudaStreamSynchronize(m.stream));
+    for (int64_t e = 0; e < nnz; ++e) toff[col[e] + 1]++;
+    for (int64_t i = 0; i < np; ++i) toff[i + 1] += toff[i];
+    std::vector<int> fill(toff.begin(), toff.end() - 1);
+    for (int64_t i = 0; i < np; ++i)
+        for (int e = off[i]; e < off[i + 1]; ++e) {
+            const int d = fill[col[e]]++;
+            tcol[d] = (int)i;
+            tval[d] = val[e];
+        }
+    m.ntT_off.alloc(np + 1);
+    m.ntT_col.alloc(nnz);
+    m.ntT_val.alloc(nnz);
+    BEM_CUDA(cudaMemcpyAsync(m.ntT_off.p, toff.data(), (np + 1) * sizeof(int), cudaMemcpyHostToDevice, m.stream));
+    if (nnz > 0) {
+        BEM_CUDA(cudaMemcpyAsync(m.ntT_col.p, tcol.data(), nnz * sizeof(int), cudaMemcpyHostToDevice, m.stream));
+        BEM_CUDA(cudaMemcpyAsync(m.ntT_val.p, tval.data(), nnz * sizeof(double), cudaMemcpyHostToDevice, m.stream));
+    }
+    BEM_CUDA(cudaStreamSynchronize(m.stream));
+}
+
 void build_near_table(Mesh &m) {
     if (m.opt.precision == BEM_MIXED) near_table_impl<float>(m);
     else near_table_impl<double>(m);
+    transpose_near_table(m);
+}
+
+
+template <class T>
+static void run_pass_t(Mesh &m, const double *lam, double *out) {
+    using B = PassBufs<T>;
+    cudaStream_t s = m.stream;
+    const Tree &t = m.tp;
+    const TreeView tv = view(t);
+    const int p = m.opt.p;
+    const int nc = (p + 1) * (p + 1);
+    const int cs = cell_stride(p);
+    const double h = m.side / (double)(1 << t.L);
+    const T inv_h = (T)(1.0 / h);
+    const bool far = !(m.opt.flags & BEM_FLAG_NO_FAR) && t.L >= 2;
+    const bool near = !(m.opt.flags & BEM_FLAG_NO_NEAR);
+    T *far_b = B::far(m), *near_b = B::near(m);
+    build_qp_of_panel(m);
+    if (far) {
+        T *M = B::M(m), *L = B::L(m);
+        const int rblocks = cdiv(nc, TR_BM);
+        const size_t trsm = translate_smem<T, TR_BN_M2L>();
+        const size_t trsm_t = translate_smem<T, TR_BN_TREE>();
+        set_smem<T>(k_translate<T, TR_BN_M2L>, trsm);
+        set_smem<T>(k_translate<T, TR_BN_TREE>, trsm_t);
+        {
+            const int th = std::max(32, p2m_threads(p, sizeof(T)));
+            const size_t sm = (size_t)th * nc * sizeof(T);
+            set_smem<T>(k_p2m_dipole<T>, sm);
+            k_p2m_dipole<T><<<t.nleaf, th, sm, s>>>(tv, B::cen(m), B::nrm(m), lam, p, cs, inv_h, M);
+            BEM_CHECK_LAUNCH();
+        }
+        if (t.L >= 3)
+            BEM_CUDA(cudaMemsetAsync(M + (size_t)t.lvl_off[2] * cs, 0,
+                                     (size_t)(t.lvl_off[t.L] - t.lvl_off[2]) * cs * sizeof(T), s));
+        for (int c = t.L; c >= 3; --c) {
+            if (t.m2m_nchunk[c] == 0) continue;
+            dim3 g(t.m2m_nchunk[c], rblocks);
+            k_translate<T, TR_BN_TREE><<<g, TR_THREADS, trsm_t, s>>>(B::Om2m(m), nc, cs, t.g_chunk.p + t.m2m_chunk0[c],
+                                                                      t.g_out.p, t.g_in.p, M, M);
+            BEM_CHECK_LAUNCH();
+        }
+        BEM_CUDA(cudaMemsetAsync(L + (size_t)t.lvl_off[2] * cs, 0,
+                                 (size_t)(t.ncell - t.lvl_off[2]) * cs * sizeof(T), s));
+        if (t.m2l_nchunk > 0) {
+            dim3 g(t.m2l_nchunk, rblocks);
+            k_translate<T, TR_BN_M2L><<<g, TR_THREADS, trsm, s>>>(B::Om2l(m), nc, cs, t.g_chunk.p + t.m2l_chunk0,
+                                                                   t.g_out.p, t.g_in.p, M, L);
+            BEM_CHECK_LAUNCH();
+        }
+        for (int c = 3; c <= t.L; ++c) {
+            if (t.l2l_nchunk[c] == 0) continue;
+            dim3 g(t.l2l_nchunk[c], rblocks);
+            k_translate<T, TR_BN_TREE><<<g, TR_THREADS, trsm_t, s>>>(B::Ol2l(m), nc, cs, t.g_chunk.p + t.l2l_chunk0[c],
+                                                                      t.g_out.p, t.g_in.p, L, L);
+            BEM_CHECK_LAUNCH();
+        }
+        const size_t sm = (size_t)(p + 1) * (2 * p + 1) * sizeof(cpx<T>);
+        auto kern = k_l2p<T, TGT_QUAD_PHI>;
+        set_smem<T>(kern, sm);
+        kern<<<t.nleaf, 128, sm, s>>>(tv, B::qp(m), B::nrm(m), p, cs, inv_h, L, far_b);
+        BEM_CHECK_LAUNCH();
+    }
+    if (near) {
+        BEM_CUDA(cudaMemsetAsync(near_b, 0, m.nqp * sizeof(T), s));
+        k_p2p_t<T><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, B::cen(m), B::nrm(m), lam, B::qp(m), (T)h, near_b);
+        BEM_CHECK_LAUNCH();
+    }
+    k_panel_reduce<T><<<cdiv(m.np, 256), 256, 0, s>>>(far ? far_b : nullptr, near ? near_b : nullptr,
+                                                      m.qp_of_panel.p, m.qw64.p, (int)m.nq, m.np, out);
+    BEM_CHECK_LAUNCH();
+}
+
+void fmm_pass_t(Mesh &m, const double *lam, double *out) {
+    if (m.opt.precision == BEM_MIXED) run_pass_t<float>(m, lam, out);
+    else run_pass_t<double>(m, lam, out);
 }
 
 void fmm_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const double *dens, double *out,

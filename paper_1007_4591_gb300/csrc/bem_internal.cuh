@@ -17,6 +17,7 @@
 #include <stdint.h>
 #include <stdexcept>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "../../include/bem.h"
@@ -95,6 +96,16 @@ struct Tree {
     DArray<int> m2l_off, m2l_src, m2l_ofs; // per cell CSR: source cell, offset class
     int64_t nnbr = 0, nm2l = 0;
     int64_t p2p_pairs_cq = 0;     // (centroid target, quad source) pairs
+    // translations grouped by operator for the batched dense form:
+    // M2L pairs (out = target cell, in = source cell) sorted by offset class,
+    // M2M pairs (out = parent, in = child) and L2L pairs (out = child,
+    // in = parent) per child level, sorted by the child's octant.  A chunk is
+    // (operator, first pair, pair count <= 64, 0).
+    DArray<int> g_out, g_in;      // all grouped pairs: M2L, then M2M and L2L per level
+    DArray<int4> g_chunk;
+    DArray<int> p2p_order;        // leaves by decreasing near-field work (launch order)
+    int m2l_chunk0 = 0, m2l_nchunk = 0;
+    std::vector<int> m2m_chunk0, m2m_nchunk, l2l_chunk0, l2l_nchunk; // indexed by child level
     size_t bytes() const;
 };
 
@@ -106,21 +117,31 @@ struct TreeView {
     const int *cen_beg, *qp_beg, *chg_beg;
     const int *nbr_off, *nbr;
     const int *m2l_off, *m2l_src, *m2l_ofs;
+    const int *p2p_order;
 };
 
 TreeView view(const Tree &t);
 
 // Source and target kinds of one fast multipole pass.
-enum SrcKind { SRC_QUAD = 0, SRC_CHARGE = 1 };
-enum TgtKind { TGT_CEN_DN = 0, TGT_CHG_PHI = 1 };
+enum SrcKind { SRC_QUAD = 0, SRC_CHARGE = 1, SRC_DIPOLE = 2 };
+enum TgtKind { TGT_CEN_DN = 0, TGT_CHG_PHI = 1, TGT_QUAD_PHI = 2 };
 
 struct Mesh;
 
-// Expansion/translation tables of one expansion order and precision.
+// Expansion/translation tables of one expansion order and precision, shared
+// by every mesh of the device (built once per (device, p, precision)).
+//   Rm2m: solid harmonics R_k^l of the 8 child offsets, full m range;
+//   If:   irregular harmonics I_n^m (n <= 2p) of the 343 offset classes;
+//   Om2l, Om2m, Ol2l: the translations as real (p+1)^2 x (p+1)^2 matrices
+//         in the compact real layout, stored column-major ([in][out]).
 struct Tables {
     int p = 0;
-    DArray<float> Rm2m_f, If_f;   // FP32 tables
-    DArray<double> Rm2m_d, If_d;  // FP64 tables
+    DArray<float> Rm2m_f, If_f, Om2l_f, Om2m_f, Ol2l_f;
+    DArray<double> Rm2m_d, If_d, Om2l_d, Om2m_d, Ol2l_d;
+    size_t bytes() const {
+        return Rm2m_f.bytes() + If_f.bytes() + Om2l_f.bytes() + Om2m_f.bytes() + Ol2l_f.bytes() +
+               Rm2m_d.bytes() + If_d.bytes() + Om2l_d.bytes() + Om2m_d.bytes() + Ol2l_d.bytes();
+    }
 };
 
 struct Timers {
@@ -166,12 +187,13 @@ struct Mesh {
     Tree tp;   // panels (centroids + quadrature points): K' and K'^T
     Tree tc;   // panels + charges: B, C and the adjoint charge terms
 
-    // near-singular FP64 table (CSR over sorted targets)
-    DArray<int> nt_off, nt_col;
-    DArray<double> nt_val;
+    // near-singular FP64 table (CSR over sorted targets) and its transpose
+    DArray<int> nt_off, nt_col, ntT_off, ntT_col;
+    DArray<double> nt_val, ntT_val;
     int64_t nt_nnz = 0;
+    DArray<int> qp_of_panel;           // [np][nq] sorted quadrature points of each sorted panel
 
-    Tables tab;
+    std::shared_ptr<Tables> tab;
 
     // expansion buffers (sized for the larger tree)
     DArray<float> Mf, Lf;
@@ -183,6 +205,8 @@ struct Mesh {
     DArray<double> far_d, near_d;      // (fp64 mode)
     DArray<double> io_a, io_b;         // staging for host or unsorted arguments
     DArray<double> red;                // reduction scratch
+    DArray<float4> str32;              // per-pass source strength records (mixed)
+    DArray<double4> str64;             // (fp64 mode)
     DArray<float> dpart_f;             // direct-sum partials (mixed)
     DArray<double> dpart_d;            // direct-sum partials (fp64)
     double *h_pinned = nullptr;        // small pinned host buffer
@@ -199,6 +223,8 @@ struct Mesh {
 
 // --------------------------------------------------------------- helpers
 inline int ncoef(int p) { return (p + 1) * (p + 1); }
+// per-cell stride of the expansion arrays: (p+1)^2 rounded up to 4 values
+inline int cell_stride(int p) { return ((p + 1) * (p + 1) + 3) & ~3; }
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // geometry + trees (bem_tree.cu)
@@ -206,6 +232,7 @@ void build_geometry_and_trees(Mesh &m, const double *d_panels, const double *d_c
 void rebuild_charge_tree(Mesh &m, const double *d_charges);
 void build_near_table(Mesh &m);
 void build_tables(Mesh &m);
+void build_translation_groups(Mesh &m, Tree &t);
 void compute_bbox(const double *d, int64_t n, int stride, double *lo, double *hi, cudaStream_t s);
 
 // fast multipole passes (bem_fmm.cu).  `dens` is indexed in sorted panel
@@ -216,6 +243,10 @@ void compute_bbox(const double *d, int64_t n, int stride, double *lo, double *hi
 //   TGT_CHG_PHI: s / (4 pi |x_k - y|)
 void fmm_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const double *dens, double *out,
               bool timed);
+// Transposed K' pass: out[j] = (K'^T lam)_j without the near-singular table
+// (dipoles lam_i n_i at the collocation points, potential at the quadrature
+// points, weighted sum over each panel's points).
+void fmm_pass_t(Mesh &m, const double *lam, double *out);
 
 // Products between the charges and the surface (B q, C sigma): the fast
 // multipole pass on the charge tree, or the direct sum over all pairs,
@@ -230,6 +261,6 @@ void matvec_t_sorted(Mesh &m, const double *xs, double *ys);
 void exclusive_scan_int(const int *in, int *out, int n, cudaStream_t s);
 void gather_f64(const double *src, const int *perm, double *dst, int64_t n, cudaStream_t s);
 void scatter_f64(const double *src, const int *perm, double *dst, int64_t n, cudaStream_t s);
-void gather_rows3(const double *src, const int *perm, double *dst, int64_t n, cudaStream_t s);
+void scatter_rows3(const double *src, const int *perm, double *dst, int64_t n, cudaStream_t s);
 
 }  // namespace bem

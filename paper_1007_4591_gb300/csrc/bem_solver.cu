@@ -54,7 +54,7 @@ void scatter_f64(const double *src, const int *perm, double *dst, int64_t n, cud
     k_scatter<<<cdiv(n, 256), 256, 0, s>>>(src, perm, dst, n);
     BEM_CHECK_LAUNCH();
 }
-void gather_rows3(const double *src, const int *perm, double *dst, int64_t n, cudaStream_t s) {
+void scatter_rows3(const double *src, const int *perm, double *dst, int64_t n, cudaStream_t s) {
     k_scatter3<<<cdiv(n, 256), 256, 0, s>>>(src, perm, dst, n);
     BEM_CHECK_LAUNCH();
 }

@@ -642,7 +642,8 @@ static void build_tree(Mesh &m, Tree &t, SetKeys cen, SetKeys qp, SetKeys chg) {
 }
 
 size_t Tree::bytes() const {
-    return key.bytes() + ijk.bytes() + parent.bytes() + child_beg.bytes() + child_end.bytes() +
+    return g_out.bytes() + g_in.bytes() + g_chunk.bytes() + p2p_order.bytes() +
+           key.bytes() + ijk.bytes() + parent.bytes() + child_beg.bytes() + child_end.bytes() +
            cen_beg.bytes() + qp_beg.bytes() + chg_beg.bytes() + nbr_off.bytes() + nbr.bytes() +
            m2l_off.bytes() + m2l_src.bytes() + m2l_ofs.bytes();
 }
@@ -665,6 +666,7 @@ TreeView view(const Tree &t) {
     v.m2l_off = t.m2l_off.p;
     v.m2l_src = t.m2l_src.p;
     v.m2l_ofs = t.m2l_ofs.p;
+    v.p2p_order = t.p2p_order.p;
     return v;
 }
 

@@ -52,14 +52,31 @@ def test_near_field_only_matches_dense(pkg, born3, precision, tol):
     assert rel((y - x) / P.ehat, kx_ref) < 50 * tol
 
 
-@pytest.mark.parametrize("depth,p", [(2, 10), (3, 10), (3, 12), (4, 12)])
-def test_fmm_matvec_matches_dense(pkg, small4, depth, p):
+@pytest.mark.parametrize("depth,p", [(2, 10), (3, 10), (3, 12), (4, 12), (4, 16)])
+@pytest.mark.parametrize("m2l_mode", [1, 2])
+def test_fmm_matvec_matches_dense(pkg, small4, depth, p, m2l_mode):
     m, P = small4
     for x in (_x(m.n_p, 1), P.bq()):
         ref = P.A(x)
-        with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=depth, p=p) as g:
+        with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=depth, p=p,
+                      m2l_mode=m2l_mode) as g:
             y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
-        assert rel(y, ref) < 1e-5, (depth, p, rel(y, ref))
+        assert rel(y, ref) < 1e-5, (depth, p, m2l_mode, rel(y, ref))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_translation_modes_agree(pkg, small4, precision):
+    """The grouped dense operators and the per-target complex sums are the same
+    linear maps: results agree to the working precision."""
+    m, P = small4
+    x = P.bq()
+    ys = []
+    for mode in (1, 2):
+        with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=4, p=10,
+                      m2l_mode=mode, precision=precision) as g:
+            ys.append(g.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
+    kx = (ys[1] - x)
+    assert rel(ys[0] - x, kx) < (2e-6 if precision == 0 else 1e-12)
 
 
 @pytest.mark.parametrize("depth", [2, 3])
@@ -141,7 +158,8 @@ def test_host_and_device_arguments_agree(pkg, small4):
         xd = torch.from_numpy(x).cuda()
         yd = torch.empty_like(xd)
         pkg.bem_matvec(h, xd, yd)
-        assert np.array_equal(y_host, yd.cpu().numpy())
+        # atomically accumulated translations: equal up to summation order
+        assert rel(y_host, yd.cpu().numpy()) < 1e-7
     finally:
         pkg.bem_mesh_destroy(h)
 
