@@ -121,6 +121,21 @@ def _max_over_ranks(v, ws):
     return float(t.item())
 
 
+def _traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    capture, or None when the kernel's source changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, rec["source_file"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
+                return None
+        return rec["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def workload():
     import synth
     return synth.globular(6)
@@ -186,7 +201,7 @@ def run_ours(args):
     mol = workload()
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    opts = dict(p=args.p, leaf_size=args.leaf, precision=0)
+    opts = dict(p=args.p, leaf_size=args.leaf, precision=0, m2l_mode=args.m2l_mode)
     t0 = time.perf_counter()
     mesh = pkg.Mesh(mol.panels, mol.charges, mol.eps_in, mol.eps_out, **opts)
     tree_s = time.perf_counter() - t0
@@ -235,7 +250,7 @@ def run_ours(args):
     achieved = p2p_flops / (ph["p2p"] * 1e-3) / 1e12 if ph["p2p"] > 0 else 0.0
     roofline = {"kernel": "k_p2p (near-field panel quadrature)", "bound": "alu",
                 "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                "frac": round(achieved / fp32_peak, 4), "traffic": _traffic(),
                 "peak_source": f"FP32: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                f"{f_mhz:.0f} MHz (sm_max_mhz from MEASURED_PEAKS.json, {src})",
                 "algorithmic": f"20 flop x {info['p2p_pairs']} (collocation point, source point) pairs"}
@@ -297,7 +312,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--p", type=int, default=10)
-    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--leaf", type=int, default=128)
+    ap.add_argument("--m2l-mode", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")

@@ -85,14 +85,16 @@ typedef struct bem_options {
     int charge_mode;   /* products with B, B^T, C, C^T (charges <-> surface):
                           0 = auto (direct sum when n_c * n_p * quad_points <= 4e10,
                               fast multipole otherwise), 1 = fast multipole, 2 = direct */
-    int m2l_mode;      /* translations (M2M, M2L, L2L): 0 = auto, 1 = dense real operators
-                          grouped by offset class (batched GEMM), 2 = per-target complex
-                          sums (reference form) */
+    int m2l_mode;      /* translations (M2M, M2L, L2L): 0 = auto (3 when available, else 1),
+                          1 = dense real operators grouped by offset class (batched SIMT
+                          GEMM), 2 = per-target complex sums (reference form), 3 = as 1
+                          with M2L on the tensor cores (tcgen05, 3xTF32; BEM_MIXED, p <= 10) */
 } bem_options;
 
 #define BEM_M2L_AUTO 0
 #define BEM_M2L_DENSE 1
 #define BEM_M2L_DIRECT 2
+#define BEM_M2L_TC 3
 
 #define BEM_CHARGE_AUTO 0
 #define BEM_CHARGE_FMM 1

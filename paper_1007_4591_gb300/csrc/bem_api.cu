@@ -61,7 +61,18 @@ static void finish_out(Mesh &m, const OutArg &o) {
         BEM_CUDA(cudaMemcpyAsync(o.user, o.dev, o.n * sizeof(double), cudaMemcpyDeviceToHost, m.stream));
 }
 
-static void sync(Mesh &m) { BEM_CUDA(cudaStreamSynchronize(m.stream)); }
+// Synchronise the mesh's stream and report a bounded device wait that ran out.
+static void sync(Mesh &m) {
+    BEM_CUDA(cudaStreamSynchronize(m.stream));
+    if (m.dev_err.p) {
+        int e = 0;
+        BEM_CUDA(cudaMemcpy(&e, m.dev_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            BEM_CUDA(cudaMemset(m.dev_err.p, 0, sizeof(int)));
+            throw Error(BEM_ETIMEOUT, "a bounded device wait ran out (tensor-core M2L)");
+        }
+    }
+}
 
 template <class F>
 static int guarded(F &&f) {
@@ -93,6 +104,7 @@ size_t Mesh::bytes() const {
     b += str32.bytes() + str64.bytes() + dpart_f.bytes() + dpart_d.bytes();
     b += xs.bytes() + ys.bytes() + zs.bytes() + far_f.bytes() + near_f.bytes() + far_d.bytes() +
          near_d.bytes() + io_a.bytes() + io_b.bytes() + red.bytes();
+    b += dev_err.bytes();
     b += V.bytes() + H.bytes() + gv.bytes() + cs.bytes() + sn.bytes() + yv.bytes() + hv.bytes() +
          part.bytes() + sigma_s.bytes();
     return b;
@@ -122,6 +134,10 @@ static void alloc_work(Mesh &m) {
     m.ys.alloc(nv);
     m.zs.alloc(nv * 3);
     m.red.alloc(16);
+    if (!m.dev_err.p) {
+        m.dev_err.alloc(1);
+        BEM_CUDA(cudaMemsetAsync(m.dev_err.p, 0, sizeof(int), m.stream));
+    }
     m.part.alloc((size_t)(std::max(1, m.opt.gmres_restart) + 2) * 1024);
 }
 
@@ -136,7 +152,7 @@ static void validate_options(const bem_options &o) {
     if (o.max_iter < 1) throw Error(BEM_EINVAL, "max_iter must be positive");
     if (!(o.tol > 0.0)) throw Error(BEM_EINVAL, "tol must be positive");
     if (o.charge_mode < 0 || o.charge_mode > 2) throw Error(BEM_EINVAL, "charge_mode must be 0, 1 or 2");
-    if (o.m2l_mode < 0 || o.m2l_mode > 2) throw Error(BEM_EINVAL, "m2l_mode must be 0, 1 or 2");
+    if (o.m2l_mode < 0 || o.m2l_mode > 3) throw Error(BEM_EINVAL, "m2l_mode must be 0, 1, 2 or 3");
 }
 
 }  // namespace bem

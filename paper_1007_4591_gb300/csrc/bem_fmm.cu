@@ -26,6 +26,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "bem_internal.cuh"
 
@@ -1090,6 +1091,14 @@ static std::shared_ptr<Tables> make_tables(int p, int prec) {
             im *= s;
         }, &ol2l[(size_t)o * osz]);
     }
+    if (prec == BEM_MIXED && nc <= 128) {
+        std::vector<float> hi, lo;
+        build_tc_tables(p, om2l, NOFFSET, hi, lo);
+        t->Tc_hi.alloc(hi.size());
+        t->Tc_lo.alloc(lo.size());
+        BEM_CUDA(cudaMemcpy(t->Tc_hi.p, hi.data(), hi.size() * sizeof(float), cudaMemcpyHostToDevice));
+        BEM_CUDA(cudaMemcpy(t->Tc_lo.p, lo.data(), lo.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     if (prec == BEM_MIXED) {
         upload(t->Rm2m_f, rtab);
         upload(t->If_f, it);
@@ -1303,6 +1312,7 @@ void build_translation_groups(Mesh &m, Tree &t) {
             for (int64_t b = start[o]; b < start[o + 1]; b += TR_BN_M2L)
                 chunks.push_back(make_int4(o, (int)b, (int)std::min<int64_t>(TR_BN_M2L, start[o + 1] - b), 0));
         t.m2l_nchunk = (int)chunks.size();
+        build_tc_super(t, chunks, s);
     }
     // M2M (out parent, in child) and L2L (out child, in parent) per child level
     for (int c = 3; c <= L; ++c) {
@@ -1391,6 +1401,15 @@ static void ev_rec(Mesh &m, bool timed, int k) {
     if (timed && m.tm.on) BEM_CUDA(cudaEventRecord(m.tm.ev[k], m.stream));
 }
 
+bool use_tc_m2l(const Mesh &m) {
+    if (!tc_m2l_available(m)) return false;
+    return m.opt.m2l_mode == BEM_M2L_TC || m.opt.m2l_mode == BEM_M2L_AUTO;
+}
+
+template <class T>
+static void m2l_dense(Mesh &m, const Tree &t, const T *Oop, int nc, int cs, int rblocks, size_t trsm,
+                      T *M, T *L);
+
 template <class T>
 static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const double *dens,
                      double *out, bool timed) {
@@ -1473,12 +1492,7 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
         if (dense) {
             BEM_CUDA(cudaMemsetAsync(L + (size_t)t.lvl_off[2] * cs, 0,
                                      (size_t)(t.ncell - t.lvl_off[2]) * cs * sizeof(T), s));
-            if (t.m2l_nchunk > 0) {
-                dim3 g(t.m2l_nchunk, rblocks);
-                k_translate<T, TR_BN_M2L><<<g, TR_THREADS, trsm, s>>>(B::Om2l(m), nc, cs, t.g_chunk.p + t.m2l_chunk0,
-                                                            t.g_out.p, t.g_in.p, M, L);
-                BEM_CHECK_LAUNCH();
-            }
+            m2l_dense<T>(m, t, B::Om2l(m), nc, cs, rblocks, trsm, M, L);
         } else {
             const size_t sm = ((size_t)(p + 1) * W + (size_t)(2 * p + 1) * W2) * sizeof(cpx<T>);
             set_smem<T>(k_m2l<T>, sm);
@@ -1639,6 +1653,22 @@ void build_near_table(Mesh &m) {
 
 
 template <class T>
+static void m2l_dense(Mesh &m, const Tree &t, const T *Oop, int nc, int cs, int rblocks, size_t trsm,
+                      T *M, T *L) {
+    if (t.m2l_nchunk == 0) return;
+    if constexpr (std::is_same<T, float>::value) {
+        if (use_tc_m2l(m)) {
+            m2l_tc(m, t, M, L);
+            return;
+        }
+    }
+    dim3 g(t.m2l_nchunk, rblocks);
+    k_translate<T, TR_BN_M2L><<<g, TR_THREADS, trsm, m.stream>>>(Oop, nc, cs, t.g_chunk.p + t.m2l_chunk0,
+                                                                  t.g_out.p, t.g_in.p, M, L);
+    BEM_CHECK_LAUNCH();
+}
+
+template <class T>
 static void run_pass_t(Mesh &m, const double *lam, double *out) {
     using B = PassBufs<T>;
     cudaStream_t s = m.stream;
@@ -1679,12 +1709,7 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
         }
         BEM_CUDA(cudaMemsetAsync(L + (size_t)t.lvl_off[2] * cs, 0,
                                  (size_t)(t.ncell - t.lvl_off[2]) * cs * sizeof(T), s));
-        if (t.m2l_nchunk > 0) {
-            dim3 g(t.m2l_nchunk, rblocks);
-            k_translate<T, TR_BN_M2L><<<g, TR_THREADS, trsm, s>>>(B::Om2l(m), nc, cs, t.g_chunk.p + t.m2l_chunk0,
-                                                                   t.g_out.p, t.g_in.p, M, L);
-            BEM_CHECK_LAUNCH();
-        }
+        m2l_dense<T>(m, t, B::Om2l(m), nc, cs, rblocks, trsm, M, L);
         for (int c = 3; c <= t.L; ++c) {
             if (t.l2l_nchunk[c] == 0) continue;
             dim3 g(t.l2l_nchunk[c], rblocks);

@@ -104,6 +104,8 @@ struct Tree {
     DArray<int> g_out, g_in;      // all grouped pairs: M2L, then M2M and L2L per level
     DArray<int4> g_chunk;
     DArray<int> p2p_order;        // leaves by decreasing near-field work (launch order)
+    DArray<int4> tc_super;        // tensor-core M2L work items (offset, first chunk, chunks)
+    int tc_nsuper = 0;
     int m2l_chunk0 = 0, m2l_nchunk = 0;
     std::vector<int> m2m_chunk0, m2m_nchunk, l2l_chunk0, l2l_nchunk; // indexed by child level
     size_t bytes() const;
@@ -138,8 +140,9 @@ struct Tables {
     int p = 0;
     DArray<float> Rm2m_f, If_f, Om2l_f, Om2m_f, Ol2l_f;
     DArray<double> Rm2m_d, If_d, Om2l_d, Om2m_d, Ol2l_d;
+    DArray<float> Tc_hi, Tc_lo;   // M2L operators split for 3xTF32, tensor-core tile order
     size_t bytes() const {
-        return Rm2m_f.bytes() + If_f.bytes() + Om2l_f.bytes() + Om2m_f.bytes() + Ol2l_f.bytes() +
+        return Tc_hi.bytes() + Tc_lo.bytes() + Rm2m_f.bytes() + If_f.bytes() + Om2l_f.bytes() + Om2m_f.bytes() + Ol2l_f.bytes() +
                Rm2m_d.bytes() + If_d.bytes() + Om2l_d.bytes() + Om2m_d.bytes() + Ol2l_d.bytes();
     }
 };
@@ -217,6 +220,7 @@ struct Mesh {
     DArray<double> sigma_s;
     bool have_sigma = false;
 
+    DArray<int> dev_err;               // device error word (bounded waits that ran out)
     Timers tm;
     size_t bytes() const;
 };
@@ -233,6 +237,13 @@ void rebuild_charge_tree(Mesh &m, const double *d_charges);
 void build_near_table(Mesh &m);
 void build_tables(Mesh &m);
 void build_translation_groups(Mesh &m, Tree &t);
+// tensor-core M2L (bem_tc.cu)
+bool tc_m2l_available(const Mesh &m);
+void build_tc_tables(int p, const std::vector<double> &om2l, int nops, std::vector<float> &hi,
+                     std::vector<float> &lo);
+void build_tc_super(Tree &t, const std::vector<int4> &chunks_m2l, cudaStream_t s);
+void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L);
+bool use_tc_m2l(const Mesh &m);
 void compute_bbox(const double *d, int64_t n, int stride, double *lo, double *hi, cudaStream_t s);
 
 // fast multipole passes (bem_fmm.cu).  `dens` is indexed in sorted panel

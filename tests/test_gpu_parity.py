@@ -53,7 +53,7 @@ def test_near_field_only_matches_dense(pkg, born3, precision, tol):
 
 
 @pytest.mark.parametrize("depth,p", [(2, 10), (3, 10), (3, 12), (4, 12), (4, 16)])
-@pytest.mark.parametrize("m2l_mode", [1, 2])
+@pytest.mark.parametrize("m2l_mode", [1, 2, 3])
 def test_fmm_matvec_matches_dense(pkg, small4, depth, p, m2l_mode):
     m, P = small4
     for x in (_x(m.n_p, 1), P.bq()):
@@ -62,6 +62,17 @@ def test_fmm_matvec_matches_dense(pkg, small4, depth, p, m2l_mode):
                       m2l_mode=m2l_mode) as g:
             y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
         assert rel(y, ref) < 1e-5, (depth, p, m2l_mode, rel(y, ref))
+
+
+def test_tensor_core_m2l_matches_simt(pkg, small4):
+    """M2L on the tensor cores (3xTF32) against the SIMT FP32 operators."""
+    m, P = small4
+    x = P.bq()
+    ys = []
+    for mode in (1, 3):
+        with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=4, p=10, m2l_mode=mode) as g:
+            ys.append(g.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
+    assert rel(ys[1] - x, ys[0] - x) < 2e-6
 
 
 @pytest.mark.parametrize("precision", [0, 1])
