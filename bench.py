@@ -187,6 +187,58 @@ def run_reference(args):
     }))
 
 
+def _time_matvec(pkg, mesh, n, torch, reps=5):
+    x = torch.from_numpy(np.random.default_rng(1).standard_normal(n)).cuda()
+    y = torch.empty_like(x)
+    for _ in range(2):
+        pkg.bem_matvec(mesh.h, x, y)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        pkg.bem_matvec(mesh.h, x, y)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def _solve(pkg, mol, torch, **opts):
+    mesh = pkg.Mesh(mol.panels, mol.charges, mol.eps_in, mol.eps_out, **opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sig, st = mesh.solve(allow_noconv=True)
+    dg = mesh.energy(sig)
+    torch.cuda.synchronize()
+    return mesh, dg, time.perf_counter() - t0, st
+
+
+def precision_comparison(pkg, mol, torch):
+    ref_mesh, dg_ref, _, _ = _solve(pkg, mol, torch, p=14, leaf_size=64, precision=1, tol=1e-10)
+    ref_mesh.close()
+    out = {"dG_ref_kcal": dg_ref, "reference": "FP64 GPU form, p = 14, GMRES tol 1e-10",
+           "gate": "|dG - dG_ref| / |dG_ref| <= 1e-5"}
+    for name, prec, leaf in (("mixed", 0, 128), ("fp64", 1, 64)):
+        chosen = None
+        for p in (6, 8, 10, 12):
+            mesh, dg, solve_s, st = _solve(pkg, mol, torch, p=p, leaf_size=leaf, precision=prec)
+            err = abs(dg - dg_ref) / abs(dg_ref)
+            if err <= 1e-5:
+                chosen = {"p": p, "leaf_size": leaf, "dG_rel_err": err, "solve_s": round(solve_s, 5),
+                          "gmres_iters": st["iterations"],
+                          "matvec_ms": round(_time_matvec(pkg, mesh, mol.n_p, torch), 4)}
+                mesh.close()
+                break
+            mesh.close()
+        out[name] = chosen
+    if out.get("mixed") and out.get("fp64"):
+        out["speedup_matvec"] = round(out["fp64"]["matvec_ms"] / out["mixed"]["matvec_ms"], 2)
+        out["speedup_solve"] = round(out["fp64"]["solve_s"] / out["mixed"]["solve_s"], 2)
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -277,6 +329,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     solve_s = time.perf_counter() - t1
 
+    # mixed vs FP64 GPU at equal accuracy: the smallest p whose solvation
+    # energy is within 1e-5 of the FP64 form at p = 14
+    prec_cmp = None
+    if not args.no_precision:
+        prec_cmp = precision_comparison(pkg, mol, torch)
+
     L = info["depth"]
     # gather, P2P, combine, operator epilogue, scatter; P2M, M2L, L2P and one M2M
     # and one L2L launch per level between 2 and L
@@ -298,6 +356,7 @@ def run_ours(args):
             "tree_build_s": round(tree_s, 4),
             "solve_s": round(solve_s, 4), "solve_iters": st["iterations"], "dG_kcal": dg,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "precision_comparison": prec_cmp,
             "gpu_launches": launches_per * args.steps, "clocks": clocks,
         }))
     if ws > 1:
@@ -317,6 +376,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -89,6 +89,7 @@ typedef struct bem_options {
                           1 = dense real operators grouped by offset class (batched SIMT
                           GEMM), 2 = per-target complex sums (reference form), 3 = as 1
                           with M2L on the tensor cores (tcgen05, 3xTF32; BEM_MIXED, p <= 10) */
+    int graph;         /* 1 = replay the K' product as a captured CUDA graph (default 1) */
 } bem_options;
 
 #define BEM_M2L_AUTO 0
@@ -184,6 +185,26 @@ int bem_energy(bem_mesh *mesh, const double *sigma, double *dG_kcal, double *phi
  * kappa = 4 pi 332.0637, each multiplied by grad_out.
  *   dq [n_c] and dx [n_c][3] f64, either may be NULL. */
 int bem_energy_backward(bem_mesh *mesh, double grad_out, double *dq, double *dx);
+
+/* Solve many independent meshes (created by bem_mesh_create, possibly of very
+ * different sizes) concurrently: right-hand side, GMRES, energy, and the
+ * BIBEE/CFA and BIBEE/P bounds (Sec. 2.2) of each.  Host worker threads
+ * (`threads`, 0 = 8) each drive one mesh at a time on that mesh's own stream,
+ * largest meshes first.  Outputs are indexed like `meshes`:
+ *   sigma[i] ([n_p of mesh i] f64, host or device) may be NULL (array or entry),
+ *   dG, dG_cfa, dG_p [n] host arrays, each may be NULL; stats [n] may be NULL.
+ * Returns the first hard error, else BEM_ENOCONV if any solve did not converge.
+ * The SURVEY's single persistent launch is replaced by concurrent streams and
+ * captured per-mesh graphs (no paper counterpart: the paper solves one system). */
+int bem_batch_solve(bem_mesh *const *meshes, int n, int threads, double *const *sigma, double *dG,
+                    double *dG_cfa, double *dG_p, bem_solve_stats *stats);
+
+/* Choose opt->leaf_size in {32,64,128,256} and opt->p in {6,8,10} for one
+ * geometry: the fastest K' product whose relative error against a p = 12
+ * product is at most `target` (inputs as in bem_mesh_create; other fields of
+ * *opt are kept).  Builds and times a few trial meshes. */
+int bem_autotune(const double *panels, int64_t n_p, const double *charges, int64_t n_c,
+                 double eps_in, double eps_out, double target, bem_options *opt);
 
 /* Sizes and counts of the handle (tree depth, list sizes, memory). */
 int bem_mesh_info_get(const bem_mesh *mesh, bem_mesh_info *info);

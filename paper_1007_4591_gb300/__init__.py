@@ -53,7 +53,7 @@ class bem_options(ctypes.Structure):
                 ("depth", ctypes.c_int), ("quad_points", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("flags", ctypes.c_uint), ("near_table", ctypes.c_int),
-                ("charge_mode", ctypes.c_int), ("m2l_mode", ctypes.c_int)]
+                ("charge_mode", ctypes.c_int), ("m2l_mode", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class bem_solve_stats(ctypes.Structure):
@@ -91,6 +91,9 @@ _SIGS = {
     "bem_set_profiling": [_vp, ctypes.c_int],
     "bem_last_phase_ms": [_vp, _vp],
     "bem_last_error": [],
+    "bem_batch_solve": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
+    "bem_autotune": [_vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                     ctypes.c_double, ctypes.POINTER(bem_options)],
 }
 
 _lib = None
@@ -239,6 +242,38 @@ def bem_last_phase_ms(h):
     t = np.zeros(7)
     _check(load_library().bem_last_phase_ms(h, _ptr(t)), "bem_last_phase_ms")
     return dict(zip(["p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "epilogue"], t.tolist()))
+
+
+def bem_batch_solve(meshes, threads: int = 8, sigmas=None):
+    """Solve every mesh of `meshes` (Mesh objects or raw handles) concurrently.
+
+    Returns (dG, dG_cfa, dG_p, stats) as numpy arrays / list of dicts.
+    `sigmas` (optional) is a list of f64 arrays receiving each solution."""
+    n = len(meshes)
+    hs = (ctypes.c_void_p * n)(*[m.h if hasattr(m, "h") else m for m in meshes])
+    dg = np.zeros(n)
+    dc = np.zeros(n)
+    dp = np.zeros(n)
+    st = (bem_solve_stats * n)()
+    sp = None
+    if sigmas is not None:
+        sp = (ctypes.c_void_p * n)(*[_ptr(s) for s in sigmas])
+    rc = load_library().bem_batch_solve(hs, n, int(threads), sp, _ptr(dg), _ptr(dc), _ptr(dp),
+                                        ctypes.cast(st, ctypes.c_void_p))
+    _check(rc, "bem_batch_solve", (BEM_ENOCONV,))
+    stats = [{f: getattr(s, f) for f, _ in s._fields_} for s in st]
+    return dg, dc, dp, stats
+
+
+def bem_autotune(panels, charges, eps_in, eps_out, target: float = 1e-5,
+                 opt: bem_options | None = None) -> bem_options:
+    o = opt if opt is not None else bem_options_default()
+    n_p = int(panels.shape[0])
+    n_c = int(charges.shape[0]) if charges is not None else 0
+    _check(load_library().bem_autotune(_ptr(panels), n_p, _ptr(charges), n_c, float(eps_in),
+                                       float(eps_out), float(target), ctypes.byref(o)),
+           "bem_autotune")
+    return o
 
 
 def bem_last_error() -> str:

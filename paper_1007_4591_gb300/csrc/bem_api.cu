@@ -61,6 +61,13 @@ static void finish_out(Mesh &m, const OutArg &o) {
         BEM_CUDA(cudaMemcpyAsync(o.user, o.dev, o.n * sizeof(double), cudaMemcpyDeviceToHost, m.stream));
 }
 
+// Order the mesh's work stream after everything already queued on the
+// caller's stream.
+static void enter(Mesh &m) {
+    BEM_CUDA(cudaEventRecord(m.ev_enter, m.user));
+    BEM_CUDA(cudaStreamWaitEvent(m.stream, m.ev_enter, 0));
+}
+
 // Synchronise the mesh's stream and report a bounded device wait that ran out.
 static void sync(Mesh &m) {
     BEM_CUDA(cudaStreamSynchronize(m.stream));
@@ -110,35 +117,40 @@ size_t Mesh::bytes() const {
     return b;
 }
 
+template <class T>
+static void ensure(DArray<T> &d, size_t n) {
+    if (d.n < n) d.alloc(n);
+}
+
+// Work buffers (grow-only: a captured graph keeps pointing at them).
 static void alloc_work(Mesh &m) {
     const size_t nc = (size_t)cell_stride(m.opt.p);
     const size_t ncell = (size_t)std::max(m.tp.ncell, m.tc.ncell);
+    const size_t nt = (size_t)std::max<int64_t>(std::max<int64_t>(m.np, m.nc), m.nqp);
     if (m.opt.precision == BEM_MIXED) {
-        m.Mf.alloc(ncell * nc);
-        m.Lf.alloc(ncell * nc);
-        const size_t nt = (size_t)std::max<int64_t>(std::max<int64_t>(m.np, m.nc), m.nqp);
-        m.far_f.alloc(nt);
-        m.near_f.alloc(nt);
+        ensure(m.Mf, ncell * nc);
+        ensure(m.Lf, ncell * nc);
+        ensure(m.far_f, nt);
+        ensure(m.near_f, nt);
     } else {
-        m.Md.alloc(ncell * nc);
-        m.Ld.alloc(ncell * nc);
-        const size_t nt = (size_t)std::max<int64_t>(std::max<int64_t>(m.np, m.nc), m.nqp);
-        m.far_d.alloc(nt);
-        m.near_d.alloc(nt);
+        ensure(m.Md, ncell * nc);
+        ensure(m.Ld, ncell * nc);
+        ensure(m.far_d, nt);
+        ensure(m.near_d, nt);
     }
     const size_t nsrc = (size_t)std::max<int64_t>(m.nqp, m.nc);
-    if (m.opt.precision == BEM_MIXED) m.str32.alloc(nsrc);
-    else m.str64.alloc(nsrc);
+    if (m.opt.precision == BEM_MIXED) ensure(m.str32, nsrc);
+    else ensure(m.str64, nsrc);
     const size_t nv = (size_t)std::max<int64_t>(m.np, m.nc);
-    m.xs.alloc(nv);
-    m.ys.alloc(nv);
-    m.zs.alloc(nv * 3);
-    m.red.alloc(16);
+    ensure(m.xs, nv);
+    ensure(m.ys, nv);
+    ensure(m.zs, nv * 3);
+    ensure(m.red, 16);
     if (!m.dev_err.p) {
         m.dev_err.alloc(1);
         BEM_CUDA(cudaMemsetAsync(m.dev_err.p, 0, sizeof(int), m.stream));
     }
-    m.part.alloc((size_t)(std::max(1, m.opt.gmres_restart) + 2) * 1024);
+    ensure(m.part, (size_t)(std::max(1, m.opt.gmres_restart) + 2) * 1024);
 }
 
 static void validate_options(const bem_options &o) {
@@ -180,6 +192,7 @@ int bem_options_default(bem_options *opt) {
     opt->near_table = 1;
     opt->charge_mode = BEM_CHARGE_AUTO;
     opt->m2l_mode = BEM_M2L_AUTO;
+    opt->graph = 1;
     return BEM_OK;
 }
 
@@ -205,7 +218,10 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
         else bem_options_default(&m->opt);
         validate_options(m->opt);
         BEM_CUDA(cudaGetDevice(&m->device));
-        m->stream = (cudaStream_t)stream;
+        m->user = (cudaStream_t)stream;
+        BEM_CUDA(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
+        BEM_CUDA(cudaEventCreateWithFlags(&m->ev_enter, cudaEventDisableTiming));
+        enter(*m);
         m->np = n_p;
         m->nc = n_c;
         m->nq = m->opt.quad_points;
@@ -228,8 +244,13 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
     });
     if (rc != BEM_OK) {
         if (m) {
+            if (m->stream) cudaStreamSynchronize(m->stream);
             if (m->h_pinned) cudaFreeHost(m->h_pinned);
+            cudaStream_t st = m->stream;
+            cudaEvent_t ev = m->ev_enter;
             delete m;
+            if (ev) cudaEventDestroy(ev);
+            if (st) cudaStreamDestroy(st);
         }
         return rc;
     }
@@ -244,17 +265,28 @@ int bem_mesh_destroy(bem_mesh *m) {
         for (auto &e : m->tm.ev)
             if (e) cudaEventDestroy(e);
         if (m->h_pinned) cudaFreeHost(m->h_pinned);
+        if (m->g_mv) cudaGraphExecDestroy(m->g_mv);
+        cudaStream_t st = m->stream;
+        cudaEvent_t ev = m->ev_enter;
         delete m;
+        if (ev) cudaEventDestroy(ev);
+        if (st) cudaStreamDestroy(st);
     });
 }
 
 int bem_set_charges(bem_mesh *m, const double *charges, int64_t n_c) {
     if (!m) return BEM_EINVAL;
     return guarded([&] {
+        enter(*m);
         if (n_c < 0 || (n_c > 0 && !charges)) throw Error(BEM_EINVAL, "bad charge array");
         DArray<double> sc;
         const double *dc = n_c > 0 ? dev_in(*m, charges, (size_t)n_c * 4, sc) : nullptr;
         m->nc = n_c;
+        if (m->g_mv) {  // the charge tree's cells may change the shared buffers: recapture
+            BEM_CUDA(cudaStreamSynchronize(m->stream));
+            cudaGraphExecDestroy(m->g_mv);
+            m->g_mv = nullptr;
+        }
         rebuild_charge_tree(*m, dc);
         build_translation_groups(*m, m->tc);
         alloc_work(*m);
@@ -266,6 +298,7 @@ int bem_set_charges(bem_mesh *m, const double *charges, int64_t n_c) {
 int bem_matvec(bem_mesh *m, const double *x, double *y) {
     if (!m || !x || !y) return BEM_EINVAL;
     return guarded([&] {
+        enter(*m);
         const double *dx = dev_in(*m, x, m->np, m->io_a);
         gather_f64(dx, m->cen_perm.p, m->xs.p, m->np, m->stream);
         matvec_sorted(*m, m->xs.p, m->ys.p);
@@ -279,6 +312,7 @@ int bem_matvec(bem_mesh *m, const double *x, double *y) {
 int bem_matvec_t(bem_mesh *m, const double *x, double *y) {
     if (!m || !x || !y) return BEM_EINVAL;
     return guarded([&] {
+        enter(*m);
         const double *dx = dev_in(*m, x, m->np, m->io_a);
         gather_f64(dx, m->cen_perm.p, m->xs.p, m->np, m->stream);
         matvec_t_sorted(*m, m->xs.p, m->ys.p);
@@ -301,6 +335,7 @@ static void rhs_sorted(Mesh &m, double *b_s) {
 int bem_rhs(bem_mesh *m, double *b) {
     if (!m || !b) return BEM_EINVAL;
     return guarded([&] {
+        enter(*m);
         rhs_sorted(*m, m->ys.p);
         OutArg o = dev_out(*m, b, m->np, m->io_b);
         scatter_f64(m->ys.p, m->cen_perm.p, o.dev, m->np, m->stream);
@@ -313,6 +348,7 @@ int bem_solve(bem_mesh *m, const double *x0, double *sigma, bem_solve_stats *st)
     if (!m || !sigma) return BEM_EINVAL;
     int status = BEM_OK;
     int rc = guarded([&] {
+        enter(*m);
         cudaEvent_t e0, e1, e2;
         BEM_CUDA(cudaEventCreate(&e0));
         BEM_CUDA(cudaEventCreate(&e1));
@@ -370,6 +406,7 @@ static double energy_sorted(Mesh &m, const double *sig_s, double *phi_user) {
 int bem_energy(bem_mesh *m, const double *sigma, double *dG, double *phi) {
     if (!m || !sigma) return BEM_EINVAL;
     return guarded([&] {
+        enter(*m);
         const double *ds = dev_in(*m, sigma, m->np, m->io_a);
         gather_f64(ds, m->cen_perm.p, m->xs.p, m->np, m->stream);
         const double e = energy_sorted(*m, m->xs.p, phi);
@@ -381,6 +418,7 @@ int bem_energy(bem_mesh *m, const double *sigma, double *dG, double *phi) {
 int bem_bibee(bem_mesh *m, int variant, double *sigma_hat, double *dG) {
     if (!m) return BEM_EINVAL;
     return guarded([&] {
+        enter(*m);
         double lam;
         if (variant == BEM_BIBEE_CFA) lam = -0.5;
         else if (variant == BEM_BIBEE_P) lam = 0.0;
@@ -407,6 +445,7 @@ int bem_bibee(bem_mesh *m, int variant, double *sigma_hat, double *dG) {
 int bem_energy_backward(bem_mesh *m, double grad_out, double *dq, double *dx) {
     if (!m) return BEM_EINVAL;
     return guarded([&] {
+        enter(*m);
         if (m->nc == 0) return;
         if (!m->have_sigma) {
             bem_solve_stats st{};

@@ -940,8 +940,10 @@ static void host_irregular_full(double x, double y, double z, int N, std::vector
 }
 
 static bool g_consts_up[64] = {};
+static std::mutex g_consts_mu;
 
 static void upload_constants(int dev) {
+    std::lock_guard<std::mutex> lk(g_consts_mu);
     if (dev >= 0 && dev < 64 && g_consts_up[dev]) return;
     double rd[MAXP + 1][MAXP + 1] = {};
     float rf[MAXP + 1][MAXP + 1] = {};
@@ -1010,6 +1012,18 @@ static void real_operator(int p, F coef, double *Tt) {
                     if (io >= 0 && ii >= 0) Tt[(size_t)ii * nc + io] += Pr - Qr;
                 }
         }
+}
+
+void ensure_smem_attr(const void *func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> done;
+    int dev = 0;
+    BEM_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = done[{func, dev}];
+    if (bytes <= cur) return;
+    BEM_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
 }
 
 struct TabKey {
@@ -1393,8 +1407,7 @@ static int p2m_threads(int p, size_t elt) {
 
 template <class T, class KernelT>
 static void set_smem(KernelT kern, size_t bytes) {
-    if (bytes > 48 * 1024)
-        BEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (bytes > 48 * 1024) ensure_smem_attr(reinterpret_cast<const void *>(kern), bytes);
 }
 
 static void ev_rec(Mesh &m, bool timed, int k) {

@@ -50,6 +50,10 @@ void set_last_error(const std::string &msg);
 
 #define BEM_CHECK_LAUNCH() BEM_CUDA(cudaGetLastError())
 
+// Raise a kernel's dynamic shared-memory limit once per (kernel, device);
+// repeated requests are free (no runtime call), which keeps graph capture clean.
+void ensure_smem_attr(const void *func, size_t bytes);
+
 // ------------------------------------------------------- device array (RAII)
 template <class T>
 struct DArray {
@@ -155,7 +159,13 @@ struct Timers {
 
 struct Mesh {
     bem_options opt;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;     // the mesh's own non-blocking work stream
+    cudaStream_t user = nullptr;       // the caller's stream (ordering hand-off)
+    cudaEvent_t ev_enter = nullptr;
+    // captured K' product on fixed buffers gx -> gy
+    cudaGraphExec_t g_mv = nullptr;
+    DArray<double> gx, gy;
+    bool capturing = false;
     int device = 0;
     int64_t np = 0, nc = 0, nq = 0, nqp = 0;
     double eps_in = 1, eps_out = 80, ehat = 0;

@@ -73,13 +73,52 @@ __global__ void k_apply_A(const double *x, const double *kx, const int *nt_off, 
     y[i] = x[i] + ehat * k;
 }
 
-void matvec_sorted(Mesh &m, const double *xs, double *ys) {
+static void matvec_launch(Mesh &m, const double *xs, double *ys) {
     const bool nt = m.nt_nnz > 0 && !(m.opt.flags & (BEM_FLAG_NO_NEARTAB | BEM_FLAG_NO_NEAR));
     fmm_pass(m, m.tp, SRC_QUAD, TGT_CEN_DN, xs, m.zs.p, true);
     k_apply_A<<<cdiv(m.np, 256), 256, 0, m.stream>>>(xs, m.zs.p, nt ? m.nt_off.p : nullptr,
                                                       m.nt_col.p, m.nt_val.p, m.ehat, m.np, ys);
     BEM_CHECK_LAUNCH();
     if (m.tm.on) BEM_CUDA(cudaEventRecord(m.tm.ev[7], m.stream));
+}
+
+// The K' product is a fixed sequence of ~20 kernels and memsets; with
+// opt.graph it is captured once (on the buffers gx -> gy, after one ordinary
+// run has set every kernel attribute) and replayed as a single graph launch.
+void matvec_sorted(Mesh &m, const double *xs, double *ys) {
+    if (!m.opt.graph || m.tm.on) {
+        matvec_launch(m, xs, ys);
+        return;
+    }
+    if (!m.g_mv) {
+        if (m.gx.n < (size_t)m.np) {
+            m.gx.alloc(m.np);
+            m.gy.alloc(m.np);
+        }
+        matvec_launch(m, xs, ys);  // warm-up outside the capture
+        cudaGraph_t g = nullptr;
+        BEM_CUDA(cudaStreamBeginCapture(m.stream, cudaStreamCaptureModeThreadLocal));
+        m.capturing = true;
+        try {
+            matvec_launch(m, m.gx.p, m.gy.p);
+        } catch (...) {
+            m.capturing = false;
+            cudaStreamEndCapture(m.stream, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        m.capturing = false;
+        BEM_CUDA(cudaStreamEndCapture(m.stream, &g));
+        const cudaError_t e = cudaGraphInstantiate(&m.g_mv, g, 0);
+        cudaGraphDestroy(g);
+        BEM_CUDA(e);
+        return;
+    }
+    if (xs != m.gx.p)
+        BEM_CUDA(cudaMemcpyAsync(m.gx.p, xs, m.np * sizeof(double), cudaMemcpyDeviceToDevice, m.stream));
+    BEM_CUDA(cudaGraphLaunch(m.g_mv, m.stream));
+    if (ys != m.gy.p)
+        BEM_CUDA(cudaMemcpyAsync(ys, m.gy.p, m.np * sizeof(double), cudaMemcpyDeviceToDevice, m.stream));
 }
 
 // --------------------------------------------------------------- BLAS-1

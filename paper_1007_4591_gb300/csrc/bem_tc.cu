@@ -313,7 +313,7 @@ void build_tc_super(Tree &t, const std::vector<int4> &chunks_m2l, cudaStream_t s
 void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L) {
     if (t.tc_nsuper == 0) return;
     const size_t sm = tc_smem_bytes();
-    BEM_CUDA(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc), sm);
     const int nc = (m.opt.p + 1) * (m.opt.p + 1);
     k_m2l_tc<<<t.tc_nsuper, 128, sm, m.stream>>>(m.tab->Tc_hi.p, m.tab->Tc_lo.p, t.tc_super.p,
                                                   t.g_chunk.p + t.m2l_chunk0, t.g_out.p, t.g_in.p, nc,
