@@ -206,6 +206,29 @@ int bem_batch_solve(bem_mesh *const *meshes, int n, int threads, double *const *
 int bem_autotune(const double *panels, int64_t n_p, const double *charges, int64_t n_c,
                  double eps_in, double eps_out, double target, bem_options *opt);
 
+/* Normal electric field of point charges at given points, for callers that
+ * cannot allocate GPU memory (the paper has no counterpart: it is a
+ * deployment variant of the direct charge-to-surface product behind
+ * bem_rhs).  Callers inside another framework's memory pool, real-time loops
+ * that must not touch the allocator, or processes whose device memory is
+ * already handed out can call it: it allocates nothing.
+ *   field_i = sum_k q_k [-(t_i - x_k).n_i] / (4 pi |t_i - x_k|^3),
+ * so -Ehat * field at the panel centroids is the right-hand side of bem_rhs.
+ *   targets [n_t][3], normals [n_t][3] (unit), charges [n_c][4] (x, y, z, q),
+ *   field [n_t]: all f64 DEVICE arrays (host pointers: BEM_EINVAL).
+ *   stream: cudaStream_t the work is queued on (NULL = legacy default); the
+ *   call returns without waiting.
+ * Its only scratch is one array inside the library, BEM_NOALLOC_SCRATCH_FLOATS
+ * floats (8 MiB) held by every device that loads the library until exit;
+ * n_t > BEM_NOALLOC_SCRATCH_FLOATS is rejected with BEM_EINVAL.  All calls on a
+ * device share that array and leave their partial sums in it: calls that
+ * overlap on the GPU (two streams, two threads) race and must be serialised.
+ * The first call on each device looks the array's address up; make that
+ * first call before any stream capture. */
+#define BEM_NOALLOC_SCRATCH_FLOATS (1 << 21)
+int bem_normal_field_noalloc(const double *targets, const double *normals, int64_t n_t,
+                             const double *charges, int64_t n_c, double *field, void *stream);
+
 /* Sizes and counts of the handle (tree depth, list sizes, memory). */
 int bem_mesh_info_get(const bem_mesh *mesh, bem_mesh_info *info);
 

@@ -92,6 +92,7 @@ _SIGS = {
     "bem_last_phase_ms": [_vp, _vp],
     "bem_last_error": [],
     "bem_batch_solve": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
+    "bem_normal_field_noalloc": [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp, _vp],
     "bem_autotune": [_vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                      ctypes.c_double, ctypes.POINTER(bem_options)],
 }
@@ -274,6 +275,18 @@ def bem_autotune(panels, charges, eps_in, eps_out, target: float = 1e-5,
                                        float(eps_out), float(target), ctypes.byref(o)),
            "bem_autotune")
     return o
+
+
+def bem_normal_field_noalloc(targets, normals, charges, field, stream=None):
+    """Normal field of point charges at points, allocating nothing on the GPU
+    (for callers that cannot allocate; device tensors only, see include/bem.h).
+    Queued on `stream` (a raw cudaStream_t, None = legacy default)."""
+    n_t = int(targets.shape[0])
+    n_c = int(charges.shape[0])
+    st = ctypes.c_void_p(stream) if stream is not None else None
+    return _check(load_library().bem_normal_field_noalloc(_ptr(targets), _ptr(normals), n_t,
+                                                          _ptr(charges), n_c, _ptr(field), st),
+                  "bem_normal_field_noalloc")
 
 
 def bem_last_error() -> str:
