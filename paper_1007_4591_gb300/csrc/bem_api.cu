@@ -108,7 +108,7 @@ size_t Mesh::bytes() const {
          ntT_val.bytes() + qp_of_panel.bytes();
     if (tab) b += tab->bytes();
     b += Mf.bytes() + Lf.bytes() + Md.bytes() + Ld.bytes();
-    b += str32.bytes() + str64.bytes() + dpart_f.bytes() + dpart_d.bytes();
+    b += Mtc.bytes() + str32.bytes() + str64.bytes() + dpart_f.bytes() + dpart_d.bytes();
     b += xs.bytes() + ys.bytes() + zs.bytes() + far_f.bytes() + near_f.bytes() + far_d.bytes() +
          near_d.bytes() + io_a.bytes() + io_b.bytes() + red.bytes();
     b += dev_err.bytes();
@@ -139,6 +139,7 @@ static void alloc_work(Mesh &m) {
         ensure(m.near_d, nt);
     }
     const size_t nsrc = (size_t)std::max<int64_t>(m.nqp, m.nc);
+    if (tc_m2l_available(m)) ensure(m.Mtc, tc_staging_floats(m));
     if (m.opt.precision == BEM_MIXED) ensure(m.str32, nsrc);
     else ensure(m.str64, nsrc);
     const size_t nv = (size_t)std::max<int64_t>(m.np, m.nc);
@@ -219,8 +220,16 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
         validate_options(m->opt);
         BEM_CUDA(cudaGetDevice(&m->device));
         m->user = (cudaStream_t)stream;
-        BEM_CUDA(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
+        // The far-field chain (small launches, each waiting on the last) runs at
+        // the highest priority, the near field beside it at the lowest, so that
+        // near-field blocks fill the SMs the chain leaves idle.
+        int prio_lo = 0, prio_hi = 0;
+        BEM_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        BEM_CUDA(cudaStreamCreateWithPriority(&m->stream, cudaStreamNonBlocking, prio_hi));
+        BEM_CUDA(cudaStreamCreateWithPriority(&m->stream2, cudaStreamNonBlocking, prio_lo));
         BEM_CUDA(cudaEventCreateWithFlags(&m->ev_enter, cudaEventDisableTiming));
+        BEM_CUDA(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+        BEM_CUDA(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
         enter(*m);
         m->np = n_p;
         m->nc = n_c;
@@ -246,11 +255,14 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
         if (m) {
             if (m->stream) cudaStreamSynchronize(m->stream);
             if (m->h_pinned) cudaFreeHost(m->h_pinned);
-            cudaStream_t st = m->stream;
-            cudaEvent_t ev = m->ev_enter;
+            if (m->stream2) cudaStreamSynchronize(m->stream2);
+            cudaStream_t st = m->stream, st2 = m->stream2;
+            cudaEvent_t ev = m->ev_enter, e1 = m->ev_fork, e2 = m->ev_join;
             delete m;
-            if (ev) cudaEventDestroy(ev);
+            for (cudaEvent_t e : {ev, e1, e2})
+                if (e) cudaEventDestroy(e);
             if (st) cudaStreamDestroy(st);
+            if (st2) cudaStreamDestroy(st2);
         }
         return rc;
     }
@@ -266,11 +278,14 @@ int bem_mesh_destroy(bem_mesh *m) {
             if (e) cudaEventDestroy(e);
         if (m->h_pinned) cudaFreeHost(m->h_pinned);
         if (m->g_mv) cudaGraphExecDestroy(m->g_mv);
-        cudaStream_t st = m->stream;
-        cudaEvent_t ev = m->ev_enter;
+        if (m->stream2) cudaStreamSynchronize(m->stream2);
+        cudaStream_t st = m->stream, st2 = m->stream2;
+        cudaEvent_t ev = m->ev_enter, e1 = m->ev_fork, e2 = m->ev_join;
         delete m;
-        if (ev) cudaEventDestroy(ev);
+        for (cudaEvent_t e : {ev, e1, e2})
+            if (e) cudaEventDestroy(e);
         if (st) cudaStreamDestroy(st);
+        if (st2) cudaStreamDestroy(st2);
     });
 }
 

@@ -1452,6 +1452,28 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             k_strength<T, SRC_CHARGE><<<cdiv(ns, 256), 256, 0, s>>>(srec, nullptr, dens, ns, strec);
         BEM_CHECK_LAUNCH();
     }
+    // The near field (compute bound) runs on a second stream next to the far
+    // field's chain of small, latency-bound launches; with phase timing on,
+    // everything stays on one stream so each phase is timed alone.
+    const bool conc = near && m.stream2 && !(timed && m.tm.on);
+    auto launch_near = [&](cudaStream_t ss) {
+        const T hh = (T)h;
+        if (sk == SRC_QUAD && tk == TGT_CEN_DN)
+            k_p2p<T, SRC_QUAD, TGT_CEN_DN><<<t.nleaf, P2P_THREADS, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
+        else if (sk == SRC_CHARGE && tk == TGT_CEN_DN)
+            k_p2p<T, SRC_CHARGE, TGT_CEN_DN><<<t.nleaf, P2P_THREADS, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
+        else if (sk == SRC_QUAD && tk == TGT_CHG_PHI)
+            k_p2p<T, SRC_QUAD, TGT_CHG_PHI><<<t.nleaf, P2P_THREADS, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
+        else
+            k_p2p<T, SRC_CHARGE, TGT_CHG_PHI><<<t.nleaf, P2P_THREADS, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
+        BEM_CHECK_LAUNCH();
+    };
+    if (conc) {
+        BEM_CUDA(cudaEventRecord(m.ev_fork, s));
+        BEM_CUDA(cudaStreamWaitEvent(m.stream2, m.ev_fork, 0));
+        launch_near(m.stream2);
+        BEM_CUDA(cudaEventRecord(m.ev_join, m.stream2));
+    }
     if (far) {
         T *M = B::M(m), *L = B::L(m);
         const int cs = cell_stride(p);
@@ -1552,19 +1574,9 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
     } else {
         for (int k = 1; k <= 5; ++k) ev_rec(m, timed, k);
     }
-    if (near) {
-        const T hh = (T)h;
-        if (sk == SRC_QUAD && tk == TGT_CEN_DN)
-            k_p2p<T, SRC_QUAD, TGT_CEN_DN><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, trec, nrec, strec, hh, near_b);
-        else if (sk == SRC_CHARGE && tk == TGT_CEN_DN)
-            k_p2p<T, SRC_CHARGE, TGT_CEN_DN><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, trec, nrec, strec, hh, near_b);
-        else if (sk == SRC_QUAD && tk == TGT_CHG_PHI)
-            k_p2p<T, SRC_QUAD, TGT_CHG_PHI><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, trec, nrec, strec, hh, near_b);
-        else
-            k_p2p<T, SRC_CHARGE, TGT_CHG_PHI><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, trec, nrec, strec, hh, near_b);
-        BEM_CHECK_LAUNCH();
-    }
+    if (near && !conc) launch_near(s);
     ev_rec(m, timed, 6);
+    if (near && conc) BEM_CUDA(cudaStreamWaitEvent(s, m.ev_join, 0));
     k_combine<T><<<cdiv(ntgt, 256), 256, 0, s>>>(far ? far_b : nullptr, near ? near_b : nullptr,
                                                   ntgt, 1.0 / FOUR_PI, out);
     BEM_CHECK_LAUNCH();
@@ -1696,6 +1708,18 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
     const bool near = !(m.opt.flags & BEM_FLAG_NO_NEAR);
     T *far_b = B::far(m), *near_b = B::near(m);
     build_qp_of_panel(m);
+    const bool conc = near && m.stream2;
+    auto launch_near = [&](cudaStream_t ss) {
+        BEM_CUDA(cudaMemsetAsync(near_b, 0, m.nqp * sizeof(T), ss));
+        k_p2p_t<T><<<t.nleaf, P2P_THREADS, 0, ss>>>(tv, B::cen(m), B::nrm(m), lam, B::qp(m), (T)h, near_b);
+        BEM_CHECK_LAUNCH();
+    };
+    if (conc) {
+        BEM_CUDA(cudaEventRecord(m.ev_fork, s));
+        BEM_CUDA(cudaStreamWaitEvent(m.stream2, m.ev_fork, 0));
+        launch_near(m.stream2);
+        BEM_CUDA(cudaEventRecord(m.ev_join, m.stream2));
+    }
     if (far) {
         T *M = B::M(m), *L = B::L(m);
         const int rblocks = cdiv(nc, TR_BM);
@@ -1736,11 +1760,8 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
         kern<<<t.nleaf, 128, sm, s>>>(tv, B::qp(m), B::nrm(m), p, cs, inv_h, L, far_b);
         BEM_CHECK_LAUNCH();
     }
-    if (near) {
-        BEM_CUDA(cudaMemsetAsync(near_b, 0, m.nqp * sizeof(T), s));
-        k_p2p_t<T><<<t.nleaf, P2P_THREADS, 0, s>>>(tv, B::cen(m), B::nrm(m), lam, B::qp(m), (T)h, near_b);
-        BEM_CHECK_LAUNCH();
-    }
+    if (near && !conc) launch_near(s);
+    if (near && conc) BEM_CUDA(cudaStreamWaitEvent(s, m.ev_join, 0));
     k_panel_reduce<T><<<cdiv(m.np, 256), 256, 0, s>>>(far ? far_b : nullptr, near ? near_b : nullptr,
                                                       m.qp_of_panel.p, m.qw64.p, (int)m.nq, m.np, out);
     BEM_CHECK_LAUNCH();

@@ -162,6 +162,8 @@ struct Mesh {
     cudaStream_t stream = nullptr;     // the mesh's own non-blocking work stream
     cudaStream_t user = nullptr;       // the caller's stream (ordering hand-off)
     cudaEvent_t ev_enter = nullptr;
+    cudaStream_t stream2 = nullptr;    // second work stream: near field next to the far field
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // captured K' product on fixed buffers gx -> gy
     cudaGraphExec_t g_mv = nullptr;
     DArray<double> gx, gy;
@@ -218,6 +220,7 @@ struct Mesh {
     DArray<double> far_d, near_d;      // (fp64 mode)
     DArray<double> io_a, io_b;         // staging for host or unsorted arguments
     DArray<double> red;                // reduction scratch
+    DArray<float> Mtc;                 // multipoles split hi|lo for the tensor-core M2L
     DArray<float4> str32;              // per-pass source strength records (mixed)
     DArray<double4> str64;             // (fp64 mode)
     DArray<float> dpart_f;             // direct-sum partials (mixed)
@@ -254,6 +257,7 @@ void build_tc_tables(int p, const std::vector<double> &om2l, int nops, std::vect
 void build_tc_super(Tree &t, const std::vector<int4> &chunks_m2l, cudaStream_t s);
 void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L);
 bool use_tc_m2l(const Mesh &m);
+size_t tc_staging_floats(const Mesh &m);
 void compute_bbox(const double *d, int64_t n, int stride, double *lo, double *hi, cudaStream_t s);
 
 // fast multipole passes (bem_fmm.cu).  `dens` is indexed in sorted panel

@@ -109,7 +109,8 @@ void matvec_sorted(Mesh &m, const double *xs, double *ys) {
         }
         m.capturing = false;
         BEM_CUDA(cudaStreamEndCapture(m.stream, &g));
-        const cudaError_t e = cudaGraphInstantiate(&m.g_mv, g, 0);
+        // keep the captured streams' priorities on the graph's kernel nodes
+        const cudaError_t e = cudaGraphInstantiateWithFlags(&m.g_mv, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         BEM_CUDA(e);
         return;

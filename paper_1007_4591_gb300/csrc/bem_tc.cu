@@ -15,6 +15,7 @@
 // expansions with coalesced atomics.  Every wait is bounded: on timeout the
 // kernel raises an error flag, waits once more (bounded) for its MMAs and
 // frees its tensor memory before returning.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -22,9 +23,10 @@
 
 namespace bem {
 
-constexpr int TC_BN = 32;          // pairs per MMA tile (N); a 64-pair chunk is two tiles
-constexpr int TC_K = 128;          // padded coefficients (K and M)
-constexpr int TC_TMEM_COLS = 128;  // allocated columns (two 32-column accumulators, power of two)
+constexpr int TC_BN = 64;            // pairs per MMA tile (N) = one 64-pair chunk
+constexpr int TC_K = 128;            // padded coefficients (K and M)
+constexpr int TC_TMEM_COLS = 512;    // A hi [0,128), A lo [128,256), 4 accumulators of 64
+constexpr int TC_A_HI = 0, TC_A_LO = 128, TC_D0 = 256;
 constexpr int TC_CHUNKS_PER_CTA = 16;
 constexpr long long TC_WAIT_CYCLES = 2000000000ll;  // about one second of SM clock
 
@@ -43,7 +45,7 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
     return d;
 }
 
-// Instruction descriptor: D f32, A and B tf32, both K-major, N = 32, M = 128.
+// Instruction descriptor: D f32, A and B tf32, both K-major, N = 64, M = 128.
 constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
                               ((uint32_t)(128 >> 4) << 24);
 
@@ -71,18 +73,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) 
     return true;
 }
 
-// element (row, k) of a K-major 128-column tile in core-matrix order (floats)
-__host__ __device__ __forceinline__ int tc_off(int row, int k) {
-    return (row >> 3) * (TC_K / 4) * 32 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc));
-}
-
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
 }
@@ -91,37 +81,55 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
 }
 
+// element (row, k) of a K-major 128-column tile in core-matrix order (floats)
+__host__ __device__ __forceinline__ int tc_off(int row, int k) {
+    return (row >> 3) * (TC_K / 4) * 32 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
+}
+
+// D += A (tensor memory) . B (shared-memory descriptor)
+__device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a), "l"(b), "r"(TC_IDESC), "r"(acc));
+}
+
 // Warp roles of the pipelined kernel.
-constexpr int TC_NS = 3;                       // shared B stages
+constexpr int TC_NS = 3;                       // shared B stages (64 KB each)
 constexpr int TC_ND = 4;                       // TMEM accumulators of TC_BN columns
 constexpr int TC_WARP_MMA = 0;                 // lane 0 issues the MMAs
 constexpr int TC_WARP_EPI0 = 1;                // warps 1..4: epilogue (TMEM lane quadrant = warp % 4)
-constexpr int TC_WARP_PROD0 = 5;               // warps 5..8: gather of B
+constexpr int TC_WARP_PROD0 = 5;               // warps 5..8: copies of B
 constexpr int TC_NPROD = 4 * 32, TC_NEPI = 4 * 32;
 constexpr int TC_THREADS = 9 * 32;
+constexpr int TC_CT_LD = TC_K + 4;             // row pitch of the transposed epilogue tile (floats)
 
-// Work item: (offset class, first 64-pair chunk, number of chunks); a
-// 64-pair chunk is two tiles of TC_BN = 32 pairs.  Pipeline: producers fill
-// B stage t % 3 (mbarrier fullB), the MMA thread waits for it and for the
-// accumulator t % 4 to be drained (emptyD), issues the 48 MMAs of the tile
-// and commits twice (emptyB: the stage may be refilled; fullD: the
-// accumulator is ready); the epilogue warps wait for fullD, read their TMEM
-// lanes, release the accumulator (emptyD) and scatter with atomics.
+// Work item: (offset class, first 64-pair chunk, number of chunks); a chunk
+// is one tile of 64 pairs.  The operator of the offset class (hi and lo
+// TF32 parts) is written once into tensor memory by the epilogue warps and is
+// the A operand of every MMA.  Pipeline: producers copy the tile's split
+// multipoles into B stage t % 3 (cp.async, tracked by mbarrier fullB); the
+// MMA thread waits for the stage and for accumulator t % 4 to be drained,
+// issues 16 K-steps x 3 products and commits twice (emptyB, fullD); the
+// epilogue warps read their TMEM lane quadrant, release the accumulator,
+// transpose the tile through shared memory and add it into the local
+// expansions with 16-byte vector atomics.
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
          const int4 *__restrict__ super, const int4 *__restrict__ chunks,
          const int *__restrict__ p_out, const int *__restrict__ p_in, int nc, int cs,
-         const float *__restrict__ Min, float *__restrict__ Lout, int *__restrict__ err) {
+         const float *__restrict__ Mtc, float *__restrict__ Lout, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smraw[];
-    float *Ahi = reinterpret_cast<float *>(smraw);
-    float *Alo = Ahi + TC_K * TC_K;
-    float *Bbuf = Alo + TC_K * TC_K;  // [TC_NS][hi, lo][TC_BN * TC_K]
+    float *Bbuf = reinterpret_cast<float *>(smraw);            // [TC_NS][hi, lo][TC_BN * TC_K]
+    float *Ct = Bbuf + (size_t)TC_NS * 2 * TC_BN * TC_K;       // [TC_BN][TC_CT_LD]
     __shared__ __align__(8) uint64_t fullB[TC_NS], emptyB[TC_NS], fullD[TC_ND], emptyD[TC_ND];
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
+    __shared__ int4 s_ch[TC_CHUNKS_PER_CTA];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int4 sc = super[blockIdx.x];
-    const int ntile = 2 * sc.z;
+    const int ntile = sc.z;
+    if (tid < sc.z) s_ch[tid] = chunks[sc.y + tid];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(TC_TMEM_COLS));
@@ -138,73 +146,94 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
         }
         s_fail = 0;
     }
-    {  // the operator of this offset class (hi, lo), asynchronous 16-byte copies
-        const char *gh = reinterpret_cast<const char *>(Ahi_all + (size_t)sc.x * TC_K * TC_K);
-        const char *gl = reinterpret_cast<const char *>(Alo_all + (size_t)sc.x * TC_K * TC_K);
-        const uint32_t sh = smem_u32(Ahi), sl = smem_u32(Alo);
-        for (int i = tid; i < TC_K * TC_K / 4; i += TC_THREADS) {
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sh + 16u * i), "l"(gh + 16 * (size_t)i));
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sl + 16u * i), "l"(gl + 16 * (size_t)i));
-        }
-        asm volatile("cp.async.commit_group;");
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tm = s_tmem;
+    // the operator of this offset class into tensor memory: lane = output
+    // coefficient (row), column = input coefficient; hi part at TC_A_HI, lo at TC_A_LO
+    if (warp >= TC_WARP_EPI0 && warp < TC_WARP_EPI0 + 4) {
+        const int quad = warp & 3, row = 32 * quad + lane;
+        const float *gh = Ahi_all + ((size_t)sc.x * TC_K + row) * TC_K;
+        const float *gl = Alo_all + ((size_t)sc.x * TC_K + row) * TC_K;
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            const float *g = half ? gl : gh;
+            const uint32_t col0 = half ? TC_A_LO : TC_A_HI;
+#pragma unroll 1
+            for (int c0 = 0; c0 < TC_K; c0 += 32) {
+                uint32_t v[32];
+#pragma unroll
+                for (int q = 0; q < 32; q += 4) {
+                    const float4 f = __ldg(reinterpret_cast<const float4 *>(g + c0 + q));
+                    v[q] = __float_as_uint(f.x);
+                    v[q + 1] = __float_as_uint(f.y);
+                    v[q + 2] = __float_as_uint(f.z);
+                    v[q + 3] = __float_as_uint(f.w);
+                }
+                asm volatile(
+                    "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                    "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(
+                        tm + ((uint32_t)(32 * quad) << 16) + col0 + (uint32_t)c0),
+                    "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+                    "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+                    "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),
+                    "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),
+                    "r"(v[29]), "r"(v[30]), "r"(v[31]));
+            }
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
 
     if (warp >= TC_WARP_PROD0) {
-        // ---------------- producers: gather tile t into stage t % TC_NS
+        // ---------------- producers: asynchronous copies of the split multipoles
+        // (hi | lo rows of Mtc) into stage t % TC_NS; each thread's copies are
+        // tracked by the stage's mbarrier (cp.async.mbarrier.arrive.noinc)
         const int ptid = tid - TC_WARP_PROD0 * 32;
+        constexpr int PER = TC_BN * (TC_K / 4) / TC_NPROD;  // 16-byte chunks per producer and half
+        constexpr int NR = PER / 2;                          // rows per producer thread (e >> 8 = u >> 1)
+        int srcs[NR], nxt[NR];
+        auto load_srcs = [&](int t, int *dst) {  // rows n = 8 v + (ptid & 7)
+            const int4 ch = s_ch[t];
+#pragma unroll
+            for (int v = 0; v < NR; ++v) {
+                const int n = 8 * v + (ptid & 7);
+                dst[v] = (n < ch.z) ? p_in[ch.y + n] : -1;
+            }
+        };
+        if (ntile > 0) load_srcs(0, srcs);
         for (int t = 0; t < ntile; ++t) {
             const int st = t % TC_NS, k = t / TC_NS;
+            if (t + 1 < ntile) load_srcs(t + 1, nxt);
             if (k >= 1 && !mbar_wait_bounded(smem_u32(&emptyB[st]), (uint32_t)((k - 1) & 1))) {
                 atomicExch(err, 1);
                 s_fail = 1;
                 break;
             }
-            const int4 ch = chunks[sc.y + (t >> 1)];
-            const int j0 = 32 * (t & 1);
-            float *Bhi = Bbuf + (size_t)st * 2 * TC_BN * TC_K, *Blo = Bhi + TC_BN * TC_K;
-            constexpr int PER = TC_BN * (TC_K / 4) / TC_NPROD;  // float4 groups per producer
-            float4 v[PER];
+            const uint32_t bh = smem_u32(Bbuf + (size_t)st * 2 * TC_BN * TC_K);
+            const uint32_t bl = bh + TC_BN * TC_K * 4;
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
-                const int e = ptid + TC_NPROD * u;
+                const int e = ptid + TC_NPROD * u;           // (n, k4): n = 8 (e >> 8) + (e & 7)
                 const int n = ((e >> 8) << 3) | (e & 7), k4 = (e >> 3) & 31;
-                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j0 + n < ch.z && 4 * k4 < nc) {
-                    const int src = p_in[ch.y + j0 + n];
-                    v[u] = __ldg(reinterpret_cast<const float4 *>(Min + (size_t)src * cs + 4 * k4));
-                }
+                const int src = srcs[e >> 8];
+                const float *g = Mtc + (size_t)(src >= 0 ? src : 0) * 2 * TC_K + 4 * k4;
+                const uint32_t nb = src >= 0 ? 16u : 0u;  // 0: zero-fill (padding rows)
+                const uint32_t off = 4u * (uint32_t)tc_off(n, 4 * k4);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bh + off), "l"(g), "r"(nb));
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bl + off), "l"(g + TC_K), "r"(nb));
             }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&fullB[st])) : "memory");
 #pragma unroll
-            for (int u = 0; u < PER; ++u) {
-                const int e = ptid + TC_NPROD * u;
-                const int n = ((e >> 8) << 3) | (e & 7), k4 = (e >> 3) & 31;
-                float w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-                float4 hi, lo;
-                float *hp = &hi.x, *lp = &lo.x;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float x = (4 * k4 + q < nc) ? w[q] : 0.f;  // the row's padding is not data
-                    const uint32_t h = to_tf32(x);
-                    hp[q] = __uint_as_float(h);
-                    lp[q] = __uint_as_float(to_tf32(x - __uint_as_float(h)));
-                }
-                const int off = tc_off(n, 4 * k4);
-                *reinterpret_cast<float4 *>(Bhi + off) = hi;
-                *reinterpret_cast<float4 *>(Blo + off) = lo;
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(smem_u32(&fullB[st]));
+            for (int v = 0; v < NR; ++v) srcs[v] = nxt[v];
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == TC_WARP_MMA) {
         // ---------------- MMA issue (one thread)
         if (lane == 0) {
-            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
             const uint32_t SBO = (TC_K / 4) * 128, LBO = 128;
             for (int t = 0; t < ntile; ++t) {
                 const int st = t % TC_NS, k = t / TC_NS;
@@ -216,18 +245,21 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                     s_fail = 1;
                     break;
                 }
+                // the stage was written by cp.async (generic proxy): order it before
+                // the tensor core's (async proxy) reads
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const float *Bhi = Bbuf + (size_t)st * 2 * TC_BN * TC_K, *Blo = Bhi + TC_BN * TC_K;
-                const uint32_t bh = smem_u32(Bhi), bl = smem_u32(Blo);
-                const uint32_t dt = tm + (uint32_t)(d * TC_BN);
-#pragma unroll 1
+                const uint32_t bh = smem_u32(Bbuf + (size_t)st * 2 * TC_BN * TC_K);
+                const uint32_t bl = bh + TC_BN * TC_K * 4;
+                const uint32_t dt = tm + (uint32_t)(TC_D0 + d * TC_BN);
+#pragma unroll 4
                 for (int ks = 0; ks < TC_K / 8; ++ks) {
                     const uint32_t ko = (uint32_t)ks * 2 * LBO;
-                    const uint64_t dah = tc_desc(ah + ko, LBO, SBO), dal = tc_desc(al + ko, LBO, SBO);
                     const uint64_t dbh = tc_desc(bh + ko, LBO, SBO), dbl = tc_desc(bl + ko, LBO, SBO);
-                    tc_mma(dt, dah, dbh, ks > 0 ? 1u : 0u);
-                    tc_mma(dt, dah, dbl, 1u);
-                    tc_mma(dt, dal, dbh, 1u);
+                    const uint32_t ah = tm + TC_A_HI + 8u * ks, al = tm + TC_A_LO + 8u * ks;
+                    tc_mma_ts(dt, ah, dbh, ks > 0 ? 1u : 0u);
+                    tc_mma_ts(dt, ah, dbl, 1u);
+                    tc_mma_ts(dt, al, dbh, 1u);
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  smem_u32(&emptyB[st]))
@@ -238,12 +270,21 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
             }
         }
     } else {
-        // ---------------- epilogue: TMEM lane quadrant (warp % 4), 32 pairs per tile
+        // ---------------- epilogue: TMEM lane quadrant (warp % 4), 64 pairs per tile
         const int quad = warp & 3;
         const int row = 32 * quad + lane;
+        const int etid = tid - TC_WARP_EPI0 * 32;  // 0..127
         for (int t = 0; t < ntile; ++t) {
             const int d = t % TC_ND, jd = t / TC_ND;
-            if (!mbar_wait_bounded(smem_u32(&fullD[d]), (uint32_t)(jd & 1))) {
+            const bool ok = mbar_wait_bounded(smem_u32(&fullD[d]), (uint32_t)(jd & 1));
+            // the four epilogue warps leave together (they meet at named barriers below)
+            uint32_t all_ok;
+            asm volatile(
+                "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
+                " selp.u32 %0, 1, 0, q;\n}\n"
+                : "=r"(all_ok)
+                : "r"((uint32_t)ok), "n"(TC_NEPI));
+            if (!all_ok) {
                 atomicExch(err, 1);
                 s_fail = 1;
                 break;
@@ -258,18 +299,23 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                       "=r"(r[cg + 5]), "=r"(r[cg + 6]), "=r"(r[cg + 7]), "=r"(r[cg + 8]), "=r"(r[cg + 9]),
                       "=r"(r[cg + 10]), "=r"(r[cg + 11]), "=r"(r[cg + 12]), "=r"(r[cg + 13]),
                       "=r"(r[cg + 14]), "=r"(r[cg + 15])
-                    : "r"(tm + ((uint32_t)(32 * quad) << 16) + (uint32_t)(d * TC_BN + cg)));
+                    : "r"(tm + ((uint32_t)(32 * quad) << 16) + (uint32_t)(TC_D0 + d * TC_BN + cg)));
             }
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(smem_u32(&emptyD[d]));
-            const int4 ch = chunks[sc.y + (t >> 1)];
-            const int j0 = 32 * (t & 1);
-            const int cnt = min(TC_BN, ch.z - j0);
-            if (row < nc) {
+            // transpose through shared memory: Ct[pair][coefficient]
+            asm volatile("bar.sync 1, %0;" ::"n"(TC_NEPI));  // previous tile's reads of Ct done
 #pragma unroll
-                for (int j = 0; j < TC_BN; ++j)
-                    if (j < cnt) atomicAdd(Lout + (size_t)p_out[ch.y + j0 + j] * cs + row, __uint_as_float(r[j]));
+            for (int j = 0; j < TC_BN; ++j) Ct[j * TC_CT_LD + row] = __uint_as_float(r[j]);
+            asm volatile("bar.sync 1, %0;" ::"n"(TC_NEPI));
+            const int4 ch = s_ch[t];
+            const int n4 = (nc + 3) >> 2;  // float4 groups per row (the last one spills into the stride padding)
+            for (int e = etid; e < ch.z * n4; e += TC_NEPI) {
+                const int j = e / n4, c4 = e - j * n4;
+                const float4 v = *reinterpret_cast<const float4 *>(Ct + j * TC_CT_LD + 4 * c4);
+                float4 *o = reinterpret_cast<float4 *>(Lout + (size_t)p_out[ch.y + j] * cs + 4 * c4);
+                atomicAdd(o, v);
             }
         }
     }
@@ -303,7 +349,9 @@ static inline float host_tf32(float x) {
     return r;
 }
 
-// hi/lo operator tiles in core order from the column-major double operators
+// hi/lo TF32 parts of the M2L operators, row-major [offset][row = output
+// coefficient][k = input coefficient], zero-padded to 128 x 128 (the kernel
+// writes them into tensor memory lane by lane)
 void build_tc_tables(int p, const std::vector<double> &om2l, int nops, std::vector<float> &hi,
                      std::vector<float> &lo) {
     const int nc = (p + 1) * (p + 1);
@@ -316,8 +364,8 @@ void build_tc_tables(int p, const std::vector<double> &om2l, int nops, std::vect
             for (int k = 0; k < nc; ++k) {
                 const float x = (float)T[(size_t)k * nc + row];
                 const float h = host_tf32(x);
-                H[tc_off(row, k)] = h;
-                L[tc_off(row, k)] = host_tf32(x - h);
+                H[(size_t)row * TC_K + k] = h;
+                L[(size_t)row * TC_K + k] = host_tf32(x - h);
             }
     }
 }
@@ -326,7 +374,7 @@ bool tc_m2l_available(const Mesh &m) {
     return m.opt.precision == BEM_MIXED && (m.opt.p + 1) * (m.opt.p + 1) <= TC_K;
 }
 
-size_t tc_smem_bytes() { return (size_t)(2 * TC_K * TC_K + 2 * TC_NS * TC_BN * TC_K) * sizeof(float); }
+size_t tc_smem_bytes() { return (size_t)(2 * TC_NS * TC_BN * TC_K + TC_BN * TC_CT_LD) * sizeof(float); }
 
 // super-chunks: up to TC_CHUNKS_PER_CTA consecutive M2L chunks of one offset class
 void build_tc_super(Tree &t, const std::vector<int4> &chunks_m2l, cudaStream_t s) {
@@ -346,15 +394,37 @@ void build_tc_super(Tree &t, const std::vector<int4> &chunks_m2l, cudaStream_t s
     BEM_CUDA(cudaStreamSynchronize(s));
 }
 
+// hi/lo TF32 split of the multipoles of the M2L sources (cells of levels
+// >= 2), rows of 2 x 128 floats: hi | lo, zero beyond (p+1)^2
+__global__ void k_split_m(const float *M, int first, int ncell, int nc, int cs, float *Mtc) {
+    const int c = first + blockIdx.x;
+    if (c >= ncell) return;
+    for (int k = threadIdx.x; k < TC_K; k += blockDim.x) {
+        const float x = k < nc ? M[(size_t)c * cs + k] : 0.f;
+        const uint32_t h = to_tf32(x);
+        Mtc[(size_t)c * 2 * TC_K + k] = __uint_as_float(h);
+        Mtc[(size_t)c * 2 * TC_K + TC_K + k] = __uint_as_float(to_tf32(x - __uint_as_float(h)));
+    }
+}
+
 void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L) {
     if (t.tc_nsuper == 0) return;
+    const int nc = (m.opt.p + 1) * (m.opt.p + 1);
+    const int cs = cell_stride(m.opt.p);
+    if (m.Mtc.n < (size_t)t.ncell * 2 * TC_K) throw Error(BEM_ECUDA, "tensor-core staging buffer too small");
+    const int first = t.lvl_off[2];
+    k_split_m<<<t.ncell - first, 128, 0, m.stream>>>(M, first, t.ncell, nc, cs, m.Mtc.p);
+    BEM_CHECK_LAUNCH();
     const size_t sm = tc_smem_bytes();
     ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc), sm);
-    const int nc = (m.opt.p + 1) * (m.opt.p + 1);
     k_m2l_tc<<<t.tc_nsuper, TC_THREADS, sm, m.stream>>>(m.tab->Tc_hi.p, m.tab->Tc_lo.p, t.tc_super.p,
-                                                  t.g_chunk.p + t.m2l_chunk0, t.g_out.p, t.g_in.p, nc,
-                                                  cell_stride(m.opt.p), M, L, m.dev_err.p);
+                                                         t.g_chunk.p + t.m2l_chunk0, t.g_out.p, t.g_in.p, nc,
+                                                         cs, m.Mtc.p, L, m.dev_err.p);
     BEM_CHECK_LAUNCH();
+}
+
+size_t tc_staging_floats(const Mesh &m) {
+    return (size_t)std::max(m.tp.ncell, m.tc.ncell) * 2 * TC_K;
 }
 
 }  // namespace bem

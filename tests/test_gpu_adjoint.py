@@ -68,9 +68,11 @@ def test_autograd_function_matches_backward(pkg):
         dg = pkg.solvation_energy(g, ch)
         dg.backward()
         dq, dx = g.energy_backward(1.0)
-        # two backward solves: equal up to the solve tolerance and summation order
-        assert torch.allclose(ch.grad[:, 3], dq, rtol=1e-6, atol=1e-9)
-        assert torch.allclose(ch.grad[:, :3], dx, rtol=1e-6, atol=1e-9)
+        # two backward solves: equal up to the solve tolerance and the order of
+        # the FP32 atomic sums (repeated mixed-precision runs differ by ~1e-7 of
+        # the largest entry, so the comparison is norm-wise)
+        assert rel(ch.grad[:, 3].cpu().numpy(), dq.cpu().numpy()) < 1e-6
+        assert rel(ch.grad[:, :3].cpu().numpy(), dx.cpu().numpy()) < 1e-6
         # quadratic in q: q . d dG/dq = 2 dG
         assert abs(float(ch.grad[:, 3] @ ch.detach()[:, 3]) - 2 * float(dg)) < 1e-6 * abs(float(dg))
 
