@@ -134,51 +134,120 @@ __device__ __forceinline__ void load_full(const T *src, int p, cpx<T> *dst) {
 }
 
 // ------------------------------------------------------------------- P2M
-template <class T, int SRC>
-__global__ void k_p2m(TreeView tv, const typename V4T<T>::t *rec, int p, int cs, T inv_h, T *M) {
+// P2M with the expansion order fixed at compile time: the recurrence of
+// regular_solid unrolls into straight-line code with its constants folded.
+// A CTA of `warps` warps owns one leaf; each warp takes 32 points at a time,
+// writes their strength-weighted harmonics into its own row buffer (odd row
+// stride: the column reads below hit 32 different banks) and every lane adds
+// up its columns over the 32 rows in registers.  The warps' column sums are
+// added in a fixed order at the end.  Lanes without a point write zero rows.
+// The same recurrence as regular_solid, unrolled by template recursion so
+// that every (n, m) step is straight-line code and its coefficients are
+// compile-time constants (rounded from double as the runtime tables are).
+template <class T, int P, int Mo, int N, class F>
+__device__ __forceinline__ void rs_column(T z, T r2, T are, T aim, T bre, T bim, F &emit) {
+    if constexpr (N <= P) {
+        constexpr T c2 = (T)(1.0 / ((double)(N + Mo) * (double)(N - Mo)));
+        constexpr T k1 = (T)(2 * N - 1);
+        const T c1 = k1 * z;
+        const T nre = (c1 * bre - r2 * are) * c2, nim = (c1 * bim - r2 * aim) * c2;
+        emit(N, Mo, nre, nim);
+        rs_column<T, P, Mo, N + 1>(z, r2, bre, bim, nre, nim, emit);
+    }
+}
+
+template <class T, int P, int Mo, class F>
+__device__ __forceinline__ void rs_sectoral(T x, T y, T z, T r2, T dre, T dim, F &emit) {
+    if constexpr (Mo <= P) {
+        if constexpr (Mo > 0) {
+            constexpr T f = -(T)(1.0 / (2.0 * Mo));
+            const T nre = f * (x * dre - y * dim), nim = f * (x * dim + y * dre);
+            dre = nre;
+            dim = nim;
+        }
+        emit(Mo, Mo, dre, dim);
+        if constexpr (Mo + 1 <= P) {
+            const T bre = z * dre, bim = z * dim;
+            emit(Mo + 1, Mo, bre, bim);
+            rs_column<T, P, Mo, Mo + 2>(z, r2, dre, dim, bre, bim, emit);
+        }
+        rs_sectoral<T, P, Mo + 1>(x, y, z, r2, dre, dim, emit);
+    }
+}
+
+template <class T, int P, class F>
+__device__ __forceinline__ void regular_solid_c(T x, T y, T z, F &&emit) {
+    const T r2 = x * x + y * y + z * z;
+    rs_sectoral<T, P, 0>(x, y, z, r2, (T)1, (T)0, emit);
+}
+
+template <class T, int P>
+static constexpr int p2m_row_stride() { return ((P + 1) * (P + 1)) | 1; }
+
+template <class T, int SRC, int P>
+__global__ void __launch_bounds__(128)
+k_p2m_c(TreeView tv, const typename V4T<T>::t *rec, int cs, T inv_h, T *M) {
+    constexpr int NC = (P + 1) * (P + 1);
+    constexpr int RS = p2m_row_stride<T, P>();
+    constexpr int KC = (NC + 31) / 32;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *sh = reinterpret_cast<T *>(smraw);
+    T *sm = reinterpret_cast<T *>(smraw);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T *buf = sm + (size_t)w * 32 * RS;
+    T *row = buf + lane * RS;
     const int leaf = blockIdx.x;
     const int *beg = SRC == SRC_QUAD ? tv.qp_beg : tv.chg_beg;
     const int b = beg[leaf], e = beg[leaf + 1];
-    const int nc = (p + 1) * (p + 1);
-    constexpr int MAXACC = 10;  // ceil((MAXP+1)^2 / 32)
-    T acc[MAXACC];
+    T acc[KC];
 #pragma unroll
-    for (int k = 0; k < MAXACC; ++k) acc[k] = 0;
-    for (int base = b; base < e; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        T *row = sh + threadIdx.x * nc;
+    for (int k = 0; k < KC; ++k) acc[k] = 0;
+    for (int base = b + w * 32; base < e; base += nw * 32) {
+        const int i = base + lane;
+        T x = 0, y = 0, z = 0, s = 0;
         if (i < e) {
             const typename V4T<T>::t r = rec[i];
-            const T s = r.w;  // strength record
-            regular_solid<T>(r.x * inv_h, r.y * inv_h, r.z * inv_h, p,
-                             [&](int n, int m, T re, T im) {
-                                 if (m == 0) row[n * n] = s * re;
-                                 else {
-                                     row[n * n + 2 * m - 1] = s * re;
-                                     row[n * n + 2 * m] = -s * im;
-                                 }
-                             });
+            x = r.x * inv_h;
+            y = r.y * inv_h;
+            z = r.z * inv_h;
+            s = r.w;
         }
-        __syncthreads();
-        const int cnt = min((int)blockDim.x, e - base);
-        int k = 0;
-        for (int c = threadIdx.x; c < nc; c += blockDim.x, ++k) {
-            T a = 0;
-            for (int j = 0; j < cnt; ++j) a += sh[j * nc + c];
+        regular_solid_c<T, P>(x, y, z, [&](int n, int m, T re, T im) {
+            if (m == 0) row[n * n] = s * re;
+            else {
+                row[n * n + 2 * m - 1] = s * re;
+                row[n * n + 2 * m] = -s * im;
+            }
+        });
+        __syncwarp();
 #pragma unroll
-            for (int q = 0; q < MAXACC; ++q)
-                if (q == k) acc[q] += a;
+        for (int k = 0; k < KC; ++k) {
+            const int c = lane + 32 * k;
+            if (c < NC) {
+                T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    s0 += buf[j * RS + c];
+                    s1 += buf[(j + 1) * RS + c];
+                    s2 += buf[(j + 2) * RS + c];
+                    s3 += buf[(j + 3) * RS + c];
+                }
+                acc[k] += (s0 + s1) + (s2 + s3);
+            }
         }
-        __syncthreads();
+        __syncwarp();
     }
-    T *out = M + (size_t)(tv.leaf0 + leaf) * cs;
-    int k = 0;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x, ++k) {
+    __syncthreads();
 #pragma unroll
-        for (int q = 0; q < MAXACC; ++q)
-            if (q == k) out[c] = acc[q];
+    for (int k = 0; k < KC; ++k) {
+        const int c = lane + 32 * k;
+        if (c < NC) sm[w * NC + c] = acc[k];
+    }
+    __syncthreads();
+    T *out = M + (size_t)(tv.leaf0 + leaf) * cs;
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) {
+        T a = 0;
+        for (int v = 0; v < nw; ++v) a += sm[v * NC + c];
+        out[c] = a;
     }
 }
 
@@ -1156,6 +1225,27 @@ template <class T> struct TrBK;
 template <> struct TrBK<float> { static constexpr int v = 32; };
 template <> struct TrBK<double> { static constexpr int v = 16; };
 
+constexpr int TR_NS = 4;  // cp.async stages of the K loop (p <= 10 fits in one round)
+
+// One element copied global -> shared without passing through registers;
+// ok = false writes zero (src-size 0: nothing is read).
+template <class T>
+__device__ __forceinline__ void cp_async_elt(T *dst, const T *src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = ok ? (int)sizeof(T) : 0;
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// out[p_out[j]] += Op[class] x in[p_in[j]] for the pairs of one chunk (one
+// operator class): a [BM x nc] x [nc x BN] product whose K loop is staged
+// through TR_NS shared-memory buffers by cp.async, so every tile's loads are
+// in flight together instead of one latency per element.
 template <class T, int BN>
 __global__ void __launch_bounds__(TR_THREADS)
 k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ chunks,
@@ -1163,10 +1253,10 @@ k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ 
             T *__restrict__ out) {
     constexpr int BK = TrBK<T>::v;
     constexpr int CPT = BN / 16;            // columns per thread
+    constexpr int STAGE = BK * TR_BM + BK * BN;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *As = reinterpret_cast<T *>(smraw);   // [BK][BM]
-    T *Bs = As + BK * TR_BM;                // [BK][BN]
-    T *Cs = As;                             // [BN][BM+1] (epilogue)
+    T *sm = reinterpret_cast<T *>(smraw);   // TR_NS x {As [BK][BM], Bs [BK][BN]}
+    T *Cs = sm;                             // [BN][BM+1] (epilogue)
     __shared__ int s_in[BN], s_out[BN];
     const int4 ch = chunks[blockIdx.x];
     const T *Tt = ops + (size_t)ch.x * nc * nc;
@@ -1182,21 +1272,35 @@ k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ 
 #pragma unroll
         for (int c = 0; c < CPT; ++c) acc[r][c] = 0;
     __syncthreads();
-    for (int k0 = 0; k0 < nc; k0 += BK) {
+    const int nk = (nc + BK - 1) / BK;
+    auto issue = [&](int kt) {
+        T *As = sm + (kt % TR_NS) * STAGE;
+        T *Bs = As + BK * TR_BM;
+        const int k0 = kt * BK;
         for (int e = tid; e < BK * TR_BM; e += TR_THREADS) {
             const int k = e / TR_BM, r = e - k * TR_BM;
-            T v = 0;
-            if (k0 + k < nc && rb + r < nc) v = Tt[(size_t)(k0 + k) * nc + rb + r];
-            As[k * TR_BM + r] = v;
+            const bool ok = k0 + k < nc && rb + r < nc;
+            cp_async_elt(As + e, ok ? Tt + (size_t)(k0 + k) * nc + rb + r : Tt, ok);
         }
         for (int e = tid; e < BK * BN; e += TR_THREADS) {
-            const int j = e / BK, k = e - j * BK;
+            const int k = e / BN, j = e - k * BN;
             const int src = s_in[j];
-            T v = 0;
-            if (src >= 0 && k0 + k < nc) v = in[(size_t)src * cs + k0 + k];
-            Bs[k * BN + j] = v;
+            const bool ok = src >= 0 && k0 + k < nc;
+            cp_async_elt(Bs + e, ok ? in + (size_t)src * cs + k0 + k : in, ok);
         }
-        __syncthreads();
+    };
+#pragma unroll
+    for (int st = 0; st < TR_NS - 1; ++st) {
+        if (st < nk) issue(st);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < nk; ++kt) {
+        cp_async_wait<TR_NS - 2>();  // this thread's copies of tile kt have landed
+        __syncthreads();             // everyone's have; stage (kt - 1) % TR_NS is free again
+        if (kt + TR_NS - 1 < nk) issue(kt + TR_NS - 1);
+        cp_async_commit();
+        const T *As = sm + (kt % TR_NS) * STAGE;
+        const T *Bs = As + BK * TR_BM;
 #pragma unroll 4
         for (int k = 0; k < BK; ++k) {
             T a[8], b[CPT];
@@ -1209,8 +1313,9 @@ k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ 
 #pragma unroll
                 for (int c = 0; c < CPT; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
         }
-        __syncthreads();
     }
+    cp_async_wait<0>();
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -1228,7 +1333,7 @@ k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ 
 template <class T, int BN>
 static size_t translate_smem() {
     constexpr int BK = TrBK<T>::v;
-    const size_t a = (size_t)(BK * TR_BM + BK * BN) * sizeof(T);
+    const size_t a = (size_t)TR_NS * (BK * TR_BM + BK * BN) * sizeof(T);
     const size_t c = (size_t)BN * (TR_BM + 1) * sizeof(T);
     return std::max(a, c);
 }
@@ -1410,6 +1515,31 @@ static void set_smem(KernelT kern, size_t bytes) {
     if (bytes > 48 * 1024) ensure_smem_attr(reinterpret_cast<const void *>(kern), bytes);
 }
 
+// P2M of one pass: the compile-time-order kernel, with as many warps per CTA
+// (up to 4) as keep its row buffers within 96 KB.
+template <class T, int SRC, int P>
+static void p2m_launch_c(const Tree &t, const TreeView &tv, const typename V4T<T>::t *strec, int cs,
+                         T inv_h, T *M, cudaStream_t s) {
+    constexpr size_t row = (size_t)32 * p2m_row_stride<T, P>() * sizeof(T);
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (96 * 1024) / row));
+    const size_t sm = warps * row;
+    auto kern = k_p2m_c<T, SRC, P>;
+    set_smem<T>(kern, sm);
+    kern<<<t.nleaf, warps * 32, sm, s>>>(tv, strec, cs, inv_h, M);
+    BEM_CHECK_LAUNCH();
+}
+
+template <class T, int SRC, int P = 1>
+static void p2m_launch(const Tree &t, const TreeView &tv, const typename V4T<T>::t *strec, int p, int cs,
+                       T inv_h, T *M, cudaStream_t s) {
+    if constexpr (P <= MAXP) {
+        if (p == P) p2m_launch_c<T, SRC, P>(t, tv, strec, cs, inv_h, M, s);
+        else p2m_launch<T, SRC, P + 1>(t, tv, strec, p, cs, inv_h, M, s);
+    } else {
+        throw Error(BEM_EINVAL, "expansion order out of range");
+    }
+}
+
 static void ev_rec(Mesh &m, bool timed, int k) {
     if (timed && m.tm.on) BEM_CUDA(cudaEventRecord(m.tm.ev[k], m.stream));
 }
@@ -1486,20 +1616,8 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             set_smem<T>(k_translate<T, TR_BN_TREE>, trsm_t);
         }
         // P2M
-        {
-            const int th = p2m_threads(p, sizeof(T));
-            const size_t sm = (size_t)th * nc * sizeof(T);
-            if (sk == SRC_QUAD) {
-                auto kern = k_p2m<T, SRC_QUAD>;
-                set_smem<T>(kern, sm);
-                kern<<<t.nleaf, th, sm, s>>>(tv, strec, p, cs, inv_h, M);
-            } else {
-                auto kern = k_p2m<T, SRC_CHARGE>;
-                set_smem<T>(kern, sm);
-                kern<<<t.nleaf, th, sm, s>>>(tv, strec, p, cs, inv_h, M);
-            }
-            BEM_CHECK_LAUNCH();
-        }
+        if (sk == SRC_QUAD) p2m_launch<T, SRC_QUAD>(t, tv, strec, p, cs, inv_h, M, s);
+        else p2m_launch<T, SRC_CHARGE>(t, tv, strec, p, cs, inv_h, M, s);
         ev_rec(m, timed, 1);
         // M2M: parents at levels L-1 .. 2
         if (dense) {
