@@ -254,6 +254,8 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     opts = dict(p=args.p, leaf_size=args.leaf, precision=0, m2l_mode=args.m2l_mode)
+    if args.graph >= 0:
+        opts["graph"] = args.graph
     t0 = time.perf_counter()
     mesh = pkg.Mesh(mol.panels, mol.charges, mol.eps_in, mol.eps_out, **opts)
     tree_s = time.perf_counter() - t0
@@ -351,7 +353,8 @@ def run_ours(args):
                                    "panels, 2,000 charges, eps 4/80)",
                        "p": args.p, "leaf_size": args.leaf, "depth": L, "precision": "mixed",
                        "global_batch": ws, "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "flushed (256 MB write) between timed products"},
+                       "l2": "flushed (256 MB write) between timed products",
+                       "cuda_graph": bool(mesh.opt.graph)},
             "phases_ms": {k: round(v, 4) for k, v in ph.items()},
             "tree_build_s": round(tree_s, 4),
             "solve_s": round(solve_s, 4), "solve_iters": st["iterations"], "dG_kcal": dg,
@@ -371,8 +374,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--p", type=int, default=10)
-    ap.add_argument("--leaf", type=int, default=128)
+    ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--m2l-mode", type=int, default=0)
+    ap.add_argument("--graph", type=int, default=-1, help="1/0: replay the product as a CUDA graph or not "
+                    "(default: the library's default)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")

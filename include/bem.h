@@ -89,7 +89,9 @@ typedef struct bem_options {
                           1 = dense real operators grouped by offset class (batched SIMT
                           GEMM), 2 = per-target complex sums (reference form), 3 = as 1
                           with M2L on the tensor cores (tcgen05, 3xTF32; BEM_MIXED, p <= 10) */
-    int graph;         /* 1 = replay the K' product as a captured CUDA graph (default 1) */
+    int graph;         /* 1 = replay the K' product as a captured CUDA graph; 0 (default) = launch
+                          its kernels on the mesh's two prioritised streams, where the near
+                          and far fields overlap better than in a replayed graph */
 } bem_options;
 
 #define BEM_M2L_AUTO 0

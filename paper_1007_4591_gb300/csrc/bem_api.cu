@@ -148,8 +148,8 @@ static void alloc_work(Mesh &m) {
     ensure(m.zs, nv * 3);
     ensure(m.red, 16);
     if (!m.dev_err.p) {
-        m.dev_err.alloc(1);
-        BEM_CUDA(cudaMemsetAsync(m.dev_err.p, 0, sizeof(int), m.stream));
+        m.dev_err.alloc(2);  // [0] error word, [1] work-item counter of the tensor-core M2L
+        BEM_CUDA(cudaMemsetAsync(m.dev_err.p, 0, 2 * sizeof(int), m.stream));
     }
     ensure(m.part, (size_t)(std::max(1, m.opt.gmres_restart) + 2) * 1024);
 }
@@ -193,7 +193,7 @@ int bem_options_default(bem_options *opt) {
     opt->near_table = 1;
     opt->charge_mode = BEM_CHARGE_AUTO;
     opt->m2l_mode = BEM_M2L_AUTO;
-    opt->graph = 1;
+    opt->graph = 0;
     return BEM_OK;
 }
 

@@ -28,7 +28,7 @@
 #include <mutex>
 #include <type_traits>
 
-#include "bem_internal.cuh"
+#include "bem_device.cuh"
 
 namespace bem {
 
@@ -54,28 +54,8 @@ template <> struct K<double> {
     __device__ static double pow2n(int j) { return c_pow2n_d[j]; }
 };
 
-template <class T> struct V4T;
-template <> struct V4T<float> { using t = float4; };
-template <> struct V4T<double> { using t = double4; };
-
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-
-template <class T>
-struct cpx {
-    T x, y;
-};
-
-template <class T>
-__device__ __forceinline__ void cmac(cpx<T> &acc, cpx<T> a, cpx<T> b) {  // acc += a*b
-    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
-    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
-}
-template <class T>
-__device__ __forceinline__ void cmac_conjb(cpx<T> &acc, cpx<T> a, cpx<T> b) {  // acc += a*conj(b)
-    acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-    acc.y = fma(a.y, b.x, fma(-a.x, b.y, acc.y));
-}
 
 // Regular solid harmonics R_n^m(x,y,z), 0 <= m <= n <= p, handed to emit(n, m, re, im).
 template <class T, class F>
@@ -134,123 +114,6 @@ __device__ __forceinline__ void load_full(const T *src, int p, cpx<T> *dst) {
 }
 
 // ------------------------------------------------------------------- P2M
-// P2M with the expansion order fixed at compile time: the recurrence of
-// regular_solid unrolls into straight-line code with its constants folded.
-// A CTA of `warps` warps owns one leaf; each warp takes 32 points at a time,
-// writes their strength-weighted harmonics into its own row buffer (odd row
-// stride: the column reads below hit 32 different banks) and every lane adds
-// up its columns over the 32 rows in registers.  The warps' column sums are
-// added in a fixed order at the end.  Lanes without a point write zero rows.
-// The same recurrence as regular_solid, unrolled by template recursion so
-// that every (n, m) step is straight-line code and its coefficients are
-// compile-time constants (rounded from double as the runtime tables are).
-template <class T, int P, int Mo, int N, class F>
-__device__ __forceinline__ void rs_column(T z, T r2, T are, T aim, T bre, T bim, F &emit) {
-    if constexpr (N <= P) {
-        constexpr T c2 = (T)(1.0 / ((double)(N + Mo) * (double)(N - Mo)));
-        constexpr T k1 = (T)(2 * N - 1);
-        const T c1 = k1 * z;
-        const T nre = (c1 * bre - r2 * are) * c2, nim = (c1 * bim - r2 * aim) * c2;
-        emit(N, Mo, nre, nim);
-        rs_column<T, P, Mo, N + 1>(z, r2, bre, bim, nre, nim, emit);
-    }
-}
-
-template <class T, int P, int Mo, class F>
-__device__ __forceinline__ void rs_sectoral(T x, T y, T z, T r2, T dre, T dim, F &emit) {
-    if constexpr (Mo <= P) {
-        if constexpr (Mo > 0) {
-            constexpr T f = -(T)(1.0 / (2.0 * Mo));
-            const T nre = f * (x * dre - y * dim), nim = f * (x * dim + y * dre);
-            dre = nre;
-            dim = nim;
-        }
-        emit(Mo, Mo, dre, dim);
-        if constexpr (Mo + 1 <= P) {
-            const T bre = z * dre, bim = z * dim;
-            emit(Mo + 1, Mo, bre, bim);
-            rs_column<T, P, Mo, Mo + 2>(z, r2, dre, dim, bre, bim, emit);
-        }
-        rs_sectoral<T, P, Mo + 1>(x, y, z, r2, dre, dim, emit);
-    }
-}
-
-template <class T, int P, class F>
-__device__ __forceinline__ void regular_solid_c(T x, T y, T z, F &&emit) {
-    const T r2 = x * x + y * y + z * z;
-    rs_sectoral<T, P, 0>(x, y, z, r2, (T)1, (T)0, emit);
-}
-
-template <class T, int P>
-static constexpr int p2m_row_stride() { return ((P + 1) * (P + 1)) | 1; }
-
-template <class T, int SRC, int P>
-__global__ void __launch_bounds__(128)
-k_p2m_c(TreeView tv, const typename V4T<T>::t *rec, int cs, T inv_h, T *M) {
-    constexpr int NC = (P + 1) * (P + 1);
-    constexpr int RS = p2m_row_stride<T, P>();
-    constexpr int KC = (NC + 31) / 32;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T *sm = reinterpret_cast<T *>(smraw);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    T *buf = sm + (size_t)w * 32 * RS;
-    T *row = buf + lane * RS;
-    const int leaf = blockIdx.x;
-    const int *beg = SRC == SRC_QUAD ? tv.qp_beg : tv.chg_beg;
-    const int b = beg[leaf], e = beg[leaf + 1];
-    T acc[KC];
-#pragma unroll
-    for (int k = 0; k < KC; ++k) acc[k] = 0;
-    for (int base = b + w * 32; base < e; base += nw * 32) {
-        const int i = base + lane;
-        T x = 0, y = 0, z = 0, s = 0;
-        if (i < e) {
-            const typename V4T<T>::t r = rec[i];
-            x = r.x * inv_h;
-            y = r.y * inv_h;
-            z = r.z * inv_h;
-            s = r.w;
-        }
-        regular_solid_c<T, P>(x, y, z, [&](int n, int m, T re, T im) {
-            if (m == 0) row[n * n] = s * re;
-            else {
-                row[n * n + 2 * m - 1] = s * re;
-                row[n * n + 2 * m] = -s * im;
-            }
-        });
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-            const int c = lane + 32 * k;
-            if (c < NC) {
-                T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-#pragma unroll
-                for (int j = 0; j < 32; j += 4) {
-                    s0 += buf[j * RS + c];
-                    s1 += buf[(j + 1) * RS + c];
-                    s2 += buf[(j + 2) * RS + c];
-                    s3 += buf[(j + 3) * RS + c];
-                }
-                acc[k] += (s0 + s1) + (s2 + s3);
-            }
-        }
-        __syncwarp();
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < KC; ++k) {
-        const int c = lane + 32 * k;
-        if (c < NC) sm[w * NC + c] = acc[k];
-    }
-    __syncthreads();
-    T *out = M + (size_t)(tv.leaf0 + leaf) * cs;
-    for (int c = threadIdx.x; c < NC; c += blockDim.x) {
-        T a = 0;
-        for (int v = 0; v < nw; ++v) a += sm[v * NC + c];
-        out[c] = a;
-    }
-}
-
 // ------------------------------------------------------------------- M2M
 // Parents [first, last) gather their children's multipoles.
 template <class T>
@@ -393,8 +256,11 @@ __global__ void k_l2l(TreeView tv, int first, const cpx<T> *Rtab, int p, int cs,
 }
 
 // ------------------------------------------------------------------- L2P
+// L2P: one CTA per leaf, sized to the leaves' average number of targets
+// (l2p_threads); the local expansion is expanded into the full
+// (n, m = -n..n) array in shared memory.
 template <class T, int TGT>
-__global__ void k_l2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
+__global__ void __launch_bounds__(128) k_l2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
                       int p, int cs, T inv_h, const T *L, T *out) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int W = 2 * p + 1;
@@ -1503,6 +1369,12 @@ struct PassBufs<double> {
     static double4 *str(Mesh &m) { return m.str64.p; }
 };
 
+// one warp per 32 targets of an average leaf, 1..4 warps
+static int l2p_threads(int64_t ntgt, int nleaf) {
+    const int64_t avg = nleaf > 0 ? (ntgt + nleaf - 1) / nleaf : 1;
+    return (int)std::min<int64_t>(128, std::max<int64_t>(32, (avg + 31) / 32 * 32));
+}
+
 static int p2m_threads(int p, size_t elt) {
     const size_t nc = (size_t)(p + 1) * (p + 1);
     int t = 128;
@@ -1515,30 +1387,6 @@ static void set_smem(KernelT kern, size_t bytes) {
     if (bytes > 48 * 1024) ensure_smem_attr(reinterpret_cast<const void *>(kern), bytes);
 }
 
-// P2M of one pass: the compile-time-order kernel, with as many warps per CTA
-// (up to 4) as keep its row buffers within 96 KB.
-template <class T, int SRC, int P>
-static void p2m_launch_c(const Tree &t, const TreeView &tv, const typename V4T<T>::t *strec, int cs,
-                         T inv_h, T *M, cudaStream_t s) {
-    constexpr size_t row = (size_t)32 * p2m_row_stride<T, P>() * sizeof(T);
-    const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (96 * 1024) / row));
-    const size_t sm = warps * row;
-    auto kern = k_p2m_c<T, SRC, P>;
-    set_smem<T>(kern, sm);
-    kern<<<t.nleaf, warps * 32, sm, s>>>(tv, strec, cs, inv_h, M);
-    BEM_CHECK_LAUNCH();
-}
-
-template <class T, int SRC, int P = 1>
-static void p2m_launch(const Tree &t, const TreeView &tv, const typename V4T<T>::t *strec, int p, int cs,
-                       T inv_h, T *M, cudaStream_t s) {
-    if constexpr (P <= MAXP) {
-        if (p == P) p2m_launch_c<T, SRC, P>(t, tv, strec, cs, inv_h, M, s);
-        else p2m_launch<T, SRC, P + 1>(t, tv, strec, p, cs, inv_h, M, s);
-    } else {
-        throw Error(BEM_EINVAL, "expansion order out of range");
-    }
-}
 
 static void ev_rec(Mesh &m, bool timed, int k) {
     if (timed && m.tm.on) BEM_CUDA(cudaEventRecord(m.tm.ev[k], m.stream));
@@ -1616,8 +1464,7 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             set_smem<T>(k_translate<T, TR_BN_TREE>, trsm_t);
         }
         // P2M
-        if (sk == SRC_QUAD) p2m_launch<T, SRC_QUAD>(t, tv, strec, p, cs, inv_h, M, s);
-        else p2m_launch<T, SRC_CHARGE>(t, tv, strec, p, cs, inv_h, M, s);
+        p2m_leaves<T>(tv, t.nleaf, sk, strec, p, cs, inv_h, M, s);
         ev_rec(m, timed, 1);
         // M2M: parents at levels L-1 .. 2
         if (dense) {
@@ -1680,11 +1527,11 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             if (tk == TGT_CEN_DN) {
                 auto kern = k_l2p<T, TGT_CEN_DN>;
                 set_smem<T>(kern, sm);
-                kern<<<t.nleaf, 128, sm, s>>>(tv, trec, nrec, p, cs, inv_h, L, far_b);
+                kern<<<t.nleaf, l2p_threads(ntgt, t.nleaf), sm, s>>>(tv, trec, nrec, p, cs, inv_h, L, far_b);
             } else {
                 auto kern = k_l2p<T, TGT_CHG_PHI>;
                 set_smem<T>(kern, sm);
-                kern<<<t.nleaf, 128, sm, s>>>(tv, trec, nrec, p, cs, inv_h, L, far_b);
+                kern<<<t.nleaf, l2p_threads(ntgt, t.nleaf), sm, s>>>(tv, trec, nrec, p, cs, inv_h, L, far_b);
             }
             BEM_CHECK_LAUNCH();
         }
@@ -1875,7 +1722,7 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
         const size_t sm = (size_t)(p + 1) * (2 * p + 1) * sizeof(cpx<T>);
         auto kern = k_l2p<T, TGT_QUAD_PHI>;
         set_smem<T>(kern, sm);
-        kern<<<t.nleaf, 128, sm, s>>>(tv, B::qp(m), B::nrm(m), p, cs, inv_h, L, far_b);
+        kern<<<t.nleaf, l2p_threads(m.nqp, t.nleaf), sm, s>>>(tv, B::qp(m), B::nrm(m), p, cs, inv_h, L, far_b);
         BEM_CHECK_LAUNCH();
     }
     if (near && !conc) launch_near(s);
@@ -1883,6 +1730,26 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
     k_panel_reduce<T><<<cdiv(m.np, 256), 256, 0, s>>>(far ? far_b : nullptr, near ? near_b : nullptr,
                                                       m.qp_of_panel.p, m.qw64.p, (int)m.nq, m.np, out);
     BEM_CHECK_LAUNCH();
+}
+
+// Whether a kernel (host stub address, as kernel graph nodes report it) is
+// one of the near-field kernels that run on the second, low-priority stream.
+bool is_near_field_kernel(const void *func) {
+    static const void *const near_kernels[] = {
+        reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CEN_DN>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CEN_DN>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CHG_PHI>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CHG_PHI>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CEN_DN>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CEN_DN>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CHG_PHI>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CHG_PHI>),
+        reinterpret_cast<const void *>(k_p2p_t<float>),
+        reinterpret_cast<const void *>(k_p2p_t<double>),
+    };
+    for (const void *k : near_kernels)
+        if (k == func) return true;
+    return false;
 }
 
 void fmm_pass_t(Mesh &m, const double *lam, double *out) {

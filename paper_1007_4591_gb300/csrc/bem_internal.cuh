@@ -272,6 +272,7 @@ void fmm_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const double *dens
 // (dipoles lam_i n_i at the collocation points, potential at the quadrature
 // points, weighted sum over each panel's points).
 void fmm_pass_t(Mesh &m, const double *lam, double *out);
+bool is_near_field_kernel(const void *func);
 
 // Products between the charges and the surface (B q, C sigma): the fast
 // multipole pass on the charge tree, or the direct sum over all pairs,

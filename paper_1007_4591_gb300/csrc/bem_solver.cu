@@ -85,6 +85,27 @@ static void matvec_launch(Mesh &m, const double *xs, double *ys) {
 // The K' product is a fixed sequence of ~20 kernels and memsets; with
 // opt.graph it is captured once (on the buffers gx -> gy, after one ordinary
 // run has set every kernel attribute) and replayed as a single graph launch.
+static cudaError_t set_node_priorities(cudaGraph_t g) {
+    int prio_lo = 0, prio_hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    size_t n = 0;
+    if (e == cudaSuccess) e = cudaGraphGetNodes(g, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess && n > 0) e = cudaGraphGetNodes(g, nodes.data(), &n);
+    for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+        cudaGraphNodeType ty;
+        e = cudaGraphNodeGetType(nodes[i], &ty);
+        if (e != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
+        if (e != cudaSuccess) break;
+        cudaLaunchAttributeValue v{};
+        v.priority = is_near_field_kernel(kp.func) ? prio_lo : prio_hi;
+        e = cudaGraphKernelNodeSetAttribute(nodes[i], cudaLaunchAttributePriority, &v);
+    }
+    return e;
+}
+
 void matvec_sorted(Mesh &m, const double *xs, double *ys) {
     if (!m.opt.graph || m.tm.on) {
         matvec_launch(m, xs, ys);
@@ -109,8 +130,11 @@ void matvec_sorted(Mesh &m, const double *xs, double *ys) {
         }
         m.capturing = false;
         BEM_CUDA(cudaStreamEndCapture(m.stream, &g));
-        // keep the captured streams' priorities on the graph's kernel nodes
-        const cudaError_t e = cudaGraphInstantiateWithFlags(&m.g_mv, g, cudaGraphInstantiateFlagUseNodePriority);
+        // Kernel nodes do not keep their capturing stream's priority: give the
+        // near-field kernels the lowest and every other kernel the highest, so
+        // that the graph runs the two branches as the streams would.
+        cudaError_t e = set_node_priorities(g);
+        if (e == cudaSuccess) e = cudaGraphInstantiateWithFlags(&m.g_mv, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         BEM_CUDA(e);
         return;

@@ -6,15 +6,16 @@
 // this is a GEMM  D[128 x 64] = T_o[128 x 128] . B[128 x 64]  ((p+1)^2 = 121
 // coefficients padded to 128; p <= 10).  It runs as tcgen05.mma kind::tf32
 // with the 3xTF32 split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (tf32 keeps
-// 11 significant bits; the split recovers FP32-level products), operands in
-// shared memory in the canonical K-major layout without swizzle (8 x 16-byte
-// core matrices, K-adjacent cores 128 B apart, 8-row groups 4 KB apart), the
-// accumulator in tensor memory.  One elected thread issues the 48 MMAs of a
-// chunk and commits them to an mbarrier; the four warps then read their 32
-// TMEM lanes (one output coefficient per lane) and add them into the local
-// expansions with coalesced atomics.  Every wait is bounded: on timeout the
-// kernel raises an error flag, waits once more (bounded) for its MMAs and
-// frees its tensor memory before returning.
+// 11 significant bits; the split recovers FP32-level products).  The
+// operator (A) and the accumulators live in tensor memory; the multipoles (B)
+// are staged in shared memory in the canonical K-major layout without
+// swizzle (8 x 16-byte core matrices, K-adjacent cores 128 B apart, 8-row
+// groups 4 KB apart).  A persistent, warp-specialised kernel runs
+// the pairs of one class as a stream of tiles (producers, one MMA thread,
+// epilogue; see k_m2l_tc) and adds each pair's local expansion into its
+// target with one bulk asynchronous reduction.  Every wait is bounded: on
+// timeout the kernel raises an error flag, waits once more (bounded) for its
+// MMAs and frees its tensor memory before returning.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -27,7 +28,7 @@ constexpr int TC_BN = 64;            // pairs per MMA tile (N) = one 64-pair chu
 constexpr int TC_K = 128;            // padded coefficients (K and M)
 constexpr int TC_TMEM_COLS = 512;    // A hi [0,128), A lo [128,256), 4 accumulators of 64
 constexpr int TC_A_HI = 0, TC_A_LO = 128, TC_D0 = 256;
-constexpr int TC_CHUNKS_PER_CTA = 16;
+constexpr int TC_CHUNKS_PER_ITEM = 16;
 constexpr long long TC_WAIT_CYCLES = 2000000000ll;  // about one second of SM clock
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -97,39 +98,47 @@ __device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a, uint64_t b, ui
 // Warp roles of the pipelined kernel.
 constexpr int TC_NS = 3;                       // shared B stages (64 KB each)
 constexpr int TC_ND = 4;                       // TMEM accumulators of TC_BN columns
+constexpr int TC_RING = 16;                    // work items in flight between the roles
 constexpr int TC_WARP_MMA = 0;                 // lane 0 issues the MMAs
 constexpr int TC_WARP_EPI0 = 1;                // warps 1..4: epilogue (TMEM lane quadrant = warp % 4)
-constexpr int TC_WARP_PROD0 = 5;               // warps 5..8: copies of B
+constexpr int TC_WARP_PROD0 = 5;               // warps 5..8: copies of B, operator into TMEM
 constexpr int TC_NPROD = 4 * 32, TC_NEPI = 4 * 32;
 constexpr int TC_THREADS = 9 * 32;
-constexpr int TC_CT_LD = TC_K + 4;             // row pitch of the transposed epilogue tile (floats)
 
-// Work item: (offset class, first 64-pair chunk, number of chunks); a chunk
-// is one tile of 64 pairs.  The operator of the offset class (hi and lo
-// TF32 parts) is written once into tensor memory by the epilogue warps and is
-// the A operand of every MMA.  Pipeline: producers copy the tile's split
-// multipoles into B stage t % 3 (cp.async, tracked by mbarrier fullB); the
-// MMA thread waits for the stage and for accumulator t % 4 to be drained,
-// issues 16 K-steps x 3 products and commits twice (emptyB, fullD); the
-// epilogue warps read their TMEM lane quadrant, release the accumulator,
-// transpose the tile through shared memory and add it into the local
-// expansions with 16-byte vector atomics.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *g, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"(bytes) : "memory");
+}
+
+// The persistent kernel: one CTA per SM takes work items (offset class,
+// first pair, number of pairs: up to TC_CHUNKS_PER_ITEM tiles of 64 pairs)
+// from a global counter, largest first.  Tiles are numbered continuously across a CTA's items, so the
+// pipeline never drains between items:
+//  * producers (warps 5-8): the leader fetches the next item, publishes it
+//    in a shared ring (mbarrier itemFull) and prefetches its operator into
+//    L2; all 128 copy the tiles' split multipoles into B stage t % 3
+//    (cp.async, mbarrier fullB).  After the first tile of an item they wait
+//    for the last MMA of the previous item (its fullD commit) and write the
+//    item's operator (hi | lo TF32 parts) into tensor memory (aReady).
+//  * MMA (warp 0, lane 0): per item waits aReady; per tile waits fullB and a
+//    free accumulator (emptyD), issues 16 K-steps x 3 products with A from
+//    tensor memory and commits to emptyB and fullD.
+//  * epilogue (warps 1-4): reads its TMEM lane quadrant, frees the
+//    accumulator, transposes the tile into shared memory rows (one local
+//    expansion row of cs floats per pair) and adds each row into its target
+//    with one bulk asynchronous reduction (cp.reduce.async.bulk .add.f32).
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
-         const int4 *__restrict__ super, const int4 *__restrict__ chunks,
-         const int *__restrict__ p_out, const int *__restrict__ p_in, int nc, int cs,
+         const int4 *__restrict__ items, int nitems, int *__restrict__ next_item,
+         const int *__restrict__ p_out, const int *__restrict__ p_in, int cs,
          const float *__restrict__ Mtc, float *__restrict__ Lout, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     float *Bbuf = reinterpret_cast<float *>(smraw);            // [TC_NS][hi, lo][TC_BN * TC_K]
-    float *Ct = Bbuf + (size_t)TC_NS * 2 * TC_BN * TC_K;       // [TC_BN][TC_CT_LD]
+    float *Ct = Bbuf + (size_t)TC_NS * 2 * TC_BN * TC_K;       // [TC_BN][cs]
     __shared__ __align__(8) uint64_t fullB[TC_NS], emptyB[TC_NS], fullD[TC_ND], emptyD[TC_ND];
+    __shared__ __align__(8) uint64_t aReady, itemFull[TC_RING];
+    __shared__ int4 s_item[TC_RING];
     __shared__ uint32_t s_tmem;
-    __shared__ int s_fail;
-    __shared__ int4 s_ch[TC_CHUNKS_PER_CTA];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int4 sc = super[blockIdx.x];
-    const int ntile = sc.z;
-    if (tid < sc.z) s_ch[tid] = chunks[sc.y + tid];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(TC_TMEM_COLS));
@@ -144,190 +153,278 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
             mbar_init(smem_u32(&fullD[i]), 1);
             mbar_init(smem_u32(&emptyD[i]), TC_NEPI);
         }
-        s_fail = 0;
+        mbar_init(smem_u32(&aReady), TC_NPROD);
+        for (int i = 0; i < TC_RING; ++i) mbar_init(smem_u32(&itemFull[i]), 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tm = s_tmem;
-    // the operator of this offset class into tensor memory: lane = output
-    // coefficient (row), column = input coefficient; hi part at TC_A_HI, lo at TC_A_LO
-    if (warp >= TC_WARP_EPI0 && warp < TC_WARP_EPI0 + 4) {
-        const int quad = warp & 3, row = 32 * quad + lane;
-        const float *gh = Ahi_all + ((size_t)sc.x * TC_K + row) * TC_K;
-        const float *gl = Alo_all + ((size_t)sc.x * TC_K + row) * TC_K;
-#pragma unroll 1
-        for (int half = 0; half < 2; ++half) {
-            const float *g = half ? gl : gh;
-            const uint32_t col0 = half ? TC_A_LO : TC_A_HI;
-#pragma unroll 1
-            for (int c0 = 0; c0 < TC_K; c0 += 32) {
-                uint32_t v[32];
-#pragma unroll
-                for (int q = 0; q < 32; q += 4) {
-                    const float4 f = __ldg(reinterpret_cast<const float4 *>(g + c0 + q));
-                    v[q] = __float_as_uint(f.x);
-                    v[q + 1] = __float_as_uint(f.y);
-                    v[q + 2] = __float_as_uint(f.z);
-                    v[q + 3] = __float_as_uint(f.w);
-                }
-                asm volatile(
-                    "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-                    "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(
-                        tm + ((uint32_t)(32 * quad) << 16) + col0 + (uint32_t)c0),
-                    "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
-                    "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
-                    "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),
-                    "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),
-                    "r"(v[29]), "r"(v[30]), "r"(v[31]));
-            }
-        }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    int ntile_done = 0;  // tiles whose MMAs were issued (MMA thread)
 
     if (warp >= TC_WARP_PROD0) {
-        // ---------------- producers: asynchronous copies of the split multipoles
-        // (hi | lo rows of Mtc) into stage t % TC_NS; each thread's copies are
-        // tracked by the stage's mbarrier (cp.async.mbarrier.arrive.noinc)
+        // ---------------- producers
         const int ptid = tid - TC_WARP_PROD0 * 32;
+        const int quad = warp & 3, row = 32 * quad + lane;  // TMEM lane of this thread
         constexpr int PER = TC_BN * (TC_K / 4) / TC_NPROD;  // 16-byte chunks per producer and half
         constexpr int NR = PER / 2;                          // rows per producer thread (e >> 8 = u >> 1)
-        int srcs[NR], nxt[NR];
-        auto load_srcs = [&](int t, int *dst) {  // rows n = 8 v + (ptid & 7)
-            const int4 ch = s_ch[t];
-#pragma unroll
-            for (int v = 0; v < NR; ++v) {
-                const int n = 8 * v + (ptid & 7);
-                dst[v] = (n < ch.z) ? p_in[ch.y + n] : -1;
+        // every wait is made warp-uniform (__all_sync) and every item starts with
+        // a vote of all producers, so that on a timeout they leave together
+        bool fail = false;
+        int t = 0;
+        for (int i = 0;; ++i) {
+            const int slot = i % TC_RING;
+            uint32_t all_ok;
+            asm volatile(
+                "{\n .reg .pred p, q;\n setp.eq.u32 p, %1, 0;\n bar.red.and.pred q, 2, %2, p;\n"
+                " selp.u32 %0, 1, 0, q;\n}\n"
+                : "=r"(all_ok)
+                : "r"((uint32_t)fail), "n"(TC_NPROD));
+            if (!all_ok) break;
+            if (ptid == 0) {
+                const int idx = atomicAdd(next_item, 1);
+                const int4 it = idx < nitems ? items[idx] : make_int4(-1, 0, 0, 0);
+                if (it.x >= 0) {
+                    bulk_prefetch_l2(Ahi_all + (size_t)it.x * TC_K * TC_K, TC_K * TC_K * 4);
+                    bulk_prefetch_l2(Alo_all + (size_t)it.x * TC_K * TC_K, TC_K * TC_K * 4);
+                }
+                s_item[slot] = it;
+                mbar_arrive(smem_u32(&itemFull[slot]));
             }
-        };
-        if (ntile > 0) load_srcs(0, srcs);
-        for (int t = 0; t < ntile; ++t) {
-            const int st = t % TC_NS, k = t / TC_NS;
-            if (t + 1 < ntile) load_srcs(t + 1, nxt);
-            if (k >= 1 && !mbar_wait_bounded(smem_u32(&emptyB[st]), (uint32_t)((k - 1) & 1))) {
-                atomicExch(err, 1);
-                s_fail = 1;
-                break;
-            }
-            const uint32_t bh = smem_u32(Bbuf + (size_t)st * 2 * TC_BN * TC_K);
-            const uint32_t bl = bh + TC_BN * TC_K * 4;
+            asm volatile("bar.sync 2, %0;" ::"n"(TC_NPROD) : "memory");
+            const int4 sc = s_item[slot];
+            if (sc.x < 0) break;
+            const int ntl = (sc.z + TC_BN - 1) / TC_BN;
+            // source cells of a tile's pairs (rows n = 8 v + (ptid & 7)); the
+            // next tile's are loaded while this one waits and copies
+            auto load_srcs = [&](int c, int *dst) {
+                const int y = sc.y + TC_BN * c, z = min(TC_BN, sc.z - TC_BN * c);
 #pragma unroll
-            for (int u = 0; u < PER; ++u) {
-                const int e = ptid + TC_NPROD * u;           // (n, k4): n = 8 (e >> 8) + (e & 7)
-                const int n = ((e >> 8) << 3) | (e & 7), k4 = (e >> 3) & 31;
-                const int src = srcs[e >> 8];
-                const float *g = Mtc + (size_t)(src >= 0 ? src : 0) * 2 * TC_K + 4 * k4;
-                const uint32_t nb = src >= 0 ? 16u : 0u;  // 0: zero-fill (padding rows)
-                const uint32_t off = 4u * (uint32_t)tc_off(n, 4 * k4);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bh + off), "l"(g), "r"(nb));
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bl + off), "l"(g + TC_K), "r"(nb));
-            }
-            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&fullB[st])) : "memory");
+                for (int v = 0; v < NR; ++v) {
+                    const int n = 8 * v + (ptid & 7);
+                    dst[v] = (n < z) ? p_in[y + n] : -1;
+                }
+            };
+            int srcs[NR], nxt[NR];
+            load_srcs(0, srcs);
+            for (int c = 0; c < ntl; ++c, ++t) {
+                if (c + 1 < ntl) load_srcs(c + 1, nxt);
+                const int st = t % TC_NS, k = t / TC_NS;
+                const bool okB = __all_sync(0xffffffffu, k < 1 || mbar_wait_bounded(smem_u32(&emptyB[st]),
+                                                                                   (uint32_t)((k - 1) & 1)));
+                if (!okB) {
+                    atomicExch(err, 1);
+                    fail = true;
+                    break;
+                }
+                const uint32_t bh = smem_u32(Bbuf + (size_t)st * 2 * TC_BN * TC_K);
+                const uint32_t bl = bh + TC_BN * TC_K * 4;
 #pragma unroll
-            for (int v = 0; v < NR; ++v) srcs[v] = nxt[v];
+                for (int u = 0; u < PER; ++u) {
+                    const int e = ptid + TC_NPROD * u;           // (n, k4): n = 8 (e >> 8) + (e & 7)
+                    const int n = ((e >> 8) << 3) | (e & 7), k4 = (e >> 3) & 31;
+                    const int src = srcs[u >> 1];  // = e >> 8, as ptid < 128
+                    const float *g = Mtc + (size_t)(src >= 0 ? src : 0) * 2 * TC_K + 4 * k4;
+                    const uint32_t nb = src >= 0 ? 16u : 0u;  // 0: zero-fill (padding rows)
+                    const uint32_t off = 4u * (uint32_t)tc_off(n, 4 * k4);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bh + off), "l"(g), "r"(nb));
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bl + off), "l"(g + TC_K), "r"(nb));
+                }
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&fullB[st])) : "memory");
+                if (c == 0) {
+                    // the item's operator into tensor memory, once the previous
+                    // item's MMAs (which read the old one) have completed
+                    const int tp = t - 1;
+                    const bool okA = __all_sync(0xffffffffu, t < 1 || mbar_wait_bounded(smem_u32(&fullD[tp % TC_ND]),
+                                                                                       (uint32_t)((tp / TC_ND) & 1)));
+                    if (!okA) {
+                        atomicExch(err, 1);
+                        fail = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const float *gh = Ahi_all + ((size_t)sc.x * TC_K + row) * TC_K;
+                    const float *gl = Alo_all + ((size_t)sc.x * TC_K + row) * TC_K;
+#pragma unroll 1
+                    for (int part = 0; part < 4; ++part) {
+                        const float *g = (part < 2 ? gh : gl) + (part & 1) * 64;
+                        const uint32_t col = (part < 2 ? TC_A_HI : TC_A_LO) + (part & 1) * 64;
+                        uint32_t v[64];
+#pragma unroll
+                        for (int q = 0; q < 64; q += 4) {
+                            const float4 f = __ldg(reinterpret_cast<const float4 *>(g + q));
+                            v[q] = __float_as_uint(f.x);
+                            v[q + 1] = __float_as_uint(f.y);
+                            v[q + 2] = __float_as_uint(f.z);
+                            v[q + 3] = __float_as_uint(f.w);
+                        }
+#pragma unroll
+                        for (int h = 0; h < 64; h += 32) {
+                            asm volatile(
+                                "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                                "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(
+                                    tm + ((uint32_t)(32 * quad) << 16) + col + (uint32_t)h),
+                                "r"(v[h + 0]), "r"(v[h + 1]), "r"(v[h + 2]), "r"(v[h + 3]), "r"(v[h + 4]),
+                                "r"(v[h + 5]), "r"(v[h + 6]), "r"(v[h + 7]), "r"(v[h + 8]), "r"(v[h + 9]),
+                                "r"(v[h + 10]), "r"(v[h + 11]), "r"(v[h + 12]), "r"(v[h + 13]), "r"(v[h + 14]),
+                                "r"(v[h + 15]), "r"(v[h + 16]), "r"(v[h + 17]), "r"(v[h + 18]), "r"(v[h + 19]),
+                                "r"(v[h + 20]), "r"(v[h + 21]), "r"(v[h + 22]), "r"(v[h + 23]), "r"(v[h + 24]),
+                                "r"(v[h + 25]), "r"(v[h + 26]), "r"(v[h + 27]), "r"(v[h + 28]), "r"(v[h + 29]),
+                                "r"(v[h + 30]), "r"(v[h + 31]));
+                        }
+                    }
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    mbar_arrive(smem_u32(&aReady));
+                }
+#pragma unroll
+                for (int v = 0; v < NR; ++v) srcs[v] = nxt[v];
+            }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == TC_WARP_MMA) {
         // ---------------- MMA issue (one thread)
         if (lane == 0) {
             const uint32_t SBO = (TC_K / 4) * 128, LBO = 128;
-            for (int t = 0; t < ntile; ++t) {
-                const int st = t % TC_NS, k = t / TC_NS;
-                const int d = t % TC_ND, jd = t / TC_ND;
-                bool ok = mbar_wait_bounded(smem_u32(&fullB[st]), (uint32_t)(k & 1));
-                if (ok && jd >= 1) ok = mbar_wait_bounded(smem_u32(&emptyD[d]), (uint32_t)((jd - 1) & 1));
-                if (!ok) {
+            bool fail = false;
+            int t = 0;
+            for (int i = 0; !fail; ++i) {
+                const int slot = i % TC_RING;
+                if (!mbar_wait_bounded(smem_u32(&itemFull[slot]), (uint32_t)((i / TC_RING) & 1))) {
                     atomicExch(err, 1);
-                    s_fail = 1;
                     break;
                 }
-                // the stage was written by cp.async (generic proxy): order it before
-                // the tensor core's (async proxy) reads
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t bh = smem_u32(Bbuf + (size_t)st * 2 * TC_BN * TC_K);
-                const uint32_t bl = bh + TC_BN * TC_K * 4;
-                const uint32_t dt = tm + (uint32_t)(TC_D0 + d * TC_BN);
-#pragma unroll 4
-                for (int ks = 0; ks < TC_K / 8; ++ks) {
-                    const uint32_t ko = (uint32_t)ks * 2 * LBO;
-                    const uint64_t dbh = tc_desc(bh + ko, LBO, SBO), dbl = tc_desc(bl + ko, LBO, SBO);
-                    const uint32_t ah = tm + TC_A_HI + 8u * ks, al = tm + TC_A_LO + 8u * ks;
-                    tc_mma_ts(dt, ah, dbh, ks > 0 ? 1u : 0u);
-                    tc_mma_ts(dt, ah, dbl, 1u);
-                    tc_mma_ts(dt, al, dbh, 1u);
+                const int4 sc = s_item[slot];
+                if (sc.x < 0) break;
+                if (!mbar_wait_bounded(smem_u32(&aReady), (uint32_t)(i & 1))) {
+                    atomicExch(err, 1);
+                    break;
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(&emptyB[st]))
-                             : "memory");
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(&fullD[d]))
-                             : "memory");
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const int ntl = (sc.z + TC_BN - 1) / TC_BN;
+                for (int c = 0; c < ntl; ++c, ++t) {
+                    const int st = t % TC_NS, k = t / TC_NS;
+                    const int d = t % TC_ND, jd = t / TC_ND;
+                    bool ok = mbar_wait_bounded(smem_u32(&fullB[st]), (uint32_t)(k & 1));
+                    if (ok && jd >= 1) ok = mbar_wait_bounded(smem_u32(&emptyD[d]), (uint32_t)((jd - 1) & 1));
+                    if (!ok) {
+                        atomicExch(err, 1);
+                        fail = true;
+                        break;
+                    }
+                    // the stage was written by cp.async (generic proxy): order it before
+                    // the tensor core's (async proxy) reads
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t bh = smem_u32(Bbuf + (size_t)st * 2 * TC_BN * TC_K);
+                    const uint32_t bl = bh + TC_BN * TC_K * 4;
+                    const uint32_t dt = tm + (uint32_t)(TC_D0 + d * TC_BN);
+#pragma unroll 4
+                    for (int ks = 0; ks < TC_K / 8; ++ks) {
+                        const uint32_t ko = (uint32_t)ks * 2 * LBO;
+                        const uint64_t dbh = tc_desc(bh + ko, LBO, SBO), dbl = tc_desc(bl + ko, LBO, SBO);
+                        const uint32_t ah = tm + TC_A_HI + 8u * ks, al = tm + TC_A_LO + 8u * ks;
+                        tc_mma_ts(dt, ah, dbh, ks > 0 ? 1u : 0u);
+                        tc_mma_ts(dt, ah, dbl, 1u);
+                        tc_mma_ts(dt, al, dbh, 1u);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&emptyB[st]))
+                                 : "memory");
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&fullD[d]))
+                                 : "memory");
+                }
             }
+            ntile_done = t;
         }
     } else {
         // ---------------- epilogue: TMEM lane quadrant (warp % 4), 64 pairs per tile
         const int quad = warp & 3;
         const int row = 32 * quad + lane;
-        const int etid = tid - TC_WARP_EPI0 * 32;  // 0..127
-        for (int t = 0; t < ntile; ++t) {
-            const int d = t % TC_ND, jd = t / TC_ND;
-            const bool ok = mbar_wait_bounded(smem_u32(&fullD[d]), (uint32_t)(jd & 1));
-            // the four epilogue warps leave together (they meet at named barriers below)
+        const bool issuer = warp == TC_WARP_EPI0;  // its lanes issue the bulk reductions
+        bool fail = false;
+        int t = 0;
+        for (int i = 0; !fail; ++i) {
+            const int slot = i % TC_RING;
+            const bool okI = mbar_wait_bounded(smem_u32(&itemFull[slot]), (uint32_t)((i / TC_RING) & 1));
             uint32_t all_ok;
             asm volatile(
                 "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
                 " selp.u32 %0, 1, 0, q;\n}\n"
                 : "=r"(all_ok)
-                : "r"((uint32_t)ok), "n"(TC_NEPI));
+                : "r"((uint32_t)okI), "n"(TC_NEPI));
             if (!all_ok) {
                 atomicExch(err, 1);
-                s_fail = 1;
                 break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            uint32_t r[TC_BN];
-#pragma unroll
-            for (int cg = 0; cg < TC_BN; cg += 16) {
+            const int4 sc = s_item[slot];
+            if (sc.x < 0) break;
+            const int ntl = (sc.z + TC_BN - 1) / TC_BN;
+            for (int c = 0; c < ntl; ++c, ++t) {
+                const int d = t % TC_ND, jd = t / TC_ND;
+                const bool ok = mbar_wait_bounded(smem_u32(&fullD[d]), (uint32_t)(jd & 1));
+                // the four epilogue warps leave together (they meet at named barriers below)
                 asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                    : "=r"(r[cg + 0]), "=r"(r[cg + 1]), "=r"(r[cg + 2]), "=r"(r[cg + 3]), "=r"(r[cg + 4]),
-                      "=r"(r[cg + 5]), "=r"(r[cg + 6]), "=r"(r[cg + 7]), "=r"(r[cg + 8]), "=r"(r[cg + 9]),
-                      "=r"(r[cg + 10]), "=r"(r[cg + 11]), "=r"(r[cg + 12]), "=r"(r[cg + 13]),
-                      "=r"(r[cg + 14]), "=r"(r[cg + 15])
-                    : "r"(tm + ((uint32_t)(32 * quad) << 16) + (uint32_t)(TC_D0 + d * TC_BN + cg)));
-            }
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            mbar_arrive(smem_u32(&emptyD[d]));
-            // transpose through shared memory: Ct[pair][coefficient]
-            asm volatile("bar.sync 1, %0;" ::"n"(TC_NEPI));  // previous tile's reads of Ct done
+                    "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
+                    " selp.u32 %0, 1, 0, q;\n}\n"
+                    : "=r"(all_ok)
+                    : "r"((uint32_t)ok), "n"(TC_NEPI));
+                if (!all_ok) {
+                    atomicExch(err, 1);
+                    fail = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                uint32_t r[TC_BN];
 #pragma unroll
-            for (int j = 0; j < TC_BN; ++j) Ct[j * TC_CT_LD + row] = __uint_as_float(r[j]);
-            asm volatile("bar.sync 1, %0;" ::"n"(TC_NEPI));
-            const int4 ch = s_ch[t];
-            const int n4 = (nc + 3) >> 2;  // float4 groups per row (the last one spills into the stride padding)
-            for (int e = etid; e < ch.z * n4; e += TC_NEPI) {
-                const int j = e / n4, c4 = e - j * n4;
-                const float4 v = *reinterpret_cast<const float4 *>(Ct + j * TC_CT_LD + 4 * c4);
-                float4 *o = reinterpret_cast<float4 *>(Lout + (size_t)p_out[ch.y + j] * cs + 4 * c4);
-                atomicAdd(o, v);
+                for (int cg = 0; cg < TC_BN; cg += 16) {
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(r[cg + 0]), "=r"(r[cg + 1]), "=r"(r[cg + 2]), "=r"(r[cg + 3]), "=r"(r[cg + 4]),
+                          "=r"(r[cg + 5]), "=r"(r[cg + 6]), "=r"(r[cg + 7]), "=r"(r[cg + 8]), "=r"(r[cg + 9]),
+                          "=r"(r[cg + 10]), "=r"(r[cg + 11]), "=r"(r[cg + 12]), "=r"(r[cg + 13]),
+                          "=r"(r[cg + 14]), "=r"(r[cg + 15])
+                        : "r"(tm + ((uint32_t)(32 * quad) << 16) + (uint32_t)(TC_D0 + d * TC_BN + cg)));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                mbar_arrive(smem_u32(&emptyD[d]));
+                // the previous tile's bulk reductions have finished reading Ct
+                if (issuer) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                asm volatile("bar.sync 1, %0;" ::"n"(TC_NEPI) : "memory");
+                if (row < cs) {
+#pragma unroll
+                    for (int j = 0; j < TC_BN; ++j) Ct[j * cs + row] = __uint_as_float(r[j]);
+                }
+                // generic-proxy writes of Ct before the bulk copies (async proxy) read it
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("bar.sync 1, %0;" ::"n"(TC_NEPI) : "memory");
+                if (issuer) {
+                    const int y = sc.y + TC_BN * c, z = min(TC_BN, sc.z - TC_BN * c);
+                    for (int j = lane; j < z; j += 32) {
+                        float *dst = Lout + (size_t)p_out[y + j] * cs;
+                        asm volatile(
+                            "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
+                            "r"(smem_u32(Ct + j * cs)), "r"((uint32_t)cs * 4u)
+                            : "memory");
+                    }
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
             }
         }
+        if (issuer) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     // before the CTA's shared memory and tensor memory go away, every commit
     // arrival must have landed: the MMA thread waits (bounded) for the last
     // completion of each B stage and of the last accumulator
-    if (warp == TC_WARP_MMA && lane == 0 && ntile > 0) {
-        for (int st = 0; st < TC_NS && st < ntile; ++st) {
-            const int t = st + ((ntile - 1 - st) / TC_NS) * TC_NS;  // last tile on stage st
+    if (warp == TC_WARP_MMA && lane == 0 && ntile_done > 0) {
+        const int nt = ntile_done;
+        for (int st = 0; st < TC_NS && st < nt; ++st) {
+            const int t = st + ((nt - 1 - st) / TC_NS) * TC_NS;  // last tile on stage st
             mbar_wait_bounded(smem_u32(&emptyB[st]), (uint32_t)((t / TC_NS) & 1));
         }
-        const int t = ntile - 1;
+        const int t = nt - 1;
         mbar_wait_bounded(smem_u32(&fullD[t % TC_ND]), (uint32_t)((t / TC_ND) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -374,19 +471,22 @@ bool tc_m2l_available(const Mesh &m) {
     return m.opt.precision == BEM_MIXED && (m.opt.p + 1) * (m.opt.p + 1) <= TC_K;
 }
 
-size_t tc_smem_bytes() { return (size_t)(2 * TC_NS * TC_BN * TC_K + TC_BN * TC_CT_LD) * sizeof(float); }
+size_t tc_smem_bytes() { return (size_t)(2 * TC_NS * TC_BN * TC_K + TC_BN * TC_K) * sizeof(float); }
 
-// super-chunks: up to TC_CHUNKS_PER_CTA consecutive M2L chunks of one offset class
+// Work items of the persistent kernel: (offset class, first pair, number of
+// pairs), up to TC_CHUNKS_PER_ITEM consecutive 64-pair chunks of one class,
+// largest first.
 void build_tc_super(Tree &t, const std::vector<int4> &chunks_m2l, cudaStream_t s) {
     std::vector<int4> sup;
     int i = 0;
     const int n = (int)chunks_m2l.size();
-    while (i < n) {
-        int j = i + 1;
-        while (j < n && j - i < TC_CHUNKS_PER_CTA && chunks_m2l[j].x == chunks_m2l[i].x) ++j;
-        sup.push_back(make_int4(chunks_m2l[i].x, i, j - i, 0));
+    while (i < n) {  // chunks of one class cover consecutive pairs
+        int j = i + 1, np = chunks_m2l[i].z;
+        while (j < n && j - i < TC_CHUNKS_PER_ITEM && chunks_m2l[j].x == chunks_m2l[i].x) np += chunks_m2l[j++].z;
+        sup.push_back(make_int4(chunks_m2l[i].x, chunks_m2l[i].y, np, 0));
         i = j;
     }
+    std::stable_sort(sup.begin(), sup.end(), [](const int4 &a, const int4 &b) { return a.z > b.z; });
     t.tc_super.alloc(sup.size());
     t.tc_nsuper = (int)sup.size();
     if (!sup.empty())
@@ -417,9 +517,14 @@ void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L) {
     BEM_CHECK_LAUNCH();
     const size_t sm = tc_smem_bytes();
     ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc), sm);
-    k_m2l_tc<<<t.tc_nsuper, TC_THREADS, sm, m.stream>>>(m.tab->Tc_hi.p, m.tab->Tc_lo.p, t.tc_super.p,
-                                                         t.g_chunk.p + t.m2l_chunk0, t.g_out.p, t.g_in.p, nc,
-                                                         cs, m.Mtc.p, L, m.dev_err.p);
+    int dev = 0, nsm = 0;
+    BEM_CUDA(cudaGetDevice(&dev));
+    BEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = std::max(1, std::min(t.tc_nsuper, nsm));
+    BEM_CUDA(cudaMemsetAsync(m.dev_err.p + 1, 0, sizeof(int), m.stream));  // work-item counter
+    k_m2l_tc<<<grid, TC_THREADS, sm, m.stream>>>(m.tab->Tc_hi.p, m.tab->Tc_lo.p, t.tc_super.p, t.tc_nsuper,
+                                                 m.dev_err.p + 1, t.g_out.p, t.g_in.p, cs, m.Mtc.p, L,
+                                                 m.dev_err.p);
     BEM_CHECK_LAUNCH();
 }
 
