@@ -121,13 +121,13 @@ def _max_over_ranks(v, ws):
     return float(t.item())
 
 
-def _traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
+def _traffic(kernel):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
     capture, or None when the kernel's source changed since the capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
-            rec = json.load(f)
+            rec = json.load(f)[kernel]
         with open(os.path.join(ROOT, rec["source_file"]), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
                 return None
@@ -288,7 +288,9 @@ def run_ours(args):
     t_ms = _max_over_ranks(t_ms, ws)
     value = ws * n * args.steps / (t_ms * 1e-3) / 1e6
 
-    # roofline of the dominant kernel (P2P): phase events on the library's stream
+    # rooflines of the two large kernels from phase events on the library's
+    # stream (phases run one after another in this mode); the dominant one is
+    # the "roofline" entry
     pkg.bem_set_profiling(mesh.h, True)
     phases = []
     for _ in range(max(3, min(args.steps, 10))):
@@ -301,13 +303,39 @@ def run_ours(args):
     f_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * f_mhz * 1e6 / 1e12
     p2p_flops = 20.0 * info["p2p_pairs"]
-    achieved = p2p_flops / (ph["p2p"] * 1e-3) / 1e12 if ph["p2p"] > 0 else 0.0
-    roofline = {"kernel": "k_p2p (near-field panel quadrature)", "bound": "alu",
-                "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": _traffic(),
-                "peak_source": f"FP32: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                               f"{f_mhz:.0f} MHz (sm_max_mhz from MEASURED_PEAKS.json, {src})",
-                "algorithmic": f"20 flop x {info['p2p_pairs']} (collocation point, source point) pairs"}
+    rl_p2p = {"kernel": "k_p2p (near-field panel quadrature)", "bound": "alu",
+              "achieved": round(p2p_flops / (ph["p2p"] * 1e-3) / 1e12, 3), "peak": round(fp32_peak, 2),
+              "unit": "TFLOP/s", "traffic": _traffic("k_p2p"), "time_ms": round(ph["p2p"], 4),
+              "peak_source": f"FP32: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                             f"{f_mhz:.0f} MHz (sm_max_mhz from MEASURED_PEAKS.json, {src})",
+              "algorithmic": f"20 flop x {info['p2p_pairs']} (collocation point, source point) pairs"}
+    rl_p2p["frac"] = round(rl_p2p["achieved"] / fp32_peak, 4)
+    # M2L: credited with the rotation-form count (8,866 flop per translation at
+    # p = 10), not the dense 121 x 121 product the kernel executes; peak = the
+    # dense TF32 tensor rate, the measured bf16 rate x the nominal 1.1 / 2.25
+    p = args.p
+    m2l_unit = 2 * (2 * (p + 1) * (2 * p + 1) * (2 * p + 3) / 3 + (p + 1) ** 2 + p * (p + 1) * (2 * p + 1) / 3)
+    m2l_flops = m2l_unit * info["m2l_pairs"]
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    tf32_peak = bf16 * 1.1 / 2.25
+    rl_m2l = {"kernel": "k_m2l_tc (tensor-core M2L; stage time incl. k_split_m and the L memset)",
+              "bound": "tensor", "achieved": round(m2l_flops / (ph["m2l"] * 1e-3) / 1e12, 3),
+              "peak": round(tf32_peak, 1), "unit": "TFLOP/s", "traffic": _traffic("k_m2l_tc"),
+              "time_ms": round(ph["m2l"], 4),
+              "peak_source": f"dense TF32 = bf16 {bf16:.1f} TFLOP/s (MEASURED_PEAKS.json, {src}) x 1.1/2.25",
+              "algorithmic": f"{m2l_unit:.0f} flop (rotation-form count, p={p}) x {info['m2l_pairs']} translations"}
+    rl_m2l["frac"] = round(rl_m2l["achieved"] / tf32_peak, 4)
+    roofline = dict(rl_m2l if ph["m2l"] >= ph["p2p"] else rl_p2p)
+    # the whole product: algorithmic flops of every stage / (time x FP32 peak)
+    nq = info["source_points"]
+    mm_unit = m2l_unit
+    alg = (p2p_flops + m2l_flops + mm_unit * 2 * info["m2m_pairs"] + 8 * (p + 1) ** 2 * nq
+           + 12 * (p + 1) ** 2 * n)
+    matvec_roofline = {"algorithmic_gflop": round(alg / 1e9, 3),
+                       "achieved_tflops": round(alg / (t_ms / args.steps * 1e-3) / 1e12, 3),
+                       "frac_of_fp32_peak": round(alg / (t_ms / args.steps * 1e-3) / 1e12 / fp32_peak, 4),
+                       "counts": "P2P 20/pair, M2L and M2M/L2L 8,866/translation (p=10), "
+                                 "P2M 8(p+1)^2/source point, L2P 12(p+1)^2/target"}
 
     # end to end through the C-ABI with host buffers
     xh = np.ascontiguousarray(x.cpu().numpy())
@@ -358,13 +386,68 @@ def run_ours(args):
             "phases_ms": {k: round(v, 4) for k, v in ph.items()},
             "tree_build_s": round(tree_s, 4),
             "solve_s": round(solve_s, 4), "solve_iters": st["iterations"], "dG_kcal": dg,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "roofline_kernels": {"p2p": rl_p2p, "m2l": rl_m2l},
+            "matvec_roofline": matvec_roofline, "cpu_baseline": cpu, "e2e": e2e,
             "precision_comparison": prec_cmp,
             "gpu_launches": launches_per * args.steps, "clocks": clocks,
         }))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_batch(args):
+    """Batched uneven molecules: 64 spheres (R ~ U[10, 25] A, subdivisions
+    5-7, 500-4,000 charges, seed 4), (leaf size, p) autotuned once per
+    subdivision level on its first molecule, then one bem_batch_solve giving
+    the full solve and both BIBEE bounds of every molecule."""
+    import torch
+    import synth
+    import paper_1007_4591_gb300 as pkg
+    torch.cuda.set_device(0)
+    pkg.load_library()
+    mols = synth.batch(64, seed=4)
+    tuned = {}
+    t0 = time.perf_counter()
+    for m in mols:
+        s = m.name.split("-s")[-1]
+        if s not in tuned:
+            o = pkg.bem_autotune(np.ascontiguousarray(m.panels), np.ascontiguousarray(m.charges),
+                                 m.eps_in, m.eps_out, target=1e-5)
+            tuned[s] = (int(o.leaf_size), int(o.p))
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    meshes = []
+    for m in mols:
+        leaf, p = tuned[m.name.split("-s")[-1]]
+        meshes.append(pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=p, leaf_size=leaf,
+                               precision=0, tol=1e-8))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    n_p = sum(m.n_p for m in mols)
+    times = []
+    for it in range(max(1, args.warmup) + max(1, args.steps)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        dg, dc, dpb, st = pkg.bem_batch_solve(meshes, threads=8)
+        torch.cuda.synchronize()
+        if it >= max(1, args.warmup):
+            times.append(time.perf_counter() - t1)
+    ok = all(s["converged"] == 1 for s in st) and all(p_ < g < c for g, c, p_ in zip(dg, dc, dpb))
+    t = float(np.median(times))
+    print(json.dumps({
+        "metric": "batched FMM-BEM solve + BIBEE bounds, panels solved per second",
+        "value": round(n_p / t / 1e6, 3), "unit": "Mpanels/s", "n_gpus": 1, "steps": len(times),
+        "warmup": max(1, args.warmup), "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "batch64 (64 spheres, R ~ U[10,25] A, icosphere subdivisions 5-7, "
+                               "500-4,000 charges, eps 4/80, seed 4)",
+                   "molecules": len(mols), "panels": n_p, "tuned_leaf_p_by_subdivision": tuned,
+                   "gmres_tol": 1e-8, "threads": 8},
+        "batch_solve_s": round(t, 4), "autotune_s": round(tune_s, 2), "mesh_build_s": round(build_s, 2),
+        "all_converged_and_bounded": bool(ok),
+        "gmres_iters_max": int(max(s["iterations"] for s in st))}), flush=True)
+    for g in meshes:
+        g.close()
 
 
 def main():
@@ -382,8 +465,13 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--workload", default="globular-s6", choices=["globular-s6", "batch64"],
+                    help="globular-s6: the K' product and solve (default); batch64: 64 uneven "
+                         "molecules solved with their BIBEE bounds in one batched call")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.workload == "batch64":
+        run_batch(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

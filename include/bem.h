@@ -196,8 +196,9 @@ int bem_energy_backward(bem_mesh *mesh, double grad_out, double *dq, double *dx)
  *   sigma[i] ([n_p of mesh i] f64, host or device) may be NULL (array or entry),
  *   dG, dG_cfa, dG_p [n] host arrays, each may be NULL; stats [n] may be NULL.
  * Returns the first hard error, else BEM_ENOCONV if any solve did not converge.
- * The SURVEY's single persistent launch is replaced by concurrent streams and
- * captured per-mesh graphs (no paper counterpart: the paper solves one system). */
+ * The molecules run concurrently, each on its own prioritised streams (and,
+ * with opt.graph, as its own captured graph) rather than as one persistent
+ * launch over all of them (no paper counterpart: the paper solves one system). */
 int bem_batch_solve(bem_mesh *const *meshes, int n, int threads, double *const *sigma, double *dG,
                     double *dG_cfa, double *dG_p, bem_solve_stats *stats);
 

@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
 
-Tolerances (the benchmark spec): relative L2 error of the operator product <= 1e-5
-and of solvation energies <= 1e-5 in the mixed FP32/FP64 mode; the FP64 mode
+Tolerances: relative L2 error of the operator product <= 1e-5 and of
+solvation energies <= 1e-5 in the mixed FP32/FP64 mode; the FP64 mode
 of the near field alone agrees with the dense FP64 sum to roundoff.
 """
 import numpy as np
