@@ -391,20 +391,27 @@ template <> struct Pk<double> {
 template <class T> struct P2PTpt;
 template <> struct P2PTpt<float> { static constexpr int v = 4; };
 template <> struct P2PTpt<double> { static constexpr int v = 2; };
-constexpr int P2P_TILE = 2 * P2P_THREADS;
+// Forward kernel: CTA size NT (128 for leaves of a few dozen targets, 256
+// above) and sources fetched per thread for each shared tile (8 in FP32: few
+// barriers per source; 2 in FP64 to stay within static shared memory).
+template <class T> struct P2PFpt;
+template <> struct P2PFpt<float> { static constexpr int v = 8; };
+template <> struct P2PFpt<double> { static constexpr int v = 2; };
 
-template <class T, int SRC, int TGT>
-__global__ void __launch_bounds__(P2P_THREADS)
+template <class T, int SRC, int TGT, int P2PF_THREADS>
+__global__ void __launch_bounds__(P2PF_THREADS)
 k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
       const typename V4T<T>::t *src, T h, T *out) {
     using V4 = typename V4T<T>::t;
     using P = Pk<T>;
     using v2 = typename P::v;
     constexpr int P2P_TPT = P2PTpt<T>::v;
-    __shared__ V4 shA[P2P_THREADS], shB[P2P_THREADS];
+    constexpr int P2PF_TILE = P2PF_THREADS * P2PFpt<T>::v;  // sources per tile
+    constexpr int P2PF_PAIRS = P2PF_TILE / 2;
+    __shared__ V4 shA[P2PF_PAIRS], shB[P2PF_PAIRS];
     __shared__ int s_beg[28], s_cum[28];
     __shared__ T s_off[27][3];
-    __shared__ T s_part[P2P_THREADS * 4];
+    __shared__ T s_part[P2PF_THREADS * 4];
     const int leaf = tv.p2p_order[blockIdx.x];  // heaviest leaves first
     const int *tb_ = TGT == TGT_CEN_DN ? tv.cen_beg : tv.chg_beg;
     const int *sb_ = SRC == SRC_QUAD ? tv.qp_beg : tv.chg_beg;
@@ -430,7 +437,7 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
     const int total = s_cum[nn];
     const int ntgt = te - tb;
     const v2 EPS2 = P::mk(P2PEps<T>::v, P2PEps<T>::v);
-    constexpr int MAXT = (P2P_THREADS / 4) * P2P_TPT;  // targets per pass (G >= 4)
+    constexpr int MAXT = (P2PF_THREADS / 4) * P2P_TPT;  // targets per pass (G >= 4)
     // staged source v (0 <= v < total) in the target leaf's frame, or a zero-weight dummy
     auto fetch = [&](int v, T &x, T &y, T &z, T &w) {
         x = y = z = w = 0;
@@ -451,7 +458,7 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
     for (int t0 = 0; t0 < ntgt; t0 += MAXT) {
         const int nt = min(ntgt - t0, MAXT);
         const int ngroups = (nt + P2P_TPT - 1) / P2P_TPT;
-        const int G = P2P_THREADS / ngroups;
+        const int G = P2PF_THREADS / ngroups;
         const int grp = threadIdx.x / G, g = threadIdx.x - grp * G;
         const bool active = grp < ngroups;
         v2 cx[P2P_TPT], cy[P2P_TPT], cz[P2P_TPT], nx[P2P_TPT], ny[P2P_TPT], nz[P2P_TPT];
@@ -480,20 +487,22 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
             nz[q] = P::mk(f, f);
             outer[q] = 0;
         }
-        for (int vb = 0; vb < total; vb += P2P_TILE) {
+        for (int vb = 0; vb < total; vb += P2PF_TILE) {
             __syncthreads();
-            {
+#pragma unroll
+            for (int f = 0; f < P2PF_PAIRS / P2PF_THREADS; ++f) {
+                const int pi = threadIdx.x + f * P2PF_THREADS;
                 T x0, y0, z0, w0, x1, y1, z1, w1;
-                fetch(vb + 2 * threadIdx.x, x0, y0, z0, w0);
-                fetch(vb + 2 * threadIdx.x + 1, x1, y1, z1, w1);
+                fetch(vb + 2 * pi, x0, y0, z0, w0);
+                fetch(vb + 2 * pi + 1, x1, y1, z1, w1);
                 V4 a, b;
                 a.x = x0; a.y = x1; a.z = y0; a.w = y1;
                 b.x = z0; b.y = z1; b.z = w0; b.w = w1;
-                shA[threadIdx.x] = a;
-                shB[threadIdx.x] = b;
+                shA[pi] = a;
+                shB[pi] = b;
             }
             __syncthreads();
-            const int npair = min(P2P_THREADS, (total - vb + 1) >> 1);
+            const int npair = min(P2PF_PAIRS, (total - vb + 1) >> 1);
             if (active) {
                 v2 acc[P2P_TPT];
 #pragma unroll
@@ -1436,14 +1445,20 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
     const bool conc = near && m.stream2 && !(timed && m.tm.on);
     auto launch_near = [&](cudaStream_t ss) {
         const T hh = (T)h;
+        // 128-thread CTAs when the average leaf holds at most 32 targets
+        const bool small = ntgt <= (int64_t)32 * t.nleaf;
+        auto go = [&](auto k128, auto k256) {
+            if (small) k128<<<t.nleaf, 128, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
+            else k256<<<t.nleaf, 256, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
+        };
         if (sk == SRC_QUAD && tk == TGT_CEN_DN)
-            k_p2p<T, SRC_QUAD, TGT_CEN_DN><<<t.nleaf, P2P_THREADS, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
+            go(k_p2p<T, SRC_QUAD, TGT_CEN_DN, 128>, k_p2p<T, SRC_QUAD, TGT_CEN_DN, 256>);
         else if (sk == SRC_CHARGE && tk == TGT_CEN_DN)
-            k_p2p<T, SRC_CHARGE, TGT_CEN_DN><<<t.nleaf, P2P_THREADS, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
+            go(k_p2p<T, SRC_CHARGE, TGT_CEN_DN, 128>, k_p2p<T, SRC_CHARGE, TGT_CEN_DN, 256>);
         else if (sk == SRC_QUAD && tk == TGT_CHG_PHI)
-            k_p2p<T, SRC_QUAD, TGT_CHG_PHI><<<t.nleaf, P2P_THREADS, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
+            go(k_p2p<T, SRC_QUAD, TGT_CHG_PHI, 128>, k_p2p<T, SRC_QUAD, TGT_CHG_PHI, 256>);
         else
-            k_p2p<T, SRC_CHARGE, TGT_CHG_PHI><<<t.nleaf, P2P_THREADS, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
+            go(k_p2p<T, SRC_CHARGE, TGT_CHG_PHI, 128>, k_p2p<T, SRC_CHARGE, TGT_CHG_PHI, 256>);
         BEM_CHECK_LAUNCH();
     };
     if (conc) {
@@ -1736,14 +1751,22 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
 // one of the near-field kernels that run on the second, low-priority stream.
 bool is_near_field_kernel(const void *func) {
     static const void *const near_kernels[] = {
-        reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CEN_DN>),
-        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CEN_DN>),
-        reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CHG_PHI>),
-        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CHG_PHI>),
-        reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CEN_DN>),
-        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CEN_DN>),
-        reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CHG_PHI>),
-        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CHG_PHI>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CEN_DN, 128>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CEN_DN, 256>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CEN_DN, 128>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CEN_DN, 256>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CHG_PHI, 128>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CHG_PHI, 256>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CHG_PHI, 128>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CHG_PHI, 256>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CEN_DN, 128>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CEN_DN, 256>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CEN_DN, 128>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CEN_DN, 256>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CHG_PHI, 128>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CHG_PHI, 256>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CHG_PHI, 128>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CHG_PHI, 256>),
         reinterpret_cast<const void *>(k_p2p_t<float>),
         reinterpret_cast<const void *>(k_p2p_t<double>),
     };
