@@ -1057,18 +1057,29 @@ static std::shared_ptr<Tables> make_tables(int p, int prec) {
         BEM_CUDA(cudaMemcpy(t->Tc_hi.p, hi.data(), hi.size() * sizeof(float), cudaMemcpyHostToDevice));
         BEM_CUDA(cudaMemcpy(t->Tc_lo.p, lo.data(), lo.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
+    // translation operators with each [in] row padded to the cell stride, so
+    // that k_translate stages them with 16-byte copies
+    const int ld = cell_stride(p);
+    auto pad = [&](const std::vector<double> &ops, int nops) {
+        std::vector<double> r((size_t)nops * nc * ld, 0.0);
+        for (size_t o = 0; o < (size_t)nops; ++o)
+            for (int k = 0; k < nc; ++k)
+                std::copy_n(&ops[(o * nc + k) * nc], nc, &r[(o * nc + k) * ld]);
+        return r;
+    };
+    const std::vector<double> pm2l = pad(om2l, NOFFSET), pm2m = pad(om2m, 8), pl2l = pad(ol2l, 8);
     if (prec == BEM_MIXED) {
         upload(t->Rm2m_f, rtab);
         upload(t->If_f, it);
-        upload(t->Om2l_f, om2l);
-        upload(t->Om2m_f, om2m);
-        upload(t->Ol2l_f, ol2l);
+        upload(t->Om2l_f, pm2l);
+        upload(t->Om2m_f, pm2m);
+        upload(t->Ol2l_f, pl2l);
     } else {
         upload(t->Rm2m_d, rtab);
         upload(t->If_d, it);
-        upload(t->Om2l_d, om2l);
-        upload(t->Om2m_d, om2m);
-        upload(t->Ol2l_d, ol2l);
+        upload(t->Om2l_d, pm2l);
+        upload(t->Om2m_d, pm2m);
+        upload(t->Ol2l_d, pl2l);
     }
     return t;
 }
@@ -1094,6 +1105,7 @@ void build_tables(Mesh &m) {
 // shared memory, 8 x 4 outputs per thread, then scattered with coalesced
 // atomic adds (a warp adds 32 consecutive coefficients of one cell).
 constexpr int TR_BM = 128, TR_THREADS = 256;
+constexpr int TR_THREADS_TREE = 128;  // k_translate for M2M / L2L chunks of 16 pairs
 constexpr int TR_BN_M2L = 64;  // pairs per chunk for M2L (many pairs per offset class)
 constexpr int TR_BN_TREE = 16; // pairs per chunk for M2M / L2L (8 operators per level)
 template <class T> struct TrBK;
@@ -1117,26 +1129,38 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// 16-byte copy global -> shared (ok = false writes zero, src-size 0)
+__device__ __forceinline__ void cp_async_16(void *dst, const void *src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+
 // out[p_out[j]] += Op[class] x in[p_in[j]] for the pairs of one chunk (one
 // operator class): a [BM x nc] x [nc x BN] product whose K loop is staged
-// through TR_NS shared-memory buffers by cp.async, so every tile's loads are
-// in flight together instead of one latency per element.
-template <class T, int BN>
-__global__ void __launch_bounds__(TR_THREADS)
+// through TR_NS shared-memory buffers by cp.async (the operator rows, padded
+// to the cell stride, in 16-byte copies), so every tile's loads are in flight
+// together.  NTH threads; each owns 8 consecutive output rows (two or four
+// 16-byte shared loads per k) and BN x 16 / NTH pair columns.
+template <class T, int BN, int NTH>
+__global__ void __launch_bounds__(NTH)
 k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ chunks,
             const int *__restrict__ p_out, const int *__restrict__ p_in, const T *__restrict__ in,
             T *__restrict__ out) {
     constexpr int BK = TrBK<T>::v;
-    constexpr int CPT = BN / 16;            // columns per thread
+    constexpr int NTY = TR_BM / 8;          // row groups of 8
+    constexpr int NTX = NTH / NTY;          // column groups
+    constexpr int CPT = BN / NTX;           // columns per thread
+    static_assert(NTH % NTY == 0 && BN % NTX == 0, "translate tiling");
+    constexpr int VEC = 16 / (int)sizeof(T);
     constexpr int STAGE = BK * TR_BM + BK * BN;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sm = reinterpret_cast<T *>(smraw);   // TR_NS x {As [BK][BM], Bs [BK][BN]}
     T *Cs = sm;                             // [BN][BM+1] (epilogue)
     __shared__ int s_in[BN], s_out[BN];
     const int4 ch = chunks[blockIdx.x];
-    const T *Tt = ops + (size_t)ch.x * nc * nc;
+    const T *Tt = ops + (size_t)ch.x * nc * cs;
     const int rb = blockIdx.y * TR_BM;
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int tid = threadIdx.x, ty = tid / NTX, tx = tid - ty * NTX;
     if (tid < BN) {
         s_in[tid] = tid < ch.z ? p_in[ch.y + tid] : -1;
         s_out[tid] = tid < ch.z ? p_out[ch.y + tid] : -1;
@@ -1152,12 +1176,12 @@ k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ 
         T *As = sm + (kt % TR_NS) * STAGE;
         T *Bs = As + BK * TR_BM;
         const int k0 = kt * BK;
-        for (int e = tid; e < BK * TR_BM; e += TR_THREADS) {
-            const int k = e / TR_BM, r = e - k * TR_BM;
-            const bool ok = k0 + k < nc && rb + r < nc;
-            cp_async_elt(As + e, ok ? Tt + (size_t)(k0 + k) * nc + rb + r : Tt, ok);
+        for (int e = tid; e < BK * TR_BM / VEC; e += NTH) {
+            const int k = e / (TR_BM / VEC), r = (e - k * (TR_BM / VEC)) * VEC;
+            const bool ok = k0 + k < nc && rb + r < cs;  // cs % VEC == 0: a copy never crosses a row
+            cp_async_16(As + k * TR_BM + r, ok ? Tt + (size_t)(k0 + k) * cs + rb + r : Tt, ok);
         }
-        for (int e = tid; e < BK * BN; e += TR_THREADS) {
+        for (int e = tid; e < BK * BN; e += NTH) {
             const int k = e / BN, j = e - k * BN;
             const int src = s_in[j];
             const bool ok = src >= 0 && k0 + k < nc;
@@ -1180,7 +1204,19 @@ k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ 
         for (int k = 0; k < BK; ++k) {
             T a[8], b[CPT];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) a[r] = As[k * TR_BM + ty * 8 + r];
+            for (int q = 0; q < 8; q += VEC) {
+                if constexpr (sizeof(T) == 4) {
+                    const float4 v = *reinterpret_cast<const float4 *>(As + k * TR_BM + ty * 8 + q);
+                    a[q] = v.x;
+                    a[q + 1] = v.y;
+                    a[q + 2] = v.z;
+                    a[q + 3] = v.w;
+                } else {
+                    const double2 v = *reinterpret_cast<const double2 *>(As + k * TR_BM + ty * 8 + q);
+                    a[q] = v.x;
+                    a[q + 1] = v.y;
+                }
+            }
 #pragma unroll
             for (int c = 0; c < CPT; ++c) b[c] = Bs[k * BN + tx * CPT + c];
 #pragma unroll
@@ -1198,7 +1234,7 @@ k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ 
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
     const int rows = min(TR_BM, nc - rb);
-    for (int j = warp; j < ch.z; j += TR_THREADS / 32) {
+    for (int j = warp; j < ch.z; j += NTH / 32) {
         T *o = out + (size_t)s_out[j] * cs + rb;
         const T *cj = Cs + j * (TR_BM + 1);
         for (int r = lane; r < rows; r += 32) atomicAdd(o + r, cj[r]);
@@ -1475,8 +1511,8 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
         const size_t trsm = translate_smem<T, TR_BN_M2L>();
         const size_t trsm_t = translate_smem<T, TR_BN_TREE>();
         if (dense) {
-            set_smem<T>(k_translate<T, TR_BN_M2L>, trsm);
-            set_smem<T>(k_translate<T, TR_BN_TREE>, trsm_t);
+            set_smem<T>(k_translate<T, TR_BN_M2L, TR_THREADS>, trsm);
+            set_smem<T>(k_translate<T, TR_BN_TREE, TR_THREADS_TREE>, trsm_t);
         }
         // P2M
         p2m_leaves<T>(tv, t.nleaf, sk, strec, p, cs, inv_h, M, s);
@@ -1489,7 +1525,7 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             for (int c = t.L; c >= 3; --c) {
                 if (t.m2m_nchunk[c] == 0) continue;
                 dim3 g(t.m2m_nchunk[c], rblocks);
-                k_translate<T, TR_BN_TREE><<<g, TR_THREADS, trsm_t, s>>>(B::Om2m(m), nc, cs, t.g_chunk.p + t.m2m_chunk0[c],
+                k_translate<T, TR_BN_TREE, TR_THREADS_TREE><<<g, TR_THREADS_TREE, trsm_t, s>>>(B::Om2m(m), nc, cs, t.g_chunk.p + t.m2m_chunk0[c],
                                                             t.g_out.p, t.g_in.p, M, M);
                 BEM_CHECK_LAUNCH();
             }
@@ -1522,7 +1558,7 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             for (int c = 3; c <= t.L; ++c) {
                 if (t.l2l_nchunk[c] == 0) continue;
                 dim3 g(t.l2l_nchunk[c], rblocks);
-                k_translate<T, TR_BN_TREE><<<g, TR_THREADS, trsm_t, s>>>(B::Ol2l(m), nc, cs, t.g_chunk.p + t.l2l_chunk0[c],
+                k_translate<T, TR_BN_TREE, TR_THREADS_TREE><<<g, TR_THREADS_TREE, trsm_t, s>>>(B::Ol2l(m), nc, cs, t.g_chunk.p + t.l2l_chunk0[c],
                                                             t.g_out.p, t.g_in.p, L, L);
                 BEM_CHECK_LAUNCH();
             }
@@ -1668,7 +1704,7 @@ static void m2l_dense(Mesh &m, const Tree &t, const T *Oop, int nc, int cs, int 
         }
     }
     dim3 g(t.m2l_nchunk, rblocks);
-    k_translate<T, TR_BN_M2L><<<g, TR_THREADS, trsm, m.stream>>>(Oop, nc, cs, t.g_chunk.p + t.m2l_chunk0,
+    k_translate<T, TR_BN_M2L, TR_THREADS><<<g, TR_THREADS, trsm, m.stream>>>(Oop, nc, cs, t.g_chunk.p + t.m2l_chunk0,
                                                                   t.g_out.p, t.g_in.p, M, L);
     BEM_CHECK_LAUNCH();
 }
@@ -1705,8 +1741,8 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
         const int rblocks = cdiv(nc, TR_BM);
         const size_t trsm = translate_smem<T, TR_BN_M2L>();
         const size_t trsm_t = translate_smem<T, TR_BN_TREE>();
-        set_smem<T>(k_translate<T, TR_BN_M2L>, trsm);
-        set_smem<T>(k_translate<T, TR_BN_TREE>, trsm_t);
+        set_smem<T>(k_translate<T, TR_BN_M2L, TR_THREADS>, trsm);
+        set_smem<T>(k_translate<T, TR_BN_TREE, TR_THREADS_TREE>, trsm_t);
         {
             const int th = std::max(32, p2m_threads(p, sizeof(T)));
             const size_t sm = (size_t)th * nc * sizeof(T);
@@ -1720,7 +1756,7 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
         for (int c = t.L; c >= 3; --c) {
             if (t.m2m_nchunk[c] == 0) continue;
             dim3 g(t.m2m_nchunk[c], rblocks);
-            k_translate<T, TR_BN_TREE><<<g, TR_THREADS, trsm_t, s>>>(B::Om2m(m), nc, cs, t.g_chunk.p + t.m2m_chunk0[c],
+            k_translate<T, TR_BN_TREE, TR_THREADS_TREE><<<g, TR_THREADS_TREE, trsm_t, s>>>(B::Om2m(m), nc, cs, t.g_chunk.p + t.m2m_chunk0[c],
                                                                       t.g_out.p, t.g_in.p, M, M);
             BEM_CHECK_LAUNCH();
         }
@@ -1730,7 +1766,7 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
         for (int c = 3; c <= t.L; ++c) {
             if (t.l2l_nchunk[c] == 0) continue;
             dim3 g(t.l2l_nchunk[c], rblocks);
-            k_translate<T, TR_BN_TREE><<<g, TR_THREADS, trsm_t, s>>>(B::Ol2l(m), nc, cs, t.g_chunk.p + t.l2l_chunk0[c],
+            k_translate<T, TR_BN_TREE, TR_THREADS_TREE><<<g, TR_THREADS_TREE, trsm_t, s>>>(B::Ol2l(m), nc, cs, t.g_chunk.p + t.l2l_chunk0[c],
                                                                       t.g_out.p, t.g_in.p, L, L);
             BEM_CHECK_LAUNCH();
         }

@@ -139,7 +139,8 @@ struct Mesh;
 //   Rm2m: solid harmonics R_k^l of the 8 child offsets, full m range;
 //   If:   irregular harmonics I_n^m (n <= 2p) of the 343 offset classes;
 //   Om2l, Om2m, Ol2l: the translations as real (p+1)^2 x (p+1)^2 matrices
-//         in the compact real layout, stored column-major ([in][out]).
+//         in the compact real layout, stored column-major ([in][out]) with
+//         each [in] row padded with zeros to the cell stride.
 struct Tables {
     int p = 0;
     DArray<float> Rm2m_f, If_f, Om2l_f, Om2m_f, Ol2l_f;
