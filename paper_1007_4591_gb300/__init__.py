@@ -430,3 +430,44 @@ def solvation_energy(mesh: "Mesh", charges):
     if _SE is None:
         _SE = _energy_function()
     return _SE.apply(charges, mesh)
+
+# ------------------------------------------------------------ workflows
+def binding_free_energy(complex_, receptor, ligand, threads: int = 3, **opts):
+    """Electrostatic binding free energy (Eq. binding, Sec. 5):
+        dG_bind = dG_complex - dG_receptor - dG_ligand,
+    each term a full solve on its own mesh; the three solves run as one
+    bem_batch_solve.  Arguments are molecules with .panels, .charges,
+    .eps_in, .eps_out (e.g. synth.complex_pair()); opts go to make_options.
+    Returns (dG_bind, (dG_complex, dG_receptor, dG_ligand)) in kcal/mol."""
+    meshes = [Mesh(m.panels, m.charges, m.eps_in, m.eps_out, **opts) for m in (complex_, receptor, ligand)]
+    try:
+        dg, _, _, _ = bem_batch_solve(meshes, threads=threads)
+    finally:
+        for g in meshes:
+            g.close()
+    return float(dg[0] - dg[1] - dg[2]), (float(dg[0]), float(dg[1]), float(dg[2]))
+
+
+def superposition_energy(isolated, system, copies: int, **opts):
+    """The crowded-solution heuristic (Sec. 5): the induced surface charge of
+    one isolated molecule is reused on every copy in the system instead of
+    solving the whole system self-consistently.  `system`'s panels must be
+    `copies` rigid copies of `isolated`'s panels, copy after copy (rigid
+    motions leave the per-panel induced charge unchanged), with the copies'
+    charges.  Returns a dict with
+        dG_coupled     energy of the self-consistent solve of the system,
+        dG_superposed  energy of the system with the isolated induced charge
+                       on every copy (interactions between copies included),
+        dG_isolated    copies x the isolated molecule's energy,
+    all in kcal/mol."""
+    with Mesh(isolated.panels, isolated.charges, isolated.eps_in, isolated.eps_out, **opts) as g:
+        s_iso, _ = g.solve()
+        e_iso = g.energy(s_iso)
+    with Mesh(system.panels, system.charges, system.eps_in, system.eps_out, **opts) as G:
+        if G.n_p != copies * int(s_iso.shape[0]):
+            raise ValueError("system panels are not `copies` copies of the isolated molecule")
+        e_sup = G.energy(s_iso.repeat(copies))
+        s, _ = G.solve()
+        e = G.energy(s)
+    return {"dG_coupled": float(e), "dG_superposed": float(e_sup), "dG_isolated": float(copies * e_iso)}
+

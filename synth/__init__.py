@@ -19,6 +19,9 @@ stand-ins for the protein meshes, which are not available:
                 500..4,000 charges in the ball of radius R - 3 A, seed 4.
 * ``lattice``   1,000 rotated copies of ``globular`` on a 10x10x10 lattice at
                 50 A spacing, seed 5.
+* ``complex_pair`` a two-sphere "complex": a receptor sphere and a ligand
+                sphere a small gap apart, each with its own charges, plus the
+                two unbound molecules (for binding free energies).
 
 Panels are returned as float64 arrays of shape [n, 3, 3] (three vertices per
 triangle, counter-clockwise seen from outside so that the right-hand normal
@@ -31,7 +34,7 @@ import numpy as np
 
 __all__ = [
     "icosphere", "ball_charges", "random_rotation", "Molecule", "born",
-    "globular", "lattice", "batch", "small_molecule",
+    "globular", "lattice", "batch", "small_molecule", "complex_pair",
 ]
 
 
@@ -210,3 +213,25 @@ def batch(n_molecules: int = 64, seed: int = 4, subdivisions=(5, 6, 7),
         ch = ball_charges(nc, R - 3.0, rng)
         mols.append(Molecule(f"batch{b}-s{s}", icosphere(s, R), ch, eps_in, eps_out, R))
     return mols
+
+
+def complex_pair(s_rec: int = 6, r_rec: float = 20.0, n_rec: int = 2000, s_lig: int = 4,
+                 r_lig: float = 6.0, n_lig: int = 60, gap: float = 2.0, seed: int = 11,
+                 eps_in: float = 4.0, eps_out: float = 80.0):
+    """A receptor sphere at the origin and a ligand sphere centred on the x
+    axis with `gap` A between the two surfaces; charges in balls 3 A inside
+    each surface (receptor net +8 e, ligand net -1 e).  Returns (complex,
+    receptor, ligand): the complex is both closed surfaces and both charge
+    sets (the solvent surrounds two disjoint dielectric balls)."""
+    rng = np.random.default_rng(seed)
+    c_lig = (r_rec + gap + r_lig, 0.0, 0.0)
+    ch_r = ball_charges(n_rec, r_rec - 3.0, rng)
+    ch_l = ball_charges(n_lig, r_lig - 3.0, rng, net=-1.0, center=c_lig)
+    pan_r = icosphere(s_rec, r_rec)
+    pan_l = icosphere(s_lig, r_lig) + np.asarray(c_lig)
+    rec = Molecule(f"receptor-s{s_rec}", pan_r, ch_r, eps_in, eps_out, r_rec)
+    lig = Molecule(f"ligand-s{s_lig}", np.ascontiguousarray(pan_l), ch_l, eps_in, eps_out, r_lig, c_lig)
+    cpx = Molecule(f"complex-s{s_rec}-s{s_lig}", np.ascontiguousarray(np.concatenate([pan_r, pan_l])),
+                   np.ascontiguousarray(np.concatenate([ch_r, ch_l])), eps_in, eps_out)
+    return cpx, rec, lig
+
