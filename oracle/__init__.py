@@ -73,6 +73,10 @@ def _load():
             "oracle_ct": (None, [i64, ci, d, d, i64, d, d, d]),
             "oracle_grad_c": (None, [i64, ci, d, d, i64, d, d, d]),
             "oracle_grad_bt": (None, [i64, d, d, i64, d, d, d]),
+            "oracle_solid_angle": (ctypes.c_double, [d, d]),
+            "oracle_panel_dn": (ctypes.c_double, [d, d, d]),
+            "oracle_kprime_rows_near_exact": (None, [i64, ci, d, d, d, d, d, d, d, i64,
+                                                     ctypes.POINTER(ctypes.c_int64), d]),
             "oracle_num_threads": (ci, []),
             "oracle_set_threads": (None, [ci]),
         }
@@ -120,6 +124,19 @@ def bibee_factor(eps_in: float, eps_out: float, lam: float) -> float:
     return -e / (1.0 + e * lam)
 
 
+def solid_angle(t, tri) -> float:
+    """int_T h / R^3 dA: the solid angle of the flat triangle tri[3][3] seen
+    from t, positive when t lies on the side its right-hand normal points to."""
+    lib = _load()
+    return float(lib.oracle_solid_angle(_p(_c(t)), _p(_c(tri))))
+
+
+def panel_dn(t, n, tri) -> float:
+    """int_T -(t - y).n / (4 pi |t - y|^3) dA_y, exactly, for a flat triangle."""
+    lib = _load()
+    return float(lib.oracle_panel_dn(_p(_c(t)), _p(_c(n)), _p(_c(tri))))
+
+
 class Problem:
     """Dense discrete operators of one molecule (panels + point charges)."""
 
@@ -158,6 +175,19 @@ class Problem:
         _load().oracle_kprime_rows(self.n, self.nq, _p(self.cen), _p(self.nrm), _p(self.qp),
                                    _p(self.qw), _p(x), rows.shape[0],
                                    rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _p(y))
+        return y
+
+    def kprime_rows_near_exact(self, x, rows):
+        """Rows of K' x with the exact flat-triangle integral for the
+        near-singular pairs (|c_i - c_j| <= 2.5 sqrt(A_i)) and the quadrature
+        rule for all other pairs."""
+        x = _c(x)
+        rows = _c(rows, np.int64)
+        y = np.empty(rows.shape[0])
+        _load().oracle_kprime_rows_near_exact(self.n, self.nq, _p(self.cen), _p(self.nrm), _p(self.area),
+                                              _p(self.panels), _p(self.qp), _p(self.qw), _p(x),
+                                              rows.shape[0],
+                                              rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _p(y))
         return y
 
     def kprime_t(self, x):

@@ -188,6 +188,129 @@ void oracle_kprime_dense(int64_t n, int nq, const double *cen, const double *nrm
             K[i * n + j] = (i == j) ? 0.0 : kprime_entry(i, j, nq, cen, nrm, qp, qw);
 }
 
+/* ------------------------------------------------------------------ */
+/* Exact integrals over one flat triangle T (vertices a0, a1, a2, unit  */
+/* normal nu = (a1-a0)x(a2-a0)/|.|) of the field of a unit surface      */
+/* density, for the near-singular pairs (higher-accuracy panel          */
+/* integration: Sec. 2.1 names analytic panel integrals for flat      */
+/* elements as the alternative to quadrature).  With R = |t - y|       */
+/* and h = (t - a0).nu, split t - y into its normal part h nu and its   */
+/* in-plane part:                                                       */
+/*   * the normal part integrates to nu * W(t), W(t) = int_T h/R^3 dA,  */
+/*     the solid angle of T seen from t, positive when t lies on the    */
+/*     side nu points to;                                               */
+/*   * the in-plane part is the in-plane gradient of 1/R with respect   */
+/*     to y, so by the divergence theorem in the plane it becomes       */
+/*     sum over edges e = (p -> q) of m_e * int_e dl / R, where m_e is  */
+/*     the edge's outward in-plane normal and                           */
+/*     int_e dl / R = asinh(s_q / d) - asinh(s_p / d)                   */
+/*                  = log((R_q + s_q) / (R_p + s_p)),                   */
+/*     s the coordinate along the edge measured from the foot of t.     */
+/* So  int_T (t - y)/R^3 dA = nu W(t) + sum_e m_e log(...), and the     */
+/* K' entry (collocation at t with normal n) is                         */
+/*   int_T -(t - y).n / (4 pi R^3) dA = -n.(nu W + sum_e m_e L_e)/(4pi).*/
+/* ------------------------------------------------------------------ */
+static void sub3(const double *a, const double *b, double *c)
+{
+    c[0] = a[0] - b[0]; c[1] = a[1] - b[1]; c[2] = a[2] - b[2];
+}
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double *a, const double *b, double *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double norm3(const double *a) { return sqrt(dot3(a, a)); }
+
+/* W(t) = int_T h / R^3 dA by the triple-product formula for the solid angle
+ * of a triangle (Van Oosterom and Strackee, IEEE Trans. Biomed. Eng. 30,
+ * 1983): with r_k = a_k - t,
+ *   tan(W'/2) = r0.(r1 x r2) / (|r0||r1||r2| + (r0.r1)|r2| + (r0.r2)|r1| + (r1.r2)|r0|),
+ * where W' is positive when the vertices appear counter-clockwise from t,
+ * i.e. when t lies on the side opposite to nu; hence W = -W'. */
+double oracle_solid_angle(const double *t, const double *tri)
+{
+    double r0[3], r1[3], r2[3], c[3];
+    sub3(tri, t, r0);
+    sub3(tri + 3, t, r1);
+    sub3(tri + 6, t, r2);
+    const double l0 = norm3(r0), l1 = norm3(r1), l2 = norm3(r2);
+    cross3(r1, r2, c);
+    const double num = dot3(r0, c);
+    const double den = l0 * l1 * l2 + dot3(r0, r1) * l2 + dot3(r0, r2) * l1 + dot3(r1, r2) * l0;
+    return -2.0 * atan2(num, den);
+}
+
+/* int_e dl / |t - y| along the segment p -> q (length > 0). */
+static double edge_log(const double *t, const double *p, const double *q)
+{
+    double e[3], dp[3], dq[3];
+    sub3(q, p, e);
+    const double len = norm3(e);
+    for (int k = 0; k < 3; ++k) e[k] /= len;
+    sub3(p, t, dp);
+    sub3(q, t, dq);
+    const double sp = dot3(dp, e), sq = dot3(dq, e);
+    const double Rp = norm3(dp), Rq = norm3(dq);
+    /* the two algebraically equal forms; take the one without cancellation */
+    if (sp + sq >= 0.0) return log((Rq + sq) / (Rp + sp));
+    return log((Rp - sp) / (Rq - sq));
+}
+
+/* int_T -(t - y).n / (4 pi |t - y|^3) dA_y for a flat triangle tri[3][3]. */
+double oracle_panel_dn(const double *t, const double *n, const double *tri)
+{
+    double e1[3], e2[3], nu[3];
+    sub3(tri + 3, tri, e1);
+    sub3(tri + 6, tri, e2);
+    cross3(e1, e2, nu);
+    const double ln = norm3(nu);
+    for (int k = 0; k < 3; ++k) nu[k] /= ln;
+    double v[3] = {0.0, 0.0, 0.0};
+    const double W = oracle_solid_angle(t, tri);
+    for (int k = 0; k < 3; ++k) v[k] = nu[k] * W;
+    for (int e = 0; e < 3; ++e) {
+        const double *p = tri + 3 * e, *q = tri + 3 * ((e + 1) % 3);
+        double te[3], m[3];
+        sub3(q, p, te);
+        const double lt = norm3(te);
+        for (int k = 0; k < 3; ++k) te[k] /= lt;
+        cross3(te, nu, m);                     /* outward in-plane normal (CCW about nu) */
+        const double L = edge_log(t, p, q);
+        for (int k = 0; k < 3; ++k) v[k] += m[k] * L;
+    }
+    return -dot3(n, v) / FOUR_PI;
+}
+
+/* Rows of K' x where every pair (i, j != i) with |c_i - c_j| <= 2.5 sqrt(A_i)
+ * uses the exact panel integral above and every other pair the quadrature
+ * rule (the near-singular set of the accelerated product). */
+void oracle_kprime_rows_near_exact(int64_t n, int nq, const double *cen, const double *nrm,
+                                   const double *area, const double *panels, const double *qp,
+                                   const double *qw, const double *x, int64_t nrows,
+                                   const int64_t *rows, double *y)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t i = rows[r];
+        const double tau = 2.5 * sqrt(area[i]);
+        double acc = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            sub3(cen + 3 * i, cen + 3 * j, d);
+            double kij;
+            if (dot3(d, d) <= tau * tau)
+                kij = oracle_panel_dn(cen + 3 * i, nrm + 3 * i, panels + 9 * j);
+            else
+                kij = kprime_entry(i, j, nq, cen, nrm, qp, qw);
+            acc += kij * x[j];
+        }
+        y[r] = acc;
+    }
+}
+
 /* E = B q: normal field of the point charges at the collocation points. */
 void oracle_bq(int64_t n, const double *cen, const double *nrm, int64_t nc,
                const double *xq /*[nc][3]*/, const double *q, double *E)

@@ -301,3 +301,77 @@ def test_one_point_rule_variant_runs_and_converges():
     assert info["converged"]
     dg, _ = P.energy(sig)
     assert abs(dg - ss.born_energy(1.0, 2.0, 1.0, 80.0)) / 81.978 < 0.05
+
+
+# ------------------------------------------- exact flat-panel integrals
+# The exact integral over a flat triangle of the normal field of a unit
+# density (solid-angle term plus edge logarithms), used for the near-singular
+# pairs in the higher-accuracy variant of the operator.
+def _refined_7pt(t, n, tri, levels):
+    import ctypes
+    bary = np.zeros(21)
+    w = np.zeros(7)
+    oracle._load().oracle_quad_rule(7, bary.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    bary = bary.reshape(7, 3)
+    tris = [np.asarray(tri, dtype=np.float64)]
+    for _ in range(levels):
+        nxt = []
+        for a, b, c in tris:
+            ab, bc, ca = (a + b) / 2, (b + c) / 2, (c + a) / 2
+            nxt += [np.array([a, ab, ca]), np.array([ab, b, bc]), np.array([ca, bc, c]),
+                    np.array([ab, bc, ca])]
+        tris = nxt
+    acc = 0.0
+    for tt in tris:
+        A = 0.5 * np.linalg.norm(np.cross(tt[1] - tt[0], tt[2] - tt[0]))
+        y = bary @ tt
+        d = np.asarray(t) - y
+        r = np.linalg.norm(d, axis=1)
+        acc += float(np.sum(A * w * (-(d @ np.asarray(n))) / (4 * np.pi * r ** 3)))
+    return acc
+
+
+def test_solid_angles_of_a_closed_surface():
+    pan = synth.icosphere(2, 1.0)
+    inside = sum(oracle.solid_angle([0.1, 0.2, -0.3], p) for p in pan)
+    outside = sum(oracle.solid_angle([2.0, 0.5, 0.1], p) for p in pan)
+    assert abs(inside + 4 * np.pi) < 1e-10          # outward normals: -4 pi inside
+    assert abs(outside) < 1e-10
+
+
+def test_exact_panel_integral_matches_refined_quadrature():
+    tri = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.2, 0.9, 0.1]])
+    n = np.array([0.2, -0.3, 0.93])
+    n /= np.linalg.norm(n)
+    # above the panel, and beyond the extension of an edge (the other log form)
+    for t in ([0.3, 0.4, 0.35], [-0.7, 0.0, 0.05]):
+        ex = oracle.panel_dn(t, n, tri)
+        assert abs(_refined_7pt(t, n, tri, 5) - ex) < 1e-9 * max(1.0, abs(ex)), (t, ex)
+        assert abs(_refined_7pt(t, n, tri, 0) - ex) > 1e-12   # the unrefined rule is not exact
+
+
+def test_exact_panel_integral_jumps_by_one_across_the_sheet():
+    # the normal field of a unit sheet density (G = 1/(4 pi r)) jumps by 1:
+    # -1/2 just on the side the normal points to, +1/2 just behind
+    tri = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    nu = np.array([0.0, 0.0, 1.0])
+    c = tri.mean(axis=0)
+    assert abs(oracle.panel_dn(c + 1e-9 * nu, nu, tri) + 0.5) < 1e-7
+    assert abs(oracle.panel_dn(c - 1e-9 * nu, nu, tri) - 0.5) < 1e-7
+
+
+def test_near_exact_rows_approach_the_exact_flat_panel_operator():
+    # against K' integrated exactly for every pair, the 7-point rule errs at
+    # the near-singular pairs; the near-exact variant keeps only the small
+    # far-pair quadrature error
+    pan = synth.icosphere(2, 1.0)
+    P = oracle.Problem(pan, np.zeros((0, 4)), 1.0, 80.0)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(P.n)
+    rows = rng.choice(P.n, 40, replace=False)
+    full = np.array([sum(oracle.panel_dn(P.cen[i], P.nrm[i], pan[j]) * x[j]
+                         for j in range(P.n) if j != i) for i in rows])
+    e_quad = np.linalg.norm(P.kprime_rows(x, rows) - full) / np.linalg.norm(full)
+    e_near = np.linalg.norm(P.kprime_rows_near_exact(x, rows) - full) / np.linalg.norm(full)
+    assert e_near < 3e-5 and e_quad > 1e-3, (e_near, e_quad)
