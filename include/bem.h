@@ -71,6 +71,10 @@ extern "C" {
 #define BEM_FLAG_NO_NEAR 2u     /* diagnostics: drop the near field (P2P + table) */
 #define BEM_FLAG_NO_NEARTAB 4u  /* diagnostics: skip the near-singular FP64 table */
 
+/* bem_options.near_table */
+#define BEM_NEAR_QUADRATURE 1
+#define BEM_NEAR_EXACT 2
+
 typedef struct bem_options {
     int precision;     /* BEM_MIXED (default) or BEM_FP64 */
     int p;             /* expansion order, 1..16 (default 10) */
@@ -81,7 +85,11 @@ typedef struct bem_options {
     int max_iter;      /* total GMRES iterations (default 300) */
     double tol;        /* relative residual |b - A x| / |b| (default 1e-8) */
     unsigned flags;    /* BEM_FLAG_* (default 0) */
-    int near_table;    /* 1 = FP64 near-singular correction table (default 1) */
+    int near_table;    /* near-singular pairs (panel i with the panels whose centroid lies
+                          within 2.5 sqrt(A_i)): 1 = corrected to their FP64 quadrature value
+                          (default); BEM_NEAR_EXACT = their exact flat-panel integral (solid
+                          angle + edge logarithms; higher accuracy, Sec. 2.1); 0 = no
+                          correction (diagnostics) */
     int charge_mode;   /* products with B, B^T, C, C^T (charges <-> surface):
                           0 = auto (direct sum when n_c * n_p * quad_points <= 4e10,
                               fast multipole otherwise), 1 = fast multipole, 2 = direct */

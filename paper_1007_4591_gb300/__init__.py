@@ -30,6 +30,8 @@ BEM_EUNSUPPORTED = -6
 
 BEM_MIXED = 0
 BEM_FP64 = 1
+BEM_NEAR_QUADRATURE = 1
+BEM_NEAR_EXACT = 2
 BEM_BIBEE_CFA = 0
 BEM_BIBEE_P = 1
 BEM_BIBEE_PLUS_HALF = 2

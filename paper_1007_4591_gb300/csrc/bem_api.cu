@@ -161,6 +161,7 @@ static void validate_options(const bem_options &o) {
     if (o.leaf_size < 1) throw Error(BEM_EINVAL, "leaf_size must be positive");
     if (o.depth > MORTON_BITS) throw Error(BEM_EINVAL, "depth must be <= 21");
     if (o.quad_points != 1 && o.quad_points != 7) throw Error(BEM_EINVAL, "quad_points must be 1 or 7");
+    if (o.near_table < 0 || o.near_table > BEM_NEAR_EXACT) throw Error(BEM_EINVAL, "near_table must be 0, 1 or 2");
     if (o.gmres_restart < 1 || o.gmres_restart > 200) throw Error(BEM_EINVAL, "gmres_restart must be in 1..200");
     if (o.max_iter < 1) throw Error(BEM_EINVAL, "max_iter must be positive");
     if (!(o.tol > 0.0)) throw Error(BEM_EINVAL, "tol must be positive");
@@ -247,7 +248,7 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
         build_translation_groups(*m, m->tp);
         build_translation_groups(*m, m->tc);
         alloc_work(*m);
-        if (m->opt.near_table) build_near_table(*m);
+        if (m->opt.near_table) build_near_table(*m, dp);
         sync(*m);
         m->ms_build = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     });

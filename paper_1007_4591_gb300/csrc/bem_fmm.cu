@@ -711,6 +711,58 @@ __global__ void k_panel_reduce(const T *far, const T *near, const int *qp_of_pan
 // adjacent to i's leaf).  For j = i the exact value is zero (flat panel).
 // Adding D x in FP64 after the near field therefore replaces the FP32
 // (or FP64) near-field values of these pairs by their FP64 quadrature.
+// Exact integral over the flat triangle v[0..8] of the normal field of a unit
+// density, times 4 pi:  -n . int_T (t - y) / |t - y|^3 dA_y.  The integrand
+// splits into the part along the triangle's normal, which integrates to the
+// solid angle the triangle subtends at t (the triple-product formula for a
+// triangle's solid angle), and the in-plane part, which the divergence
+// theorem in the plane turns into one logarithm per edge:
+//   int_T (t - y)/R^3 dA = nu Om(t) + sum_edges m_e log((R_b + s_b)/(R_a + s_a)),
+// Om > 0 when t is on the side of the unit normal nu, m_e the edge's outward
+// in-plane normal, s the coordinate along the edge from the foot of t.  t
+// must not lie on the triangle itself (a collocation point is never on
+// another panel).
+__device__ double tri_normal_field_4pi(const double t[3], const double n[3], const double *v) {
+    double a[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int c = 0; c < 3; ++c) a[k][c] = v[3 * k + c] - t[c];  // vertices relative to t
+    const double e1[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]};
+    const double e2[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
+    double nu[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const double lnu = sqrt(nu[0] * nu[0] + nu[1] * nu[1] + nu[2] * nu[2]);
+    nu[0] /= lnu;
+    nu[1] /= lnu;
+    nu[2] /= lnu;
+    double len[3];
+    for (int k = 0; k < 3; ++k) len[k] = sqrt(a[k][0] * a[k][0] + a[k][1] * a[k][1] + a[k][2] * a[k][2]);
+    const double c12[3] = {a[1][1] * a[2][2] - a[1][2] * a[2][1], a[1][2] * a[2][0] - a[1][0] * a[2][2],
+                           a[1][0] * a[2][1] - a[1][1] * a[2][0]};
+    const double trip = a[0][0] * c12[0] + a[0][1] * c12[1] + a[0][2] * c12[2];
+    auto d3 = [](const double *x, const double *y) { return x[0] * y[0] + x[1] * y[1] + x[2] * y[2]; };
+    const double den = len[0] * len[1] * len[2] + d3(a[0], a[1]) * len[2] + d3(a[0], a[2]) * len[1] +
+                       d3(a[1], a[2]) * len[0];
+    // atan2 gives half the angle seen with the vertices counter-clockwise,
+    // i.e. from the side opposite to nu
+    const double om = -2.0 * atan2(trip, den);
+    double f[3] = {nu[0] * om, nu[1] * om, nu[2] * om};
+    for (int e = 0; e < 3; ++e) {
+        const int b = (e + 1) % 3;
+        double te[3] = {a[b][0] - a[e][0], a[b][1] - a[e][1], a[b][2] - a[e][2]};
+        const double lt = sqrt(d3(te, te));
+        te[0] /= lt;
+        te[1] /= lt;
+        te[2] /= lt;
+        const double m[3] = {te[1] * nu[2] - te[2] * nu[1], te[2] * nu[0] - te[0] * nu[2],
+                             te[0] * nu[1] - te[1] * nu[0]};
+        const double sa = d3(a[e], te), sb = d3(a[b], te);
+        const double lg = (sa + sb >= 0.0) ? log((len[b] + sb) / (len[e] + sa)) : log((len[e] - sa) / (len[b] - sb));
+        f[0] += m[0] * lg;
+        f[1] += m[1] * lg;
+        f[2] += m[2] * lg;
+    }
+    return -d3(n, f);
+}
+
 template <class T, bool FILL>
 __global__ void k_near_table(int64_t np, int nq, const int *nbr_off, const int *nbr,
                              const int *cen_beg, const int4 *ijk, int leaf0, const uint64_t *cen_key,
@@ -719,7 +771,8 @@ __global__ void k_near_table(int64_t np, int nq, const int *nbr_off, const int *
                              const double *qw64, const int *qp_of_panel,
                              const typename V4T<T>::t *trec, const typename V4T<T>::t *nrec,
                              const typename V4T<T>::t *srec, const int *leaf_of_cen,
-                             const int *off, int *cnt, int *col, double *val) {
+                             const int *off, int *cnt, int *col, double *val,
+                             const double *pan, const int *perm) {
     using V4 = typename V4T<T>::t;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= np) return;
@@ -776,6 +829,20 @@ __global__ void k_near_table(int64_t np, int nq, const int *nbr_off, const int *
                     T nd, ri3;
                     dn_pair<T>(tr.x - y.x, tr.y - y.y, tr.z - y.z, nr.x, nr.y, nr.z, nd, ri3);
                     rep += -(double)y.w * (double)nd * (double)ri3;
+                }
+                // with the exact panel integrals (pan != nullptr) the pair's whole
+                // value, near and far points alike, becomes the exact integral:
+                // add it and take out the 7-point value of all the panel's points
+                if (pan && j != i) {
+                    double quad = 0.0;
+                    for (int q = 0; q < nq; ++q) {
+                        const int k = qp_of_panel[(int64_t)j * nq + q];
+                        const double ex = ci[0] - qpg64[3 * k], ey = ci[1] - qpg64[3 * k + 1],
+                                     ez = ci[2] - qpg64[3 * k + 2];
+                        const double r2 = ex * ex + ey * ey + ez * ez;
+                        quad += -qw64[k] * (ex * ni[0] + ey * ni[1] + ez * ni[2]) / (r2 * sqrt(r2));
+                    }
+                    exact += tri_normal_field_4pi(ci, ni, pan + 9 * (int64_t)perm[j]) - quad;
                 }
                 col[base + n] = j;
                 val[base + n] = (exact - rep) / FOUR_PI;
@@ -1602,7 +1669,7 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
 void build_qp_of_panel(Mesh &m);
 
 template <class T>
-static void near_table_impl(Mesh &m) {
+static void near_table_impl(Mesh &m, const double *exact_pan) {
     using B = PassBufs<T>;
     cudaStream_t s = m.stream;
     const Tree &t = m.tp;
@@ -1622,7 +1689,7 @@ static void near_table_impl(Mesh &m) {
     k_near_table<T, false><<<cdiv(np, 128), 128, 0, s>>>(
         np, nq, t.nbr_off.p, t.nbr.p, t.cen_beg.p, t.ijk.p, t.leaf0, m.cen_key.p, m.qp_key.p, shift, h,
         m.cen64.p, m.nrm64.p, m.area64.p, m.qpg64.p, m.qw64.p, qop.p, B::cen(m), B::nrm(m), B::qp(m),
-        leaf_of.p, nullptr, cnt.p, nullptr, nullptr);
+        leaf_of.p, nullptr, cnt.p, nullptr, nullptr, nullptr, nullptr);
     BEM_CHECK_LAUNCH();
     m.nt_off.alloc(np + 1);
     exclusive_scan_int(cnt.p, m.nt_off.p, (int)np + 1, s);
@@ -1635,7 +1702,7 @@ static void near_table_impl(Mesh &m) {
     k_near_table<T, true><<<cdiv(np, 128), 128, 0, s>>>(
         np, nq, t.nbr_off.p, t.nbr.p, t.cen_beg.p, t.ijk.p, t.leaf0, m.cen_key.p, m.qp_key.p, shift, h,
         m.cen64.p, m.nrm64.p, m.area64.p, m.qpg64.p, m.qw64.p, qop.p, B::cen(m), B::nrm(m), B::qp(m),
-        leaf_of.p, m.nt_off.p, nullptr, m.nt_col.p, m.nt_val.p);
+        leaf_of.p, m.nt_off.p, nullptr, m.nt_col.p, m.nt_val.p, exact_pan, m.cen_perm.p);
     BEM_CHECK_LAUNCH();
     BEM_CUDA(cudaStreamSynchronize(s));
 }
@@ -1686,9 +1753,10 @@ static void transpose_near_table(Mesh &m) {
     BEM_CUDA(cudaStreamSynchronize(m.stream));
 }
 
-void build_near_table(Mesh &m) {
-    if (m.opt.precision == BEM_MIXED) near_table_impl<float>(m);
-    else near_table_impl<double>(m);
+void build_near_table(Mesh &m, const double *panels) {
+    const double *exact_pan = m.opt.near_table == BEM_NEAR_EXACT ? panels : nullptr;
+    if (m.opt.precision == BEM_MIXED) near_table_impl<float>(m, exact_pan);
+    else near_table_impl<double>(m, exact_pan);
     transpose_near_table(m);
 }
 

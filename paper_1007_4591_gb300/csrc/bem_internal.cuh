@@ -248,7 +248,9 @@ inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // geometry + trees (bem_tree.cu)
 void build_geometry_and_trees(Mesh &m, const double *d_panels, const double *d_charges);
 void rebuild_charge_tree(Mesh &m, const double *d_charges);
-void build_near_table(Mesh &m);
+// panels: [np][3][3] f64 device array in the caller's order (read when
+// opt.near_table == BEM_NEAR_EXACT)
+void build_near_table(Mesh &m, const double *panels);
 void build_tables(Mesh &m);
 void build_translation_groups(Mesh &m, Tree &t);
 // tensor-core M2L (bem_tc.cu)
