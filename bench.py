@@ -366,9 +366,10 @@ def run_ours(args):
         prec_cmp = precision_comparison(pkg, mol, torch)
 
     L = info["depth"]
-    # gather, P2P, combine, operator epilogue, scatter; P2M, M2L, L2P and one M2M
-    # and one L2L launch per level between 2 and L
-    launches_per = 5 + (3 + 2 * (L - 2) if L >= 2 else 0)
+    # gather, source strengths, P2P, combine, operator epilogue, scatter;
+    # P2M, multipole split, M2L, L2P and one M2M and one L2L launch per level
+    # from 3 to L (16 kernels at L = 5, as the ncu launch list shows)
+    launches_per = 6 + (4 + 2 * (L - 2) if L >= 2 else 0)
     cpu = cpu_baseline(mol, budget_s=args.cpu_budget) if (rank == 0 and not args.no_cpu) else None
     mesh.close()
     if rank == 0:
@@ -435,6 +436,19 @@ def run_batch(args):
             times.append(time.perf_counter() - t1)
     ok = all(s["converged"] == 1 for s in st) and all(p_ < g < c for g, c, p_ in zip(dg, dc, dpb))
     t = float(np.median(times))
+    # algorithmic flops of the K' products the solves ran (GMRES iterations),
+    # counted as for the single product (P2P 20/pair, translations 8,866 at
+    # p = 10, P2M 8(p+1)^2/point, L2P 12(p+1)^2/target)
+    peaks, _ = _peaks()
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    alg = 0.0
+    for g, s_ in zip(meshes, st):
+        inf = g.info()
+        pp = inf["p"]
+        tu = 2 * (2 * (pp + 1) * (2 * pp + 1) * (2 * pp + 3) / 3 + (pp + 1) ** 2 + pp * (pp + 1) * (2 * pp + 1) / 3)
+        per = (20.0 * inf["p2p_pairs"] + tu * (inf["m2l_pairs"] + 2 * inf["m2m_pairs"])
+               + 8 * (pp + 1) ** 2 * inf["source_points"] + 12 * (pp + 1) ** 2 * inf["n_p"])
+        alg += per * s_["iterations"]
     print(json.dumps({
         "metric": "batched FMM-BEM solve + BIBEE bounds, panels solved per second",
         "value": round(n_p / t / 1e6, 3), "unit": "Mpanels/s", "n_gpus": 1, "steps": len(times),
@@ -445,7 +459,12 @@ def run_batch(args):
                    "gmres_tol": 1e-8, "threads": 8},
         "batch_solve_s": round(t, 4), "autotune_s": round(tune_s, 2), "mesh_build_s": round(build_s, 2),
         "all_converged_and_bounded": bool(ok),
-        "gmres_iters_max": int(max(s["iterations"] for s in st))}), flush=True)
+        "gmres_iters_max": int(max(s["iterations"] for s in st)),
+        "products_roofline": {"algorithmic_tflop": round(alg / 1e12, 4),
+                              "achieved_tflops_over_batch_time": round(alg / t / 1e12, 3),
+                              "frac_of_fp32_peak": round(alg / t / 1e12 / fp32_peak, 4),
+                              "note": "K' products only; the batch time also holds RHS, energies, "
+                                      "BIBEE passes and host work"}}), flush=True)
     for g in meshes:
         g.close()
 

@@ -169,20 +169,23 @@ static void direct_adjoint(Mesh &m, AdjSrc sk, AdjTgt tk, const double *dens, do
 }
 
 // y = A^T x = x + Ehat (K'^T x)
+// four lanes per row, as k_apply_A
 __global__ void k_apply_At(const double *x, const double *ktx, const int *off, const int *col,
                            const double *val, double ehat, int64_t n, double *y) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double k = ktx[i];
-    if (off)
-        for (int e = off[i]; e < off[i + 1]; ++e) k += val[e] * x[col[e]];
-    y[i] = x[i] + ehat * k;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2;
+    const int sub = threadIdx.x & 3;
+    double k = 0.0;
+    if (i < n && off)
+        for (int e = off[i] + sub; e < off[i + 1]; e += 4) k += val[e] * x[col[e]];
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    if (i < n && sub == 0) y[i] = x[i] + ehat * (ktx[i] + k);
 }
 
 void matvec_t_sorted(Mesh &m, const double *xs, double *ys) {
     const bool nt = m.nt_nnz > 0 && !(m.opt.flags & (BEM_FLAG_NO_NEARTAB | BEM_FLAG_NO_NEAR));
     fmm_pass_t(m, xs, m.zs.p);
-    k_apply_At<<<cdiv(m.np, 256), 256, 0, m.stream>>>(xs, m.zs.p, nt ? m.ntT_off.p : nullptr,
+    k_apply_At<<<cdiv(4 * m.np, 256), 256, 0, m.stream>>>(xs, m.zs.p, nt ? m.ntT_off.p : nullptr,
                                                        m.ntT_col.p, m.ntT_val.p, m.ehat, m.np, ys);
     BEM_CHECK_LAUNCH();
 }

@@ -63,20 +63,24 @@ void scatter_rows3(const double *src, const int *perm, double *dst, int64_t n, c
 // y = x + Ehat (K'x): kx holds the fast multipole K' x (sorted order); the
 // FP64 near-singular table replaces the FP32 near-field values of the pairs
 // it lists.
+// y = x + Ehat (K'x + table x): four lanes per row share the row's table
+// entries (a dozen or so gathers each row), then add up by shuffles.
 __global__ void k_apply_A(const double *x, const double *kx, const int *nt_off, const int *nt_col,
                           const double *nt_val, double ehat, int64_t n, double *y) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double k = kx[i];
-    if (nt_off)
-        for (int e = nt_off[i]; e < nt_off[i + 1]; ++e) k += nt_val[e] * x[nt_col[e]];
-    y[i] = x[i] + ehat * k;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2;
+    const int sub = threadIdx.x & 3;
+    double k = 0.0;
+    if (i < n && nt_off)
+        for (int e = nt_off[i] + sub; e < nt_off[i + 1]; e += 4) k += nt_val[e] * x[nt_col[e]];
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    if (i < n && sub == 0) y[i] = x[i] + ehat * (kx[i] + k);
 }
 
 static void matvec_launch(Mesh &m, const double *xs, double *ys) {
     const bool nt = m.nt_nnz > 0 && !(m.opt.flags & (BEM_FLAG_NO_NEARTAB | BEM_FLAG_NO_NEAR));
     fmm_pass(m, m.tp, SRC_QUAD, TGT_CEN_DN, xs, m.zs.p, true);
-    k_apply_A<<<cdiv(m.np, 256), 256, 0, m.stream>>>(xs, m.zs.p, nt ? m.nt_off.p : nullptr,
+    k_apply_A<<<cdiv(4 * m.np, 256), 256, 0, m.stream>>>(xs, m.zs.p, nt ? m.nt_off.p : nullptr,
                                                       m.nt_col.p, m.nt_val.p, m.ehat, m.np, ys);
     BEM_CHECK_LAUNCH();
     if (m.tm.on) BEM_CUDA(cudaEventRecord(m.tm.ev[7], m.stream));
