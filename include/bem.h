@@ -243,6 +243,20 @@ int bem_normal_field_noalloc(const double *targets, const double *normals, int64
 /* Sizes and counts of the handle (tree depth, list sizes, memory). */
 int bem_mesh_info_get(const bem_mesh *mesh, bem_mesh_info *info);
 
+/* Clock cycles one device-side pipeline wait of the tensor-core M2L kernel
+ * may spin before the call gives up with BEM_ETIMEOUT (default 2e9, about a
+ * second; 0 restores the default).  The kernel then leaves cleanly (it waits
+ * for its own MMAs, which always finish, and frees its tensor memory), so
+ * the mesh stays usable for the next call.  A tiny budget exercises that path
+ * from the host.  BEM_EINVAL for a NULL mesh or a negative count. */
+int bem_set_wait_budget(bem_mesh *mesh, long long cycles);
+
+/* Cap, in bytes, on the device memory the library's arrays hold in this
+ * process (0 = no cap, the default).  An allocation that would pass it fails
+ * with BEM_ENOMEM before reaching the CUDA allocator; arrays already held are
+ * kept.  Process-wide, for callers that share the GPU with other work. */
+int bem_set_device_memory_cap(size_t bytes);
+
 /* Per-phase device time (ms) of the last bem_matvec, measured with CUDA events
  * when enabled by bem_set_profiling(mesh, 1): order P2M, M2M, M2L, L2L, L2P,
  * P2P, epilogue.  times[7]. */

@@ -91,6 +91,8 @@ _SIGS = {
     "bem_energy_backward": [_vp, ctypes.c_double, _vp, _vp],
     "bem_mesh_info_get": [_vp, ctypes.POINTER(bem_mesh_info)],
     "bem_set_profiling": [_vp, ctypes.c_int],
+    "bem_set_wait_budget": [_vp, ctypes.c_longlong],
+    "bem_set_device_memory_cap": [ctypes.c_size_t],
     "bem_last_phase_ms": [_vp, _vp],
     "bem_last_error": [],
     "bem_batch_solve": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
@@ -239,6 +241,14 @@ def bem_mesh_info_get(h) -> bem_mesh_info:
 
 def bem_set_profiling(h, enable: bool):
     return _check(load_library().bem_set_profiling(h, 1 if enable else 0), "bem_set_profiling")
+
+
+def bem_set_wait_budget(h, cycles: int):
+    return _check(load_library().bem_set_wait_budget(h, int(cycles)), "bem_set_wait_budget")
+
+
+def bem_set_device_memory_cap(nbytes: int):
+    return _check(load_library().bem_set_device_memory_cap(int(nbytes)), "bem_set_device_memory_cap")
 
 
 def bem_last_phase_ms(h):

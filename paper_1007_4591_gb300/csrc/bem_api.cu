@@ -8,6 +8,10 @@
 #include <cstring>
 #include <string>
 
+#include <atomic>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include "bem_internal.cuh"
 
 namespace bem {
@@ -80,6 +84,26 @@ static void sync(Mesh &m) {
         }
     }
 }
+
+static std::atomic<size_t> g_dev_used{0}, g_dev_cap{0};
+
+void dev_mem_reserve(size_t bytes) {
+    const size_t cap = g_dev_cap.load();
+    const size_t now = g_dev_used.fetch_add(bytes) + bytes;
+    if (cap && now > cap) {
+        g_dev_used.fetch_sub(bytes);
+        throw Error(BEM_ENOMEM, "device memory cap of " + std::to_string(cap) + " bytes reached");
+    }
+}
+
+void dev_mem_unreserve(size_t bytes) { g_dev_used.fetch_sub(bytes); }
+
+// NVTX range around an entry point (shows up in Nsight timelines; a no-op
+// without a tool attached)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 template <class F>
 static int guarded(F &&f) {
@@ -201,6 +225,7 @@ int bem_options_default(bem_options *opt) {
 int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, int64_t n_c,
                     double eps_in, double eps_out, const bem_options *opt, void *stream,
                     bem_mesh **out) {
+    Range rng("bem_mesh_create");
     if (!out) {
         set_last_error("bem_mesh_create: out is NULL");
         return BEM_EINVAL;
@@ -291,6 +316,7 @@ int bem_mesh_destroy(bem_mesh *m) {
 }
 
 int bem_set_charges(bem_mesh *m, const double *charges, int64_t n_c) {
+    Range rng("bem_set_charges");
     if (!m) return BEM_EINVAL;
     return guarded([&] {
         enter(*m);
@@ -312,6 +338,7 @@ int bem_set_charges(bem_mesh *m, const double *charges, int64_t n_c) {
 }
 
 int bem_matvec(bem_mesh *m, const double *x, double *y) {
+    Range rng("bem_matvec");
     if (!m || !x || !y) return BEM_EINVAL;
     return guarded([&] {
         enter(*m);
@@ -326,6 +353,7 @@ int bem_matvec(bem_mesh *m, const double *x, double *y) {
 }
 
 int bem_matvec_t(bem_mesh *m, const double *x, double *y) {
+    Range rng("bem_matvec_t");
     if (!m || !x || !y) return BEM_EINVAL;
     return guarded([&] {
         enter(*m);
@@ -349,6 +377,7 @@ static void rhs_sorted(Mesh &m, double *b_s) {
 }
 
 int bem_rhs(bem_mesh *m, double *b) {
+    Range rng("bem_rhs");
     if (!m || !b) return BEM_EINVAL;
     return guarded([&] {
         enter(*m);
@@ -361,6 +390,7 @@ int bem_rhs(bem_mesh *m, double *b) {
 }
 
 int bem_solve(bem_mesh *m, const double *x0, double *sigma, bem_solve_stats *st) {
+    Range rng("bem_solve");
     if (!m || !sigma) return BEM_EINVAL;
     int status = BEM_OK;
     int rc = guarded([&] {
@@ -420,6 +450,7 @@ static double energy_sorted(Mesh &m, const double *sig_s, double *phi_user) {
 }
 
 int bem_energy(bem_mesh *m, const double *sigma, double *dG, double *phi) {
+    Range rng("bem_energy");
     if (!m || !sigma) return BEM_EINVAL;
     return guarded([&] {
         enter(*m);
@@ -432,6 +463,7 @@ int bem_energy(bem_mesh *m, const double *sigma, double *dG, double *phi) {
 }
 
 int bem_bibee(bem_mesh *m, int variant, double *sigma_hat, double *dG) {
+    Range rng("bem_bibee");
     if (!m) return BEM_EINVAL;
     return guarded([&] {
         enter(*m);
@@ -459,6 +491,7 @@ int bem_bibee(bem_mesh *m, int variant, double *sigma_hat, double *dG) {
 }
 
 int bem_energy_backward(bem_mesh *m, double grad_out, double *dq, double *dx) {
+    Range rng("bem_energy_backward");
     if (!m) return BEM_EINVAL;
     return guarded([&] {
         enter(*m);
@@ -511,6 +544,17 @@ int bem_mesh_info_get(const bem_mesh *m, bem_mesh_info *info) {
     info->root_side = m->side;
     info->device_bytes = m->bytes();
     info->ms_build = m->ms_build;
+    return BEM_OK;
+}
+
+int bem_set_wait_budget(bem_mesh *m, long long cycles) {
+    if (!m || cycles < 0) return BEM_EINVAL;
+    m->wait_budget = cycles > 0 ? cycles : 2000000000ll;
+    return BEM_OK;
+}
+
+int bem_set_device_memory_cap(size_t bytes) {
+    g_dev_cap.store(bytes);
     return BEM_OK;
 }
 

@@ -55,6 +55,12 @@ void set_last_error(const std::string &msg);
 void ensure_smem_attr(const void *func, size_t bytes);
 
 // ------------------------------------------------------- device array (RAII)
+// Device memory held by the library's arrays, process-wide.  With a cap set
+// (bem_set_device_memory_cap) an allocation beyond it fails with BEM_ENOMEM
+// before reaching the allocator.
+void dev_mem_reserve(size_t bytes);
+void dev_mem_unreserve(size_t bytes);
+
 template <class T>
 struct DArray {
     T *p = nullptr;
@@ -71,11 +77,22 @@ struct DArray {
     void alloc(size_t count) {
         release();
         if (count == 0) count = 1;
-        BEM_CUDA(cudaMalloc((void **)&p, count * sizeof(T)));
+        dev_mem_reserve(count * sizeof(T));
+        const cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            dev_mem_unreserve(count * sizeof(T));
+            cudaGetLastError();
+            throw ::bem::Error(e == cudaErrorMemoryAllocation ? BEM_ENOMEM : BEM_ECUDA,
+                               std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
         n = count;
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            cudaFree(p);
+            dev_mem_unreserve(n * sizeof(T));
+        }
         p = nullptr;
         n = 0;
     }
@@ -165,6 +182,7 @@ struct Mesh {
     cudaEvent_t ev_enter = nullptr;
     cudaStream_t stream2 = nullptr;    // second work stream: near field next to the far field
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    long long wait_budget = 2000000000ll; // clock cycles a device-side pipeline wait may take
     // captured K' product on fixed buffers gx -> gy
     cudaGraphExec_t g_mv = nullptr;
     DArray<double> gx, gy;

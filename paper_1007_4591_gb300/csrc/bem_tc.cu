@@ -13,9 +13,10 @@
 // groups 4 KB apart).  A persistent, warp-specialised kernel runs
 // the pairs of one class as a stream of tiles (producers, one MMA thread,
 // epilogue; see k_m2l_tc) and adds each pair's local expansion into its
-// target with one bulk asynchronous reduction.  Every wait is bounded: on
-// timeout the kernel raises an error flag, waits once more (bounded) for its
-// MMAs and frees its tensor memory before returning.
+// target with one bulk asynchronous reduction.  Every wait is bounded: the
+// pipeline waits by the mesh's wait budget (bem_set_wait_budget), after which
+// the kernel raises an error flag; the last wait for its own MMAs (always
+// about a second) comes before it frees its tensor memory and returns.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -67,10 +68,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase,
+                                                  long long budget = TC_WAIT_CYCLES) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, phase))
-        if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+        if (clock64() - t0 > budget) return false;
     return true;
 }
 
@@ -130,7 +132,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
          const int4 *__restrict__ items, int nitems, int *__restrict__ next_item,
          const int *__restrict__ p_out, const int *__restrict__ p_in, int cs,
-         const float *__restrict__ Mtc, float *__restrict__ Lout, int *__restrict__ err) {
+         const float *__restrict__ Mtc, float *__restrict__ Lout, int *__restrict__ err,
+         long long budget) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     float *Bbuf = reinterpret_cast<float *>(smraw);            // [TC_NS][hi, lo][TC_BN * TC_K]
     float *Ct = Bbuf + (size_t)TC_NS * 2 * TC_BN * TC_K;       // [TC_BN][cs]
@@ -211,7 +214,7 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                 if (c + 1 < ntl) load_srcs(c + 1, nxt);
                 const int st = t % TC_NS, k = t / TC_NS;
                 const bool okB = __all_sync(0xffffffffu, k < 1 || mbar_wait_bounded(smem_u32(&emptyB[st]),
-                                                                                   (uint32_t)((k - 1) & 1)));
+                                                                                   (uint32_t)((k - 1) & 1), budget));
                 if (!okB) {
                     atomicExch(err, 1);
                     fail = true;
@@ -236,7 +239,7 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                     // item's MMAs (which read the old one) have completed
                     const int tp = t - 1;
                     const bool okA = __all_sync(0xffffffffu, t < 1 || mbar_wait_bounded(smem_u32(&fullD[tp % TC_ND]),
-                                                                                       (uint32_t)((tp / TC_ND) & 1)));
+                                                                                       (uint32_t)((tp / TC_ND) & 1), budget));
                     if (!okA) {
                         atomicExch(err, 1);
                         fail = true;
@@ -290,13 +293,13 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
             int t = 0;
             for (int i = 0; !fail; ++i) {
                 const int slot = i % TC_RING;
-                if (!mbar_wait_bounded(smem_u32(&itemFull[slot]), (uint32_t)((i / TC_RING) & 1))) {
+                if (!mbar_wait_bounded(smem_u32(&itemFull[slot]), (uint32_t)((i / TC_RING) & 1), budget)) {
                     atomicExch(err, 1);
                     break;
                 }
                 const int4 sc = s_item[slot];
                 if (sc.x < 0) break;
-                if (!mbar_wait_bounded(smem_u32(&aReady), (uint32_t)(i & 1))) {
+                if (!mbar_wait_bounded(smem_u32(&aReady), (uint32_t)(i & 1), budget)) {
                     atomicExch(err, 1);
                     break;
                 }
@@ -305,8 +308,8 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                 for (int c = 0; c < ntl; ++c, ++t) {
                     const int st = t % TC_NS, k = t / TC_NS;
                     const int d = t % TC_ND, jd = t / TC_ND;
-                    bool ok = mbar_wait_bounded(smem_u32(&fullB[st]), (uint32_t)(k & 1));
-                    if (ok && jd >= 1) ok = mbar_wait_bounded(smem_u32(&emptyD[d]), (uint32_t)((jd - 1) & 1));
+                    bool ok = mbar_wait_bounded(smem_u32(&fullB[st]), (uint32_t)(k & 1), budget);
+                    if (ok && jd >= 1) ok = mbar_wait_bounded(smem_u32(&emptyD[d]), (uint32_t)((jd - 1) & 1), budget);
                     if (!ok) {
                         atomicExch(err, 1);
                         fail = true;
@@ -347,7 +350,7 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
         int t = 0;
         for (int i = 0; !fail; ++i) {
             const int slot = i % TC_RING;
-            const bool okI = mbar_wait_bounded(smem_u32(&itemFull[slot]), (uint32_t)((i / TC_RING) & 1));
+            const bool okI = mbar_wait_bounded(smem_u32(&itemFull[slot]), (uint32_t)((i / TC_RING) & 1), budget);
             uint32_t all_ok;
             asm volatile(
                 "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
@@ -363,7 +366,7 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
             const int ntl = (sc.z + TC_BN - 1) / TC_BN;
             for (int c = 0; c < ntl; ++c, ++t) {
                 const int d = t % TC_ND, jd = t / TC_ND;
-                const bool ok = mbar_wait_bounded(smem_u32(&fullD[d]), (uint32_t)(jd & 1));
+                const bool ok = mbar_wait_bounded(smem_u32(&fullD[d]), (uint32_t)(jd & 1), budget);
                 // the four epilogue warps leave together (they meet at named barriers below)
                 asm volatile(
                     "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
@@ -524,7 +527,7 @@ void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L) {
     BEM_CUDA(cudaMemsetAsync(m.dev_err.p + 1, 0, sizeof(int), m.stream));  // work-item counter
     k_m2l_tc<<<grid, TC_THREADS, sm, m.stream>>>(m.tab->Tc_hi.p, m.tab->Tc_lo.p, t.tc_super.p, t.tc_nsuper,
                                                  m.dev_err.p + 1, t.g_out.p, t.g_in.p, cs, m.Mtc.p, L,
-                                                 m.dev_err.p);
+                                                 m.dev_err.p, m.wait_budget);
     BEM_CHECK_LAUNCH();
 }
 
