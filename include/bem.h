@@ -70,6 +70,9 @@ extern "C" {
 #define BEM_FLAG_NO_FAR 1u      /* diagnostics: drop the far field (expansions) */
 #define BEM_FLAG_NO_NEAR 2u     /* diagnostics: drop the near field (P2P + table) */
 #define BEM_FLAG_NO_NEARTAB 4u  /* diagnostics: skip the near-singular FP64 table */
+#define BEM_FLAG_CHECK_CHARGES 8u /* bem_mesh_create rejects (BEM_EINVAL) a charge the surface
+                                     does not enclose (winding number from the panels' solid
+                                     angles; checked when n_c x n_p x 7 <= 4e10, skipped above) */
 
 /* bem_options.near_table */
 #define BEM_NEAR_QUADRATURE 1

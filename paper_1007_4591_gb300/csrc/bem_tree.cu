@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "bem_internal.cuh"
 
@@ -197,6 +198,37 @@ __global__ void k_check_charges(const double *ch, int64_t n, int *bad) {
     if (i >= n) return;
     for (int k = 0; k < 4; ++k)
         if (!isfinite(ch[4 * i + k])) atomicExch(bad, 1);
+}
+
+// Winding number of the surface around each charge, times 4 pi: the sum of
+// the solid angles its panels subtend (triple-product formula for a
+// triangle's solid angle), -4 pi for a point enclosed by a closed surface
+// with outward normals and 0 outside it.  Each thread sums one charge over
+// a chunk of panels (FP32: the two values are far apart).
+__global__ void k_winding(const double *pan, int64_t np, const double *ch, int64_t nc, int64_t chunk,
+                          double *wind) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nc) return;
+    const float px = (float)ch[4 * k], py = (float)ch[4 * k + 1], pz = (float)ch[4 * k + 2];
+    const int64_t j0 = (int64_t)blockIdx.y * chunk, j1 = min(np, j0 + chunk);
+    float acc = 0.f;
+    for (int64_t j = j0; j < j1; ++j) {
+        const double *v = pan + 9 * j;
+        float r[3][3], l[3];
+        for (int a = 0; a < 3; ++a) {
+            r[a][0] = (float)v[3 * a] - px;
+            r[a][1] = (float)v[3 * a + 1] - py;
+            r[a][2] = (float)v[3 * a + 2] - pz;
+            l[a] = sqrtf(r[a][0] * r[a][0] + r[a][1] * r[a][1] + r[a][2] * r[a][2]);
+        }
+        const float cx = r[1][1] * r[2][2] - r[1][2] * r[2][1], cy = r[1][2] * r[2][0] - r[1][0] * r[2][2],
+                    cz = r[1][0] * r[2][1] - r[1][1] * r[2][0];
+        const float trip = r[0][0] * cx + r[0][1] * cy + r[0][2] * cz;
+        auto d = [&](int a, int b) { return r[a][0] * r[b][0] + r[a][1] * r[b][1] + r[a][2] * r[b][2]; };
+        const float den = l[0] * l[1] * l[2] + d(0, 1) * l[2] + d(0, 2) * l[1] + d(1, 2) * l[0];
+        acc += -2.f * atan2f(trip, den);  // positive seen from the side the normal points to
+    }
+    atomicAdd(wind + k, (double)acc);
 }
 
 // Level histogram: pair (i-1, i) of sorted keys separates cells at every
@@ -747,6 +779,25 @@ void build_geometry_and_trees(Mesh &m, const double *d_panels, const double *d_c
         BEM_CHECK_LAUNCH();
     }
     if (to_host(bad.p, s)) throw Error(BEM_EINVAL, "non-finite coordinate or zero-area panel");
+    // optional: every charge must lie inside the (closed) surface
+    if ((m.opt.flags & BEM_FLAG_CHECK_CHARGES) && m.nc > 0 && (double)m.nc * (double)np * 7.0 <= 4e10) {
+        DArray<double> wind;
+        wind.alloc(m.nc);
+        BEM_CUDA(cudaMemsetAsync(wind.p, 0, m.nc * sizeof(double), s));
+        const int64_t chunk = 4096;
+        const int64_t nsplit = std::min<int64_t>(65535, (np + chunk - 1) / chunk);
+        const int64_t ch = (np + nsplit - 1) / nsplit;
+        k_winding<<<dim3(cdiv(m.nc, TB), (unsigned)nsplit), TB, 0, s>>>(d_panels, np, d_charges, m.nc, ch, wind.p);
+        BEM_CHECK_LAUNCH();
+        constexpr double kPi = 3.14159265358979323846;
+        std::vector<double> w(m.nc);
+        BEM_CUDA(cudaMemcpyAsync(w.data(), wind.p, m.nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+        BEM_CUDA(cudaStreamSynchronize(s));
+        for (int64_t k = 0; k < m.nc; ++k)
+            if (!(std::fabs(w[k] + 4.0 * kPi) < 2.0 * kPi))
+                throw Error(BEM_EINVAL, "charge " + std::to_string(k) + " is not enclosed by the surface "
+                                        "(winding " + std::to_string(w[k] / (4.0 * kPi)) + ")");
+    }
 
     // 2. root cube: bounding cube of all vertices and charges, padded
     double lo[3], hi[3];

@@ -50,3 +50,19 @@ def test_device_memory_cap_gives_enomem(pkg):
         pkg.bem_set_device_memory_cap(0)
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out) as g:   # no cap: fine again
         assert g.info()["n_p"] == m.n_p
+
+
+def test_charge_outside_the_surface_is_rejected_when_checked(pkg):
+    m = synth.small_molecule(3)
+    flags = pkg.BEM_FLAG_CHECK_CHARGES
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, flags=flags) as g:   # all enclosed
+        assert g.info()["n_c"] == m.n_c
+    bad = m.charges.copy()
+    bad[5, :3] = [2.5 * m.radius, 0.0, 0.0]
+    with pytest.raises(pkg.BemError) as ei:
+        pkg.Mesh(m.panels, bad, m.eps_in, m.eps_out, flags=flags)
+    assert ei.value.code == pkg.BEM_EINVAL and "charge 5" in pkg.bem_last_error()
+    # two disjoint closed surfaces: each charge is enclosed by its own
+    cpx, _, _ = synth.complex_pair(s_rec=3, r_rec=10.0, n_rec=50, s_lig=2, r_lig=4.0, n_lig=20)
+    with pkg.Mesh(cpx.panels, cpx.charges, cpx.eps_in, cpx.eps_out, flags=flags) as g:
+        assert g.info()["n_c"] == cpx.n_c
