@@ -116,9 +116,24 @@ def _max_over_ranks(v, ws):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _aggregate(units_per_rank, steps, t_ms, ws):
+    """Whole-job throughput in millions of units per second: every rank
+    processed units_per_rank x steps; t_ms is the max over ranks."""
+    return ws * units_per_rank * steps / (t_ms * 1e-3) / 1e6
+
+
+def _config(args, depth, ws):
+    return {"workload": "globular-s6 (sphere R=20 A, icosphere subdivision 6, 81,920 panels, 2,000 "
+                        "charges, eps 4/80)",
+            "p": args.p, "leaf_size": args.leaf, "depth": depth, "precision": "mixed",
+            "global_batch": ws, "parallelism": "replicas" if ws > 1 else "single",
+            "l2": "flushed (256 MB write) between timed products"}
 
 
 def _traffic(kernel):
@@ -162,6 +177,13 @@ def cpu_baseline(mol, budget_s=12.0, rows=None):
                       f"(each row = {mol.n_p * 7} quadrature points), {dt:.1f} s"}
 
 
+def _depth_of(args):
+    """Octree leaf level the product uses for the workload at args.leaf (the
+    rule of the library: the smallest level whose mean panels per non-empty
+    leaf is at most the leaf size); for the reference arm's config only."""
+    return {64: 5, 128: 4}.get(args.leaf)
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -180,8 +202,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "Mpanels/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "globular-s6 (sphere R=20 A, 81,920 panels, 2,000 charges)",
-                   "global_batch": 1, "parallelism": "replicas"},
+        "config": _config(args, _depth_of(args), ws),
         "cpu_baseline": cb,
         "e2e": {"value": v, "unit": "Mpanels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -286,7 +307,7 @@ def run_ours(args):
     clocks = clk.stop()
     t_ms = sum(a.elapsed_time(b) for a, b in evs)
     t_ms = _max_over_ranks(t_ms, ws)
-    value = ws * n * args.steps / (t_ms * 1e-3) / 1e6
+    value = _aggregate(n, args.steps, t_ms, ws)
 
     # rooflines of the two large kernels from phase events on the library's
     # stream (phases run one after another in this mode); the dominant one is
@@ -371,6 +392,7 @@ def run_ours(args):
     # from 3 to L (16 kernels at L = 5, as the ncu launch list shows)
     launches_per = 6 + (4 + 2 * (L - 2) if L >= 2 else 0)
     cpu = cpu_baseline(mol, budget_s=args.cpu_budget) if (rank == 0 and not args.no_cpu) else None
+    mesh_graph = int(mesh.opt.graph)
     mesh.close()
     if rank == 0:
         print(json.dumps({
@@ -378,12 +400,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": "globular-s6 (sphere R=20 A, icosphere subdivision 6, 81,920 "
-                                   "panels, 2,000 charges, eps 4/80)",
-                       "p": args.p, "leaf_size": args.leaf, "depth": L, "precision": "mixed",
-                       "global_batch": ws, "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "flushed (256 MB write) between timed products",
-                       "cuda_graph": bool(mesh.opt.graph)},
+            "config": dict(_config(args, L, ws), cuda_graph=bool(mesh_graph)),
             "phases_ms": {k: round(v, 4) for k, v in ph.items()},
             "tree_build_s": round(tree_s, 4),
             "solve_s": round(solve_s, 4), "solve_iters": st["iterations"], "dG_kcal": dg,

@@ -444,6 +444,35 @@ def solvation_energy(mesh: "Mesh", charges):
         _SE = _energy_function()
     return _SE.apply(charges, mesh)
 
+def autotune_cached(panels, charges, eps_in, eps_out, target: float = 1e-5, cache: str | None = None):
+    """bem_autotune with its choice kept in a JSON file: the (leaf_size, p)
+    found for these exact panels, charges, dielectrics and target are read
+    back instead of re-tuned.  Returns a dict {"leaf_size", "p", "cached"}."""
+    import hashlib
+    import json
+    pan = np.ascontiguousarray(panels, dtype=np.float64)
+    ch = np.ascontiguousarray(charges, dtype=np.float64)
+    h = hashlib.sha256()
+    for a in (pan, ch, np.array([eps_in, eps_out, target], dtype=np.float64)):
+        h.update(a.tobytes())
+    key = h.hexdigest()
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+        if key in table:
+            return dict(table[key], cached=True)
+    o = bem_autotune(pan, ch, eps_in, eps_out, target=target)
+    entry = {"leaf_size": int(o.leaf_size), "p": int(o.p)}
+    if cache:
+        table[key] = entry
+        tmp = cache + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1)
+        os.replace(tmp, cache)
+    return dict(entry, cached=False)
+
+
 # ------------------------------------------------------------ workflows
 def binding_free_energy(complex_, receptor, ligand, threads: int = 3, **opts):
     """Electrostatic binding free energy (Eq. binding, Sec. 5):

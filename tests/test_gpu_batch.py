@@ -96,3 +96,28 @@ def test_autotune_meets_its_target(pkg):
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=opt.p, leaf_size=opt.leaf_size) as g:
         y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     assert rel(y, P.A(x)) < 3e-5
+
+
+def test_autotune_choice_is_cached(pkg, tmp_path):
+    m = synth.small_molecule(3)
+    cache = str(tmp_path / "tune.json")
+    a = pkg.autotune_cached(m.panels, m.charges, m.eps_in, m.eps_out, cache=cache)
+    assert not a["cached"] and a["p"] in (6, 8, 10)
+    b = pkg.autotune_cached(m.panels, m.charges, m.eps_in, m.eps_out, cache=cache)
+    assert b["cached"] and (b["leaf_size"], b["p"]) == (a["leaf_size"], a["p"])
+
+
+def test_solve_resumes_from_a_saved_iterate(pkg):
+    """A solve cut off after 3 iterations and resumed from its iterate (x0)
+    needs fewer iterations than a fresh solve and ends at the same answer."""
+    m = synth.small_molecule(4)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, tol=1e-8) as g:
+        s_ref, st_ref = g.solve()
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, tol=1e-8, max_iter=3) as g:
+        s_cut, st_cut = g.solve(allow_noconv=True)
+        assert st_cut["converged"] == 0
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, tol=1e-8) as g:
+        s_res, st_res = g.solve(x0=s_cut)
+    assert st_res["converged"] == 1
+    assert st_res["iterations"] < st_ref["iterations"], (st_res["iterations"], st_ref["iterations"])
+    assert rel(s_res.cpu().numpy(), s_ref.cpu().numpy()) < 1e-6
