@@ -77,6 +77,9 @@ def _load():
             "oracle_panel_dn": (ctypes.c_double, [d, d, d]),
             "oracle_kprime_rows_near_exact": (None, [i64, ci, d, d, d, d, d, d, d, i64,
                                                      ctypes.POINTER(ctypes.c_int64), d]),
+            "oracle_kprime_rows_galerkin": (None, [i64, ci, d, d, d, d, d, d, d, i64,
+                                                   ctypes.POINTER(ctypes.c_int64), d]),
+            "oracle_bq_galerkin": (None, [i64, ci, d, d, d, d, i64, d, d, d]),
             "oracle_num_threads": (ci, []),
             "oracle_set_threads": (None, [ci]),
         }
@@ -189,6 +192,35 @@ class Problem:
                                               rows.shape[0],
                                               rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _p(y))
         return y
+
+    def kprime_rows_galerkin(self, x, rows):
+        """Rows of the Galerkin K' x: each row averaged over its panel by the
+        rule, the near-singular inner integrals exact."""
+        x = _c(x)
+        rows = _c(rows, np.int64)
+        y = np.empty(rows.shape[0])
+        _load().oracle_kprime_rows_galerkin(self.n, self.nq, _p(self.cen), _p(self.nrm), _p(self.area),
+                                            _p(self.panels), _p(self.qp), _p(self.qw), _p(x),
+                                            rows.shape[0],
+                                            rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _p(y))
+        return y
+
+    def kprime_galerkin(self, x):
+        return self.kprime_rows_galerkin(x, np.arange(self.n))
+
+    def bq_galerkin(self, q=None):
+        """Normal field of the charges averaged over each panel by the rule."""
+        q = self.q if q is None else _c(q)
+        E = np.empty(self.n)
+        _load().oracle_bq_galerkin(self.n, self.nq, _p(self.nrm), _p(self.area), _p(self.qp), _p(self.qw),
+                                   self.nc, _p(self.xq), _p(q), _p(E))
+        return E
+
+    def solve_galerkin(self, tol: float = 1e-10, restart: int = 30, maxiter: int = 500):
+        """sigma from (I + Ehat K'_G) sigma = -Ehat B_G q (Galerkin form)."""
+        b = -self.ehat * self.bq_galerkin()
+        op = lambda v: _c(v) + self.ehat * self.kprime_galerkin(v)
+        return gmres(op, b, tol=tol, restart=restart, maxiter=maxiter)
 
     def kprime_t(self, x):
         x = _c(x)

@@ -311,6 +311,63 @@ void oracle_kprime_rows_near_exact(int64_t n, int nq, const double *cen, const d
     }
 }
 
+/* Galerkin rows (Sec. 2.1 states the problem in Galerkin form; with a
+ * piecewise-constant basis and test functions the row of panel i is the
+ * average over T_i of the collocation row): the outer integral over T_i by
+ * the quadrature rule at the points y_iq (weights w_q = qw/A_i), the inner
+ * integral over T_j exact for the near-singular pairs
+ * (|c_i - c_j| <= 2.5 sqrt(A_i)) and by the rule for all others.  j = i
+ * adds nothing (the outer and inner points lie in one plane). */
+void oracle_kprime_rows_galerkin(int64_t n, int nq, const double *cen, const double *nrm,
+                                 const double *area, const double *panels, const double *qp,
+                                 const double *qw, const double *x, int64_t nrows,
+                                 const int64_t *rows, double *y)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t i = rows[r];
+        const double tau = 2.5 * sqrt(area[i]);
+        double acc = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            const double *t = qp + 3 * (i * nq + q);
+            const double wq = qw[i * nq + q] / area[i];
+            double row = 0.0;
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                double d[3];
+                sub3(cen + 3 * i, cen + 3 * j, d);
+                double kij = 0.0;
+                if (dot3(d, d) <= tau * tau)
+                    kij = oracle_panel_dn(t, nrm + 3 * i, panels + 9 * j);
+                else
+                    for (int s2 = 0; s2 < nq; ++s2)
+                        kij += qw[j * nq + s2] * dn_green(t, nrm + 3 * i, qp + 3 * (j * nq + s2));
+                row += kij * x[j];
+            }
+            acc += wq * row;
+        }
+        y[r] = acc;
+    }
+}
+
+/* Galerkin right-hand side field: the normal field of the charges averaged
+ * over each panel by the rule, E_i = sum_q (qw_iq / A_i) E_n(y_iq). */
+void oracle_bq_galerkin(int64_t n, int nq, const double *nrm, const double *area, const double *qp,
+                        const double *qw, int64_t nc, const double *xq, const double *q, double *E)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int s2 = 0; s2 < nq; ++s2) {
+            double e = 0.0;
+            for (int64_t k = 0; k < nc; ++k)
+                e += q[k] * dn_green(qp + 3 * (i * nq + s2), nrm + 3 * i, xq + 3 * k);
+            acc += qw[i * nq + s2] / area[i] * e;
+        }
+        E[i] = acc;
+    }
+}
+
 /* E = B q: normal field of the point charges at the collocation points. */
 void oracle_bq(int64_t n, const double *cen, const double *nrm, int64_t nc,
                const double *xq /*[nc][3]*/, const double *q, double *E)
