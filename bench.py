@@ -277,6 +277,8 @@ def run_ours(args):
     opts = dict(p=args.p, leaf_size=args.leaf, precision=0, m2l_mode=args.m2l_mode)
     if args.graph >= 0:
         opts["graph"] = args.graph
+    if args.galerkin:
+        opts["galerkin"] = 1
     t0 = time.perf_counter()
     mesh = pkg.Mesh(mol.panels, mol.charges, mol.eps_in, mol.eps_out, **opts)
     tree_s = time.perf_counter() - t0
@@ -400,7 +402,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": dict(_config(args, L, ws), cuda_graph=bool(mesh_graph)),
+            "config": dict(_config(args, L, ws), cuda_graph=bool(mesh_graph),
+                           form="galerkin" if args.galerkin else "collocation"),
             "phases_ms": {k: round(v, 4) for k, v in ph.items()},
             "tree_build_s": round(tree_s, 4),
             "solve_s": round(solve_s, 4), "solve_iters": st["iterations"], "dG_kcal": dg,
@@ -598,6 +601,8 @@ def main():
     ap.add_argument("--m2l-mode", type=int, default=0)
     ap.add_argument("--graph", type=int, default=-1, help="1/0: replay the product as a CUDA graph or not "
                     "(default: the library's default)")
+    ap.add_argument("--galerkin", type=int, default=0, help="1: the Galerkin form of the operator "
+                    "(rows averaged over each panel) instead of collocation")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")

@@ -103,6 +103,12 @@ typedef struct bem_options {
     int graph;         /* 1 = replay the K' product as a captured CUDA graph; 0 (default) = launch
                           its kernels on the mesh's two prioritised streams, where the near
                           and far fields overlap better than in a replayed graph */
+    int galerkin;      /* 0 (default) = collocation at the centroids; 1 = Galerkin form with
+                          piecewise-constant functions (Sec. 2.1): every row of K' and of the
+                          right-hand side field averaged over its panel by the quadrature rule,
+                          near-singular inner integrals exact.  Product, RHS, solve, energy and
+                          BIBEE; the transposed product and the gradients return
+                          BEM_EUNSUPPORTED in this form. */
 } bem_options;
 
 #define BEM_M2L_AUTO 0

@@ -56,7 +56,8 @@ class bem_options(ctypes.Structure):
                 ("depth", ctypes.c_int), ("quad_points", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("flags", ctypes.c_uint), ("near_table", ctypes.c_int),
-                ("charge_mode", ctypes.c_int), ("m2l_mode", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("charge_mode", ctypes.c_int), ("m2l_mode", ctypes.c_int), ("graph", ctypes.c_int),
+                ("galerkin", ctypes.c_int)]
 
 
 class bem_solve_stats(ctypes.Structure):

@@ -183,6 +183,7 @@ __global__ void k_apply_At(const double *x, const double *ktx, const int *off, c
 }
 
 void matvec_t_sorted(Mesh &m, const double *xs, double *ys) {
+    if (m.opt.galerkin) throw Error(BEM_EUNSUPPORTED, "the transposed product is not built for the Galerkin form");
     const bool nt = m.nt_nnz > 0 && !(m.opt.flags & (BEM_FLAG_NO_NEARTAB | BEM_FLAG_NO_NEAR));
     fmm_pass_t(m, xs, m.zs.p);
     k_apply_At<<<cdiv(4 * m.np, 256), 256, 0, m.stream>>>(xs, m.zs.p, nt ? m.ntT_off.p : nullptr,
@@ -214,6 +215,7 @@ __global__ void k_gradients(const double *cs4, const double *bl4, const double *
 void build_qp_of_panel(Mesh &m);
 
 void adjoint_gradients(Mesh &m, double grad_out, double *dq_s, double *dx_s) {
+    if (m.opt.galerkin) throw Error(BEM_EUNSUPPORTED, "gradients are not built for the Galerkin form");
     cudaStream_t s = m.stream;
     build_qp_of_panel(m);
     const int64_t np = m.np, nc = m.nc;

@@ -186,6 +186,7 @@ static void validate_options(const bem_options &o) {
     if (o.depth > MORTON_BITS) throw Error(BEM_EINVAL, "depth must be <= 21");
     if (o.quad_points != 1 && o.quad_points != 7) throw Error(BEM_EINVAL, "quad_points must be 1 or 7");
     if (o.near_table < 0 || o.near_table > BEM_NEAR_EXACT) throw Error(BEM_EINVAL, "near_table must be 0, 1 or 2");
+    if (o.galerkin != 0 && o.galerkin != 1) throw Error(BEM_EINVAL, "galerkin must be 0 or 1");
     if (o.gmres_restart < 1 || o.gmres_restart > 200) throw Error(BEM_EINVAL, "gmres_restart must be in 1..200");
     if (o.max_iter < 1) throw Error(BEM_EINVAL, "max_iter must be positive");
     if (!(o.tol > 0.0)) throw Error(BEM_EINVAL, "tol must be positive");
@@ -219,6 +220,7 @@ int bem_options_default(bem_options *opt) {
     opt->charge_mode = BEM_CHARGE_AUTO;
     opt->m2l_mode = BEM_M2L_AUTO;
     opt->graph = 0;
+    opt->galerkin = 0;
     return BEM_OK;
 }
 
@@ -269,6 +271,7 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
         const double *dp = dev_in(*m, panels, (size_t)n_p * 9, sp);
         const double *dc = n_c > 0 ? dev_in(*m, charges, (size_t)n_c * 4, sc) : nullptr;
         build_geometry_and_trees(*m, dp, dc);
+        if (m->opt.galerkin) build_galerkin_geometry(*m);
         build_tables(*m);
         build_translation_groups(*m, m->tp);
         build_translation_groups(*m, m->tc);
@@ -372,7 +375,7 @@ static void rhs_sorted(Mesh &m, double *b_s) {
         BEM_CUDA(cudaMemsetAsync(b_s, 0, m.np * sizeof(double), m.stream));
         return;
     }
-    charge_pass(m, SRC_CHARGE, TGT_CEN_DN, nullptr, m.zs.p);
+    charge_pass(m, SRC_CHARGE, m.opt.galerkin ? TGT_QUAD_DN : TGT_CEN_DN, nullptr, m.zs.p);
     axpby(m, -m.ehat, m.zs.p, 0.0, m.zs.p, b_s, m.np);
 }
 
@@ -476,7 +479,7 @@ int bem_bibee(bem_mesh *m, int variant, double *sigma_hat, double *dG) {
         const double f = -m->ehat / (1.0 + m->ehat * lam);
         if (m->nc == 0) BEM_CUDA(cudaMemsetAsync(m->xs.p, 0, m->np * sizeof(double), m->stream));
         else {
-            charge_pass(*m, SRC_CHARGE, TGT_CEN_DN, nullptr, m->zs.p);
+            charge_pass(*m, SRC_CHARGE, m->opt.galerkin ? TGT_QUAD_DN : TGT_CEN_DN, nullptr, m->zs.p);
             axpby(*m, f, m->zs.p, 0.0, m->zs.p, m->xs.p, m->np);
         }
         if (sigma_hat) {

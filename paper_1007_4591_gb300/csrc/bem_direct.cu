@@ -36,12 +36,13 @@ k_direct(int64_t ntgt, int64_t nsrc, int64_t chunk, const double *tpos, const do
     const int64_t i = blockIdx.x * (int64_t)DIRECT_THREADS + threadIdx.x;
     const int64_t sb = (int64_t)blockIdx.y * chunk;
     const int64_t se = min(nsrc, sb + chunk);
+    constexpr bool DN = TGT == TGT_CEN_DN || TGT == TGT_QUAD_DN;  // normal field, else potential
     T cx = 0, cy = 0, cz = 0, nx = 0, ny = 0, nz = 0;
     if (i < ntgt) {
         cx = (T)(tpos[3 * i] - ox);
         cy = (T)(tpos[3 * i + 1] - oy);
         cz = (T)(tpos[3 * i + 2] - oz);
-        if (TGT == TGT_CEN_DN) {
+        if (DN) {
             nx = (T)tnrm[3 * i];
             ny = (T)tnrm[3 * i + 1];
             nz = (T)tnrm[3 * i + 2];
@@ -72,7 +73,7 @@ k_direct(int64_t ntgt, int64_t nsrc, int64_t chunk, const double *tpos, const do
             const T dx = cx - y.x, dy = cy - y.y, dz = cz - y.z;
             const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
             const T ri = rsqd(r2);
-            if (TGT == TGT_CEN_DN) {
+            if (DN) {
                 const T nd = fma(nx, dx, fma(ny, dy, nz * dz));
                 acc = fma(y.w * nd, ri * ri * ri, acc);
             } else {
@@ -81,7 +82,7 @@ k_direct(int64_t ntgt, int64_t nsrc, int64_t chunk, const double *tpos, const do
         }
         outer += acc;
     }
-    if (i < ntgt) part[(size_t)blockIdx.y * ntgt + i] = (TGT == TGT_CEN_DN) ? -outer : outer;
+    if (i < ntgt) part[(size_t)blockIdx.y * ntgt + i] = DN ? -outer : outer;
 }
 
 template <class T>
@@ -93,15 +94,35 @@ __global__ void k_direct_reduce(const T *part, int nsplit, int64_t n, double sca
     out[i] = scale * s;
 }
 
+// out_j = sum_q (qw_jq / A_j) v_jq: the rule's average over panel j
+__global__ void k_panel_avg(const double *v, const int *qp_of_panel, const double *qw, const double *area,
+                            int nq, int64_t np, double *out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    double a = 0.0;
+    for (int q = 0; q < nq; ++q) {
+        const int k = qp_of_panel[j * nq + q];
+        a += qw[k] * v[k];
+    }
+    out[j] = a / area[j];
+}
+
 template <class T>
 static void direct_impl(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, double *out,
                         DArray<T> &part) {
     cudaStream_t s = m.stream;
-    const int64_t ntgt = (tk == TGT_CEN_DN) ? m.np : m.nc;
+    const int64_t ntgt = (tk == TGT_CEN_DN) ? m.np : (tk == TGT_QUAD_DN ? m.nqp : m.nc);
+    // Galerkin rows: the values at the quadrature points, then the rule's
+    // average over each panel
+    double *const final_out = out;
+    if (tk == TGT_QUAD_DN) {
+        if (!m.nrmq64.p || m.gq_tmp.n < (size_t)m.nqp) throw Error(BEM_EUNSUPPORTED, "Galerkin geometry not built");
+        out = m.gq_tmp.p;
+    }
     const int64_t nsrc = (sk == SRC_QUAD) ? m.nqp : m.nc;
     if (ntgt == 0) return;
     if (nsrc == 0) {
-        BEM_CUDA(cudaMemsetAsync(out, 0, ntgt * sizeof(double), s));
+        BEM_CUDA(cudaMemsetAsync(final_out, 0, (tk == TGT_QUAD_DN ? m.np : ntgt) * sizeof(double), s));
         return;
     }
     const int tblocks = cdiv(ntgt, DIRECT_THREADS);
@@ -115,7 +136,7 @@ static void direct_impl(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, dou
     if (part.n < need) part.alloc(need);
     const double ox = m.root_min[0] + 0.5 * m.side, oy = m.root_min[1] + 0.5 * m.side,
                  oz = m.root_min[2] + 0.5 * m.side;
-    const double *tpos = (tk == TGT_CEN_DN) ? m.cen64.p : m.chgg64.p;
+    const double *tpos = (tk == TGT_CEN_DN) ? m.cen64.p : (tk == TGT_QUAD_DN ? m.qpg64.p : m.chgg64.p);
     const double *spos = (sk == SRC_QUAD) ? m.qpg64.p : m.chgg64.p;
     const double *sw = (sk == SRC_QUAD) ? m.qw64.p : m.q64.p;
     dim3 grid(tblocks, nsplit);
@@ -128,12 +149,22 @@ static void direct_impl(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, dou
     else if (sk == SRC_QUAD && tk == TGT_CEN_DN)
         k_direct<T, SRC_QUAD, TGT_CEN_DN><<<grid, DIRECT_THREADS, 0, s>>>(
             ntgt, nsrc, chunk, tpos, m.nrm64.p, spos, sw, m.qp_panel.p, dens, ox, oy, oz, part.p);
+    else if (sk == SRC_CHARGE && tk == TGT_QUAD_DN)
+        k_direct<T, SRC_CHARGE, TGT_QUAD_DN><<<grid, DIRECT_THREADS, 0, s>>>(
+            ntgt, nsrc, chunk, tpos, m.nrmq64.p, spos, sw, nullptr, dens, ox, oy, oz, part.p);
+    else if (sk == SRC_QUAD && tk == TGT_QUAD_DN)
+        throw Error(BEM_EUNSUPPORTED, "direct quadrature-to-quadrature sums not built");
     else
         k_direct<T, SRC_CHARGE, TGT_CHG_PHI><<<grid, DIRECT_THREADS, 0, s>>>(
             ntgt, nsrc, chunk, tpos, nullptr, spos, sw, nullptr, dens, ox, oy, oz, part.p);
     BEM_CHECK_LAUNCH();
     k_direct_reduce<T><<<cdiv(ntgt, 256), 256, 0, s>>>(part.p, nsplit, ntgt, 1.0 / FOUR_PI, out);
     BEM_CHECK_LAUNCH();
+    if (tk == TGT_QUAD_DN) {
+        k_panel_avg<<<cdiv(m.np, 256), 256, 0, s>>>(out, m.qp_of_panel.p, m.qw64.p, m.area64.p, (int)m.nq,
+                                                    m.np, final_out);
+        BEM_CHECK_LAUNCH();
+    }
 }
 
 void direct_pass(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, double *out) {

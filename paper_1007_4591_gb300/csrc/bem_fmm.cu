@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(128) k_l2p(TreeView tv, const typename V4T<T>:
     const int W = 2 * p + 1;
     cpx<T> *Lf = reinterpret_cast<cpx<T> *>(smraw);
     const int leaf = blockIdx.x;
-    const int *beg = TGT == TGT_CEN_DN ? tv.cen_beg : (TGT == TGT_QUAD_PHI ? tv.qp_beg : tv.chg_beg);
+    constexpr bool DN = TGT == TGT_CEN_DN || TGT == TGT_QUAD_DN;  // normal field, else potential
+    const int *beg = TGT == TGT_CEN_DN ? tv.cen_beg : (TGT == TGT_CHG_PHI ? tv.chg_beg : tv.qp_beg);
     const int b = beg[leaf], e = beg[leaf + 1];
     if (b == e) return;
     load_full<T>(L + (size_t)(tv.leaf0 + leaf) * cs, p, Lf);
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(128) k_l2p(TreeView tv, const typename V4T<T>:
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
         const typename V4T<T>::t r = tgt[i];
         const T x = r.x * inv_h, y = r.y * inv_h, z = r.z * inv_h;
-        if (TGT == TGT_CEN_DN) {
+        if (DN) {
             cpx<T> a10, a11;
             a10.x = a10.y = a11.x = a11.y = 0;
             regular_solid<T>(x, y, z, p - 1, [&](int n, int m, T re, T im) {
@@ -413,7 +414,8 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
     __shared__ T s_off[27][3];
     __shared__ T s_part[P2PF_THREADS * 4];
     const int leaf = tv.p2p_order[blockIdx.x];  // heaviest leaves first
-    const int *tb_ = TGT == TGT_CEN_DN ? tv.cen_beg : tv.chg_beg;
+    constexpr bool DN = TGT == TGT_CEN_DN || TGT == TGT_QUAD_DN;  // normal field, else potential
+    const int *tb_ = TGT == TGT_CEN_DN ? tv.cen_beg : (TGT == TGT_QUAD_DN ? tv.qp_beg : tv.chg_beg);
     const int *sb_ = SRC == SRC_QUAD ? tv.qp_beg : tv.chg_beg;
     const int tb = tb_[leaf], te = tb_[leaf + 1];
     if (tb == te) return;
@@ -472,7 +474,7 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
                 a = cv.x;
                 b = cv.y;
                 c = cv.z;
-                if (TGT == TGT_CEN_DN) {
+                if (DN) {
                     const V4 nv = nrm[tb + t0 + ti];
                     d = nv.x;
                     e = nv.y;
@@ -517,7 +519,7 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
                         const v2 dx = P::sub(cx[q], yx), dy = P::sub(cy[q], yy), dz = P::sub(cz[q], yz);
                         const v2 r2 = P::fma(dx, dx, P::fma(dy, dy, P::fma(dz, dz, EPS2)));
                         const v2 ri = P::mk(rsq(r2.x), rsq(r2.y));
-                        if (TGT == TGT_CEN_DN) {
+                        if (DN) {
                             const v2 nd = P::fma(nx[q], dx, P::fma(ny[q], dy, P::mul(nz[q], dz)));
                             const v2 ri3 = P::mul(P::mul(ri, ri), ri);
                             acc[q] = P::fma(P::mul(yw, nd), ri3, acc[q]);
@@ -538,7 +540,7 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
             const int gr = threadIdx.x / P2P_TPT, q = threadIdx.x - gr * P2P_TPT;
             T a = 0;
             for (int k = 0; k < G; ++k) a += s_part[(gr * G + k) * P2P_TPT + q];
-            out[tb + t0 + threadIdx.x] = (TGT == TGT_CEN_DN) ? -a : a;
+            out[tb + t0 + threadIdx.x] = DN ? -a : a;
         }
     }
 }
@@ -688,7 +690,8 @@ k_p2p_t(TreeView tv, const typename V4T<T>::t *cen, const typename V4T<T>::t *nr
 // z_j = 1/(4 pi) sum_q A_j w_q (far_q + near_q) over the points of panel j
 template <class T>
 __global__ void k_panel_reduce(const T *far, const T *near, const int *qp_of_panel,
-                               const double *qw, int nq, int64_t np, double *out) {
+                               const double *qw, int nq, int64_t np, double *out,
+                               const double *area = nullptr) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= np) return;
     double a = 0.0;
@@ -698,7 +701,8 @@ __global__ void k_panel_reduce(const T *far, const T *near, const int *qp_of_pan
         if (far) v += (double)far[k];
         a += qw[k] * v;
     }
-    out[j] = a / FOUR_PI;
+    // with area: the rule's average over the panel (weights qw / A_j)
+    out[j] = (area ? a / area[j] : a) / FOUR_PI;
 }
 
 // ------------------------------------------------------ near-singular table
@@ -1459,6 +1463,7 @@ struct PassBufs<float> {
     static const float *Ol2l(Mesh &m) { return m.tab->Ol2l_f.p; }
     static const float4 *cen(Mesh &m) { return m.cen32.p; }
     static const float4 *nrm(Mesh &m) { return m.nrm32.p; }
+    static const float4 *nrmq(Mesh &m) { return m.nrmq32.p; }
     static const float4 *qp(Mesh &m) { return m.qp32.p; }
     static const float4 *chg(Mesh &m) { return m.chg32.p; }
     static float4 *str(Mesh &m) { return m.str32.p; }
@@ -1476,6 +1481,7 @@ struct PassBufs<double> {
     static const double *Ol2l(Mesh &m) { return m.tab->Ol2l_d.p; }
     static const double4 *cen(Mesh &m) { return m.cen64r.p; }
     static const double4 *nrm(Mesh &m) { return m.nrm64r.p; }
+    static const double4 *nrmq(Mesh &m) { return m.nrmq64r.p; }
     static const double4 *qp(Mesh &m) { return m.qp64r.p; }
     static const double4 *chg(Mesh &m) { return m.chg64r.p; }
     static double4 *str(Mesh &m) { return m.str64.p; }
@@ -1524,12 +1530,13 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
     const int W = 2 * p + 1, W2 = 4 * p + 1;
     const double h = m.side / (double)(1 << t.L);
     const T inv_h = (T)(1.0 / h);
-    const int64_t ntgt = (tk == TGT_CEN_DN) ? m.np : m.nc;
+    const int64_t ntgt = (tk == TGT_CEN_DN) ? m.np : (tk == TGT_QUAD_DN ? m.nqp : m.nc);
     const bool far = !(m.opt.flags & BEM_FLAG_NO_FAR) && t.L >= 2;
     const bool near = !(m.opt.flags & BEM_FLAG_NO_NEAR);
     const typename V4T<T>::t *srec = (sk == SRC_QUAD) ? B::qp(m) : B::chg(m);
-    const typename V4T<T>::t *trec = (tk == TGT_CEN_DN) ? B::cen(m) : B::chg(m);
-    const typename V4T<T>::t *nrec = B::nrm(m);
+    const typename V4T<T>::t *trec = (tk == TGT_CEN_DN) ? B::cen(m) : (tk == TGT_QUAD_DN ? B::qp(m) : B::chg(m));
+    const typename V4T<T>::t *nrec = (tk == TGT_QUAD_DN) ? B::nrmq(m) : B::nrm(m);
+    if (tk == TGT_QUAD_DN && !nrec) throw Error(BEM_EUNSUPPORTED, "quadrature-point normals not built (galerkin = 0)");
     T *far_b = B::far(m), *near_b = B::near(m);
     ev_rec(m, timed, 0);
     // strength records of this pass
@@ -1560,6 +1567,10 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             go(k_p2p<T, SRC_CHARGE, TGT_CEN_DN, 128>, k_p2p<T, SRC_CHARGE, TGT_CEN_DN, 256>);
         else if (sk == SRC_QUAD && tk == TGT_CHG_PHI)
             go(k_p2p<T, SRC_QUAD, TGT_CHG_PHI, 128>, k_p2p<T, SRC_QUAD, TGT_CHG_PHI, 256>);
+        else if (sk == SRC_QUAD && tk == TGT_QUAD_DN)
+            go(k_p2p<T, SRC_QUAD, TGT_QUAD_DN, 128>, k_p2p<T, SRC_QUAD, TGT_QUAD_DN, 256>);
+        else if (sk == SRC_CHARGE && tk == TGT_QUAD_DN)
+            go(k_p2p<T, SRC_CHARGE, TGT_QUAD_DN, 128>, k_p2p<T, SRC_CHARGE, TGT_QUAD_DN, 256>);
         else
             go(k_p2p<T, SRC_CHARGE, TGT_CHG_PHI, 128>, k_p2p<T, SRC_CHARGE, TGT_CHG_PHI, 256>);
         BEM_CHECK_LAUNCH();
@@ -1646,6 +1657,10 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
                 auto kern = k_l2p<T, TGT_CEN_DN>;
                 set_smem<T>(kern, sm);
                 kern<<<t.nleaf, l2p_threads(ntgt, t.nleaf), sm, s>>>(tv, trec, nrec, p, cs, inv_h, L, far_b);
+            } else if (tk == TGT_QUAD_DN) {
+                auto kern = k_l2p<T, TGT_QUAD_DN>;
+                set_smem<T>(kern, sm);
+                kern<<<t.nleaf, l2p_threads(ntgt, t.nleaf), sm, s>>>(tv, trec, nrec, p, cs, inv_h, L, far_b);
             } else {
                 auto kern = k_l2p<T, TGT_CHG_PHI>;
                 set_smem<T>(kern, sm);
@@ -1660,8 +1675,16 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
     if (near && !conc) launch_near(s);
     ev_rec(m, timed, 6);
     if (near && conc) BEM_CUDA(cudaStreamWaitEvent(s, m.ev_join, 0));
-    k_combine<T><<<cdiv(ntgt, 256), 256, 0, s>>>(far ? far_b : nullptr, near ? near_b : nullptr,
-                                                  ntgt, 1.0 / FOUR_PI, out);
+    if (tk == TGT_QUAD_DN) {
+        // Galerkin rows: the rule's average over each panel of its points' values
+        build_qp_of_panel(m);
+        k_panel_reduce<T><<<cdiv(m.np, 256), 256, 0, s>>>(far ? far_b : nullptr, near ? near_b : nullptr,
+                                                          m.qp_of_panel.p, m.qw64.p, (int)m.nq, m.np, out,
+                                                          m.area64.p);
+    } else {
+        k_combine<T><<<cdiv(ntgt, 256), 256, 0, s>>>(far ? far_b : nullptr, near ? near_b : nullptr,
+                                                      ntgt, 1.0 / FOUR_PI, out);
+    }
     BEM_CHECK_LAUNCH();
 }
 
@@ -1753,7 +1776,125 @@ static void transpose_near_table(Mesh &m) {
     BEM_CUDA(cudaStreamSynchronize(m.stream));
 }
 
+// Per-quadrature-point normals (the normal of the point's panel) in the
+// sorted quadrature order: relative records like nrm32 / nrm64r and absolute
+// f64 triples.
+template <class V>
+__global__ void k_qp_normals(const int *qp_panel, int64_t nqp, const V *nrm_rec, const double *nrm64, V *out_rec,
+                             double *out64) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nqp) return;
+    const int j = qp_panel[k];
+    out_rec[k] = nrm_rec[j];
+    for (int c = 0; c < 3; ++c) out64[3 * k + c] = nrm64[3 * j + c];
+}
+
+void build_galerkin_geometry(Mesh &m) {
+    cudaStream_t s = m.stream;
+    build_qp_of_panel(m);
+    m.nrmq64.alloc((size_t)m.nqp * 3);
+    m.gq_tmp.alloc((size_t)m.nqp);
+    if (m.opt.precision == BEM_MIXED) {
+        m.nrmq32.alloc(m.nqp);
+        k_qp_normals<float4><<<cdiv(m.nqp, 256), 256, 0, s>>>(m.qp_panel.p, m.nqp, m.nrm32.p, m.nrm64.p,
+                                                             m.nrmq32.p, m.nrmq64.p);
+    } else {
+        m.nrmq64r.alloc(m.nqp);
+        k_qp_normals<double4><<<cdiv(m.nqp, 256), 256, 0, s>>>(m.qp_panel.p, m.nqp, m.nrm64r.p, m.nrm64.p,
+                                                              m.nrmq64r.p, m.nrmq64.p);
+    }
+    BEM_CHECK_LAUNCH();
+}
+
+// Near-singular table of the Galerkin rows.  For panel i and each panel j
+// whose centroid lies within 2.5 sqrt(A_i) (j != i), the correction
+//   D_ij = sum_q w_iq [ exact_j(y_iq) - sum_q' A_j w_q' dn(y_iq; y_jq') ] / (4 pi)
+// (w_iq = qw / A_i the rule's weights on panel i, exact_j the exact
+// flat-triangle integral of the normal field at y_iq with normal n_i) takes
+// the pair from its quadrature value, which the near field and the
+// expansions produce, to the exact inner integral.
+__global__ void k_near_table_galerkin(int64_t np, int nq, const int *nbr_off, const int *nbr, const int *cen_beg,
+                                      const int *leaf_of_cen, const double *cen64, const double *nrm64,
+                                      const double *area64, const double *qpg64, const double *qw64,
+                                      const int *qp_of_panel, const double *pan, const int *perm,
+                                      const int *off, int *cnt, int *col, double *val) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const int T_ = leaf_of_cen[i];
+    const double ci[3] = {cen64[3 * i], cen64[3 * i + 1], cen64[3 * i + 2]};
+    const double ni[3] = {nrm64[3 * i], nrm64[3 * i + 1], nrm64[3 * i + 2]};
+    const double tau = 2.5 * sqrt(area64[i]);
+    int n = 0;
+    const bool fill = off != nullptr;
+    const int base = fill ? off[i] : 0;
+    for (int e = nbr_off[T_]; e < nbr_off[T_ + 1]; ++e) {
+        const int S = nbr[e];
+        for (int j = cen_beg[S]; j < cen_beg[S + 1]; ++j) {
+            if (j == i) continue;  // outer and inner points in one plane: nothing
+            const double dx = ci[0] - cen64[3 * j], dy = ci[1] - cen64[3 * j + 1], dz = ci[2] - cen64[3 * j + 2];
+            if (dx * dx + dy * dy + dz * dz > tau * tau) continue;
+            if (fill) {
+                double acc = 0.0;
+                for (int q = 0; q < nq; ++q) {
+                    const int k = qp_of_panel[i * nq + q];
+                    const double t[3] = {qpg64[3 * k], qpg64[3 * k + 1], qpg64[3 * k + 2]};
+                    double quad = 0.0;
+                    for (int q2 = 0; q2 < nq; ++q2) {
+                        const int k2 = qp_of_panel[(int64_t)j * nq + q2];
+                        const double ex = t[0] - qpg64[3 * k2], ey = t[1] - qpg64[3 * k2 + 1],
+                                     ez = t[2] - qpg64[3 * k2 + 2];
+                        const double r2 = ex * ex + ey * ey + ez * ez;
+                        quad += -qw64[k2] * (ex * ni[0] + ey * ni[1] + ez * ni[2]) / (r2 * sqrt(r2));
+                    }
+                    const double ex = tri_normal_field_4pi(t, ni, pan + 9 * (int64_t)perm[j]);
+                    acc += qw64[k] / area64[i] * (ex - quad);
+                }
+                col[base + n] = j;
+                val[base + n] = acc / FOUR_PI;
+            }
+            ++n;
+        }
+    }
+    if (!fill) cnt[i] = n;
+}
+
+static void near_table_galerkin(Mesh &m, const double *panels) {
+    cudaStream_t s = m.stream;
+    const Tree &t = m.tp;
+    const int64_t np = m.np;
+    DArray<int> leaf_of, cnt;
+    leaf_of.alloc(np);
+    cnt.alloc(np + 1);
+    k_leaf_of<<<t.nleaf, 128, 0, s>>>(t.cen_beg.p, t.nleaf, leaf_of.p);
+    BEM_CHECK_LAUNCH();
+    build_qp_of_panel(m);
+    BEM_CUDA(cudaMemsetAsync(cnt.p, 0, (np + 1) * sizeof(int), s));
+    k_near_table_galerkin<<<cdiv(np, 128), 128, 0, s>>>(np, (int)m.nq, t.nbr_off.p, t.nbr.p, t.cen_beg.p, leaf_of.p,
+                                                       m.cen64.p, m.nrm64.p, m.area64.p, m.qpg64.p, m.qw64.p,
+                                                       m.qp_of_panel.p, panels, m.cen_perm.p, nullptr, cnt.p,
+                                                       nullptr, nullptr);
+    BEM_CHECK_LAUNCH();
+    m.nt_off.alloc(np + 1);
+    exclusive_scan_int(cnt.p, m.nt_off.p, (int)np + 1, s);
+    int nnz = 0;
+    BEM_CUDA(cudaMemcpyAsync(&nnz, m.nt_off.p + np, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    m.nt_nnz = nnz;
+    m.nt_col.alloc(nnz);
+    m.nt_val.alloc(nnz);
+    k_near_table_galerkin<<<cdiv(np, 128), 128, 0, s>>>(np, (int)m.nq, t.nbr_off.p, t.nbr.p, t.cen_beg.p, leaf_of.p,
+                                                       m.cen64.p, m.nrm64.p, m.area64.p, m.qpg64.p, m.qw64.p,
+                                                       m.qp_of_panel.p, panels, m.cen_perm.p, m.nt_off.p,
+                                                       nullptr, m.nt_col.p, m.nt_val.p);
+    BEM_CHECK_LAUNCH();
+    BEM_CUDA(cudaStreamSynchronize(s));
+}
+
 void build_near_table(Mesh &m, const double *panels) {
+    if (m.opt.galerkin) {  // the Galerkin rows always take the exact near-singular integrals
+        near_table_galerkin(m, panels);
+        return;
+    }
     const double *exact_pan = m.opt.near_table == BEM_NEAR_EXACT ? panels : nullptr;
     if (m.opt.precision == BEM_MIXED) near_table_impl<float>(m, exact_pan);
     else near_table_impl<double>(m, exact_pan);
@@ -1871,6 +2012,14 @@ bool is_near_field_kernel(const void *func) {
         reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CHG_PHI, 256>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CHG_PHI, 128>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CHG_PHI, 256>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_QUAD_DN, 128>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_QUAD_DN, 256>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_QUAD_DN, 128>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_QUAD_DN, 256>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_QUAD_DN, 128>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_QUAD_DN, 256>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_QUAD_DN, 128>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_QUAD_DN, 256>),
         reinterpret_cast<const void *>(k_p2p_t<float>),
         reinterpret_cast<const void *>(k_p2p_t<double>),
     };

@@ -147,7 +147,10 @@ TreeView view(const Tree &t);
 
 // Source and target kinds of one fast multipole pass.
 enum SrcKind { SRC_QUAD = 0, SRC_CHARGE = 1, SRC_DIPOLE = 2 };
-enum TgtKind { TGT_CEN_DN = 0, TGT_CHG_PHI = 1, TGT_QUAD_PHI = 2 };
+// targets: normal field at the centroids (collocation), potential at the
+// charges, potential at the quadrature points, normal field at the
+// quadrature points with their panel's normal (Galerkin rows)
+enum TgtKind { TGT_CEN_DN = 0, TGT_CHG_PHI = 1, TGT_QUAD_PHI = 2, TGT_QUAD_DN = 3 };
 
 struct Mesh;
 
@@ -202,6 +205,12 @@ struct Mesh {
     DArray<double> area64;       // [np]
     DArray<float4> cen32, nrm32; // relative centroid / normal (mixed precision)
     DArray<double4> cen64r, nrm64r; // relative centroid / normal (fp64 mode)
+    // Galerkin form: each quadrature point's panel normal, in the quadrature
+    // points' order (records as nrm32 / nrm64r, and absolute f64 [nqp][3])
+    DArray<float4> nrmq32;
+    DArray<double4> nrmq64r;
+    DArray<double> nrmq64;
+    DArray<double> gq_tmp;             // [nqp] Galerkin scratch (direct sums at the quadrature points)
     DArray<uint64_t> cen_key;
     // sorted quadrature points (sources)
     DArray<int> qp_panel;        // sorted quad point -> sorted panel
@@ -269,6 +278,10 @@ void rebuild_charge_tree(Mesh &m, const double *d_charges);
 // panels: [np][3][3] f64 device array in the caller's order (read when
 // opt.near_table == BEM_NEAR_EXACT)
 void build_near_table(Mesh &m, const double *panels);
+// per panel, its quadrature points' positions in the sorted quadrature order
+void build_qp_of_panel(Mesh &m);
+// Galerkin form: per-quadrature-point normal records and the scratch it needs
+void build_galerkin_geometry(Mesh &m);
 void build_tables(Mesh &m);
 void build_translation_groups(Mesh &m, Tree &t);
 // tensor-core M2L (bem_tc.cu)

@@ -1,0 +1,80 @@
+"""The Galerkin form (galerkin = 1) on the GPU against the oracle's Galerkin
+rows, right-hand side and solve: every row of K' and of the right-hand side
+field averaged over its panel by the quadrature rule, near-singular inner
+integrals exact."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1007_4591_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_galerkin_product_matches_oracle(pkg, precision):
+    m = synth.small_molecule(4)
+    P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+    x = np.random.default_rng(31).standard_normal(m.n_p)
+    rows = np.random.default_rng(32).choice(m.n_p, 512, replace=False)
+    ref = x[rows] + P.ehat * P.kprime_rows_galerkin(x, rows)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=12, precision=precision, galerkin=1) as g:
+        y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y[rows], ref) < 1e-5, rel(y[rows], ref)
+    # a different operator from collocation
+    col = x[rows] + P.ehat * P.kprime_rows_near_exact(x, rows)
+    assert rel(col, ref) > 10 * rel(y[rows], ref)
+
+
+def test_galerkin_full_size_rows(pkg):
+    m = synth.globular(6)
+    P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+    x = np.random.default_rng(33).standard_normal(m.n_p)
+    rows = np.random.default_rng(34).choice(m.n_p, 48, replace=False)
+    ref = x[rows] + P.ehat * P.kprime_rows_galerkin(x, rows)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=10, leaf_size=64, galerkin=1) as g:
+        y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y[rows], ref) < 1e-5, rel(y[rows], ref)
+
+
+def test_galerkin_rhs_solve_and_energy(pkg):
+    m = synth.small_molecule(3)
+    P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=12, tol=1e-10, galerkin=1) as g:
+        b = g.rhs().cpu().numpy()
+        assert rel(b, -P.ehat * P.bq_galerkin()) < 1e-6
+        s, st = g.solve()
+        dg = g.energy(s)
+    s_ref, _ = P.solve_galerkin(tol=1e-11)
+    assert rel(s.cpu().numpy(), s_ref) < 1e-5
+    e_ref = P.energy(s_ref)[0]
+    assert abs(dg - e_ref) < 1e-5 * abs(e_ref), (dg, e_ref)
+
+
+def test_galerkin_born_ion(pkg):
+    import sphere_series as ss
+    m = synth.born(4)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=10, tol=1e-10, galerkin=1) as g:
+        s, _ = g.solve()
+        dg = g.energy(s)
+    born = ss.born_energy(1.0, 2.0, 1.0, 80.0)
+    assert abs(dg - born) < 0.004 * abs(born), (dg, born)     # collocation: 1.25 % at this mesh
+
+
+def test_galerkin_transpose_and_gradients_unsupported(pkg):
+    m = synth.small_molecule(2)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, galerkin=1) as g:
+        with pytest.raises(pkg.BemError) as ei:
+            g.matvec_t(torch.zeros(m.n_p, dtype=torch.float64, device="cuda"))
+        assert ei.value.code == pkg.BEM_EUNSUPPORTED
