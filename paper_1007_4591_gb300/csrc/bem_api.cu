@@ -132,7 +132,7 @@ size_t Mesh::bytes() const {
          ntT_val.bytes() + qp_of_panel.bytes();
     if (tab) b += tab->bytes();
     b += Mf.bytes() + Lf.bytes() + Md.bytes() + Ld.bytes();
-    b += Mtc.bytes() + str32.bytes() + str64.bytes() + dpart_f.bytes() + dpart_d.bytes();
+    b += Mtc.bytes() + m2lR.bytes() + str32.bytes() + str64.bytes() + dpart_f.bytes() + dpart_d.bytes();
     b += xs.bytes() + ys.bytes() + zs.bytes() + far_f.bytes() + near_f.bytes() + far_d.bytes() +
          near_d.bytes() + io_a.bytes() + io_b.bytes() + red.bytes();
     b += dev_err.bytes();
@@ -163,7 +163,10 @@ static void alloc_work(Mesh &m) {
         ensure(m.near_d, nt);
     }
     const size_t nsrc = (size_t)std::max<int64_t>(m.nqp, m.nc);
-    if (tc_m2l_available(m)) ensure(m.Mtc, tc_staging_floats(m));
+    if (tc_m2l_available(m)) {
+        ensure(m.Mtc, tc_staging_floats(m));
+        ensure(m.m2lR, m2l_store_floats(m));
+    }
     if (m.opt.precision == BEM_MIXED) ensure(m.str32, nsrc);
     else ensure(m.str64, nsrc);
     const size_t nv = (size_t)std::max<int64_t>(m.np, m.nc);

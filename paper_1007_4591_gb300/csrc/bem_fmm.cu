@@ -1414,6 +1414,21 @@ void build_translation_groups(Mesh &m, Tree &t) {
                 chunks.push_back(make_int4(o, (int)b, (int)std::min<int64_t>(TR_BN_M2L, start[o + 1] - b), 0));
         t.m2l_nchunk = (int)chunks.size();
         build_tc_super(t, chunks, s);
+        // pairs by target cell for the store-then-sum tensor-core M2L
+        t.m2l_store = use_tc_m2l(m) && m2l_store_fits(nm, m.opt.p);
+        if (t.m2l_store) {
+            const int ncl = last - first;
+            std::vector<int> toff(ncl + 1, 0), tp(nm);
+            for (int64_t e = 0; e < nm; ++e) toff[h_out[e] - first + 1]++;
+            for (int c = 0; c < ncl; ++c) toff[c + 1] += toff[c];
+            std::vector<int> fill2(toff.begin(), toff.end() - 1);
+            for (int64_t e = 0; e < nm; ++e) tp[fill2[h_out[e] - first]++] = (int)e;
+            t.m2l_toff.alloc(ncl + 1);
+            t.m2l_tpairs.alloc(nm);
+            BEM_CUDA(cudaMemcpyAsync(t.m2l_toff.p, toff.data(), (ncl + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+            BEM_CUDA(cudaMemcpyAsync(t.m2l_tpairs.p, tp.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
+            BEM_CUDA(cudaStreamSynchronize(s));
+        }
     }
     // M2M (out parent, in child) and L2L (out child, in parent) per child level
     for (int c = 3; c <= L; ++c) {
@@ -1619,8 +1634,6 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
         ev_rec(m, timed, 2);
         // M2L: every cell at levels 2..L
         if (dense) {
-            BEM_CUDA(cudaMemsetAsync(L + (size_t)t.lvl_off[2] * cs, 0,
-                                     (size_t)(t.ncell - t.lvl_off[2]) * cs * sizeof(T), s));
             m2l_dense<T>(m, t, B::Om2l(m), nc, cs, rblocks, trsm, M, L);
         } else {
             const size_t sm = ((size_t)(p + 1) * W + (size_t)(2 * p + 1) * W2) * sizeof(cpx<T>);
@@ -1905,13 +1918,16 @@ void build_near_table(Mesh &m, const double *panels) {
 template <class T>
 static void m2l_dense(Mesh &m, const Tree &t, const T *Oop, int nc, int cs, int rblocks, size_t trsm,
                       T *M, T *L) {
-    if (t.m2l_nchunk == 0) return;
+    // L at levels >= 2 = the M2L sums (cleared first unless written whole)
     if constexpr (std::is_same<T, float>::value) {
         if (use_tc_m2l(m)) {
             m2l_tc(m, t, M, L);
             return;
         }
     }
+    BEM_CUDA(cudaMemsetAsync(L + (size_t)t.lvl_off[2] * cs, 0, (size_t)(t.ncell - t.lvl_off[2]) * cs * sizeof(T),
+                             m.stream));
+    if (t.m2l_nchunk == 0) return;
     dim3 g(t.m2l_nchunk, rblocks);
     k_translate<T, TR_BN_M2L, TR_THREADS><<<g, TR_THREADS, trsm, m.stream>>>(Oop, nc, cs, t.g_chunk.p + t.m2l_chunk0,
                                                                   t.g_out.p, t.g_in.p, M, L);
@@ -1969,8 +1985,6 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
                                                                       t.g_out.p, t.g_in.p, M, M);
             BEM_CHECK_LAUNCH();
         }
-        BEM_CUDA(cudaMemsetAsync(L + (size_t)t.lvl_off[2] * cs, 0,
-                                 (size_t)(t.ncell - t.lvl_off[2]) * cs * sizeof(T), s));
         m2l_dense<T>(m, t, B::Om2l(m), nc, cs, rblocks, trsm, M, L);
         for (int c = 3; c <= t.L; ++c) {
             if (t.l2l_nchunk[c] == 0) continue;

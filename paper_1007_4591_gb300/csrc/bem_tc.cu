@@ -3,20 +3,24 @@
 // The M2L step of the downward sweep (Sec. 2.3) is, for every offset class
 // o of the interaction list, the dense product L_t += T_o M_s over all pairs
 // (t, s) with that offset: with the pairs of one class gathered as columns
-// this is a GEMM  D[128 x 64] = T_o[128 x 128] . B[128 x 64]  ((p+1)^2 = 121
-// coefficients padded to 128; p <= 10).  It runs as tcgen05.mma kind::tf32
-// with the 3xTF32 split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (tf32 keeps
-// 11 significant bits; the split recovers FP32-level products).  The
-// operator (A) and the accumulators live in tensor memory; the multipoles (B)
-// are staged in shared memory in the canonical K-major layout without
-// swizzle (8 x 16-byte core matrices, K-adjacent cores 128 B apart, 8-row
-// groups 4 KB apart).  A persistent, warp-specialised kernel runs
-// the pairs of one class as a stream of tiles (producers, one MMA thread,
-// epilogue; see k_m2l_tc) and adds each pair's local expansion into its
-// target with one bulk asynchronous reduction.  Every wait is bounded: the
-// pipeline waits by the mesh's wait budget (bem_set_wait_budget), after which
-// the kernel raises an error flag; the last wait for its own MMAs (always
-// about a second) comes before it frees its tensor memory and returns.
+// this is a GEMM  D[128 x 128] = T_o[128 x 128] . B[128 x 128 pairs]
+// ((p+1)^2 = 121 coefficients padded to 128; p <= 10).  It runs as
+// tcgen05.mma kind::tf32 with the 3xTF32 split a b ~ a_hi b_hi + a_hi b_lo +
+// a_lo b_hi (tf32 keeps 11 significant bits; the split recovers FP32-level
+// products).  The operator (A) and the accumulators live in tensor memory;
+// the multipoles (B) are staged in shared memory one K-block (32
+// coefficients, 128 bytes of a row) at a time in the K-major layout with the
+// 128-byte swizzle, so that a warp's copy instruction reads four whole
+// 128-byte rows from global memory.  A persistent, warp-specialised kernel
+// runs the pairs of one class as a stream of 128-pair tiles (producers, one
+// MMA thread, epilogue; see k_m2l_tc).  The epilogue either stores each
+// tile's 128 local-expansion rows with one bulk copy into a per-pair buffer
+// that k_m2l_sum then adds up per target cell in a fixed order (no atomics;
+// used while that buffer fits), or adds each row into its target with a
+// bulk asynchronous reduction.  Every wait is bounded: the pipeline waits by
+// the mesh's wait budget (bem_set_wait_budget), after which the kernel
+// raises an error flag; the last wait for its own MMAs (always about a
+// second) comes before it frees its tensor memory and returns.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -25,29 +29,34 @@
 
 namespace bem {
 
-constexpr int TC_BN = 64;            // pairs per MMA tile (N) = one 64-pair chunk
+constexpr int TC_BN = 128;           // pairs per MMA tile (N)
 constexpr int TC_K = 128;            // padded coefficients (K and M)
-constexpr int TC_TMEM_COLS = 512;    // A hi [0,128), A lo [128,256), 4 accumulators of 64
+constexpr int TC_KB = 32;            // K-block: one 128-byte swizzled row of TF32 values
+constexpr int TC_NKB = TC_K / TC_KB; // K-blocks per tile
+constexpr int TC_TMEM_COLS = 512;    // A hi [0,128), A lo [128,256), 2 accumulators of 128
 constexpr int TC_A_HI = 0, TC_A_LO = 128, TC_D0 = 256;
-constexpr int TC_CHUNKS_PER_ITEM = 16;
+constexpr int TC_CHUNKS_PER_ITEM = 16;  // 64-pair chunks per work item (8 tiles)
 constexpr long long TC_WAIT_CYCLES = 2000000000ll;  // about one second of SM clock
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Shared-memory matrix descriptor: start address, leading-dimension byte
-// offset (K-adjacent core matrices), stride byte offset (8-row groups),
-// descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor of a K-major operand with the 128-byte
+// swizzle: start address, 8-row groups 1024 B apart (stride byte offset),
+// descriptor version 1, swizzle mode 2 (128 B).  The leading byte offset is
+// not used: one MMA reads 8 TF32 values (32 B) of a row, inside one swizzle
+// row; the K-steps inside a K-block advance the start address by 32 B.
+__device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
-// Instruction descriptor: D f32, A and B tf32, both K-major, N = 64, M = 128.
+// Instruction descriptor: D f32, A and B tf32, both K-major, N = 128, M = 128.
 constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
                               ((uint32_t)(128 >> 4) << 24);
 
@@ -84,11 +93,6 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
 }
 
-// element (row, k) of a K-major 128-column tile in core-matrix order (floats)
-__host__ __device__ __forceinline__ int tc_off(int row, int k) {
-    return (row >> 3) * (TC_K / 4) * 32 + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
-}
-
 // D += A (tensor memory) . B (shared-memory descriptor)
 __device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t acc) {
     asm volatile(
@@ -98,45 +102,55 @@ __device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a, uint64_t b, ui
 }
 
 // Warp roles of the pipelined kernel.
-constexpr int TC_NS = 3;                       // shared B stages (64 KB each)
-constexpr int TC_ND = 4;                       // TMEM accumulators of TC_BN columns
+constexpr int TC_NS = 5;                       // B stages: one K-block of a tile, hi | lo (32 KB)
+constexpr int TC_STAGE_BYTES = 2 * TC_BN * TC_KB * 4;
+constexpr int TC_ND = 2;                       // TMEM accumulators of TC_BN columns
 constexpr int TC_RING = 16;                    // work items in flight between the roles
 constexpr int TC_WARP_MMA = 0;                 // lane 0 issues the MMAs
 constexpr int TC_WARP_EPI0 = 1;                // warps 1..4: epilogue (TMEM lane quadrant = warp % 4)
 constexpr int TC_WARP_PROD0 = 5;               // warps 5..8: copies of B, operator into TMEM
 constexpr int TC_NPROD = 4 * 32, TC_NEPI = 4 * 32;
 constexpr int TC_THREADS = 9 * 32;
+constexpr int TC_ROWS_PER_PROD = TC_BN * 8 / TC_NPROD;  // rows of a stage per producer thread (8 granules each)
 
 __device__ __forceinline__ void bulk_prefetch_l2(const void *g, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"(bytes) : "memory");
 }
 
 // The persistent kernel: one CTA per SM takes work items (offset class,
-// first pair, number of pairs: up to TC_CHUNKS_PER_ITEM tiles of 64 pairs)
-// from a global counter, largest first.  Tiles are numbered continuously across a CTA's items, so the
+// first pair, number of pairs: up to 8 tiles of 128 pairs) from a global
+// counter, largest first.  Tiles are numbered continuously across a CTA's
+// items and each tile passes through TC_NKB stages (one per K-block), so the
 // pipeline never drains between items:
 //  * producers (warps 5-8): the leader fetches the next item, publishes it
 //    in a shared ring (mbarrier itemFull) and prefetches its operator into
-//    L2; all 128 copy the tiles' split multipoles into B stage t % 3
-//    (cp.async, mbarrier fullB).  After the first tile of an item they wait
-//    for the last MMA of the previous item (its fullD commit) and write the
-//    item's operator (hi | lo TF32 parts) into tensor memory (aReady).
-//  * MMA (warp 0, lane 0): per item waits aReady; per tile waits fullB and a
-//    free accumulator (emptyD), issues 16 K-steps x 3 products with A from
-//    tensor memory and commits to emptyB and fullD.
+//    L2; all 128 copy the K-block of the tile's split multipoles into stage
+//    g % TC_NS (cp.async: a warp instruction moves four 128-byte rows,
+//    written in the 128-byte swizzle; mbarrier fullB).  After the first tile
+//    of an item they wait for the last MMA of the previous item (its fullD
+//    commit) and write the item's operator (hi | lo TF32 parts) into tensor
+//    memory (aReady).
+//  * MMA (warp 0, lane 0): per item waits aReady; per tile waits a free
+//    accumulator (emptyD), per K-block its stage (fullB), issues 4 K-steps x
+//    3 products with A from tensor memory and commits to emptyB; after the
+//    last K-block it commits to fullD.
 //  * epilogue (warps 1-4): reads its TMEM lane quadrant, frees the
 //    accumulator, transposes the tile into shared memory rows (one local
-//    expansion row of cs floats per pair) and adds each row into its target
-//    with one bulk asynchronous reduction (cp.reduce.async.bulk .add.f32).
+//    expansion row of cs floats per pair) and either stores the 128 rows
+//    with one bulk copy at the tile's first pair in `out` (STORE) or adds
+//    each row into its target cell of `out` with one bulk reduction.
+template <bool STORE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
          const int4 *__restrict__ items, int nitems, int *__restrict__ next_item,
          const int *__restrict__ p_out, const int *__restrict__ p_in, int cs,
-         const float *__restrict__ Mtc, float *__restrict__ Lout, int *__restrict__ err,
+         const float *__restrict__ Mtc, float *__restrict__ out, int *__restrict__ err,
          long long budget) {
     extern __shared__ __align__(1024) unsigned char smraw[];
-    float *Bbuf = reinterpret_cast<float *>(smraw);            // [TC_NS][hi, lo][TC_BN * TC_K]
-    float *Ct = Bbuf + (size_t)TC_NS * 2 * TC_BN * TC_K;       // [TC_BN][cs]
+    // 1024-byte aligned base (the 128-byte swizzle repeats every 1024 B)
+    unsigned char *sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
+    const uint32_t sbase = smem_u32(sm);
+    float *Ct = reinterpret_cast<float *>(sm + (size_t)TC_NS * TC_STAGE_BYTES);  // [TC_BN][cs]
     __shared__ __align__(8) uint64_t fullB[TC_NS], emptyB[TC_NS], fullD[TC_ND], emptyD[TC_ND];
     __shared__ __align__(8) uint64_t aReady, itemFull[TC_RING];
     __shared__ int4 s_item[TC_RING];
@@ -163,14 +177,15 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tm = s_tmem;
-    int ntile_done = 0;  // tiles whose MMAs were issued (MMA thread)
+    int ntile_done = 0;  // tiles whose MMAs were all issued (MMA thread)
+    int nstage_done = 0; // K-block stages whose MMAs were issued and committed (MMA thread)
 
     if (warp >= TC_WARP_PROD0) {
         // ---------------- producers
         const int ptid = tid - TC_WARP_PROD0 * 32;
+        const int pw = ptid >> 5;                            // producer warp 0..3
         const int quad = warp & 3, row = 32 * quad + lane;  // TMEM lane of this thread
-        constexpr int PER = TC_BN * (TC_K / 4) / TC_NPROD;  // 16-byte chunks per producer and half
-        constexpr int NR = PER / 2;                          // rows per producer thread (e >> 8 = u >> 1)
+        const int gq = lane & 7, r4 = lane >> 3;            // 16-byte granule, row within a group of 4
         // every wait is made warp-uniform (__all_sync) and every item starts with
         // a vote of all producers, so that on a timeout they leave together
         bool fail = false;
@@ -198,42 +213,44 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
             const int4 sc = s_item[slot];
             if (sc.x < 0) break;
             const int ntl = (sc.z + TC_BN - 1) / TC_BN;
-            // source cells of a tile's pairs (rows n = 8 v + (ptid & 7)); the
-            // next tile's are loaded while this one waits and copies
+            // source cells of the tile rows this thread copies: n = 32 pw + 4 v + r4
             auto load_srcs = [&](int c, int *dst) {
                 const int y = sc.y + TC_BN * c, z = min(TC_BN, sc.z - TC_BN * c);
 #pragma unroll
-                for (int v = 0; v < NR; ++v) {
-                    const int n = 8 * v + (ptid & 7);
+                for (int v = 0; v < TC_ROWS_PER_PROD; ++v) {
+                    const int n = 32 * pw + 4 * v + r4;
                     dst[v] = (n < z) ? p_in[y + n] : -1;
                 }
             };
-            int srcs[NR], nxt[NR];
+            int srcs[TC_ROWS_PER_PROD], nxt[TC_ROWS_PER_PROD];
             load_srcs(0, srcs);
             for (int c = 0; c < ntl; ++c, ++t) {
                 if (c + 1 < ntl) load_srcs(c + 1, nxt);
-                const int st = t % TC_NS, k = t / TC_NS;
-                const bool okB = __all_sync(0xffffffffu, k < 1 || mbar_wait_bounded(smem_u32(&emptyB[st]),
-                                                                                   (uint32_t)((k - 1) & 1), budget));
-                if (!okB) {
-                    atomicExch(err, 1);
-                    fail = true;
-                    break;
-                }
-                const uint32_t bh = smem_u32(Bbuf + (size_t)st * 2 * TC_BN * TC_K);
-                const uint32_t bl = bh + TC_BN * TC_K * 4;
+                for (int kb = 0; kb < TC_NKB && !fail; ++kb) {
+                    const int g = TC_NKB * t + kb;
+                    const int st = g % TC_NS, k = g / TC_NS;
+                    const bool okB = __all_sync(0xffffffffu, k < 1 || mbar_wait_bounded(smem_u32(&emptyB[st]),
+                                                                                       (uint32_t)((k - 1) & 1), budget));
+                    if (!okB) {
+                        atomicExch(err, 1);
+                        fail = true;
+                        break;
+                    }
+                    const uint32_t bh = sbase + (uint32_t)(st * TC_STAGE_BYTES);
+                    const uint32_t bl = bh + TC_BN * TC_KB * 4;
 #pragma unroll
-                for (int u = 0; u < PER; ++u) {
-                    const int e = ptid + TC_NPROD * u;           // (n, k4): n = 8 (e >> 8) + (e & 7)
-                    const int n = ((e >> 8) << 3) | (e & 7), k4 = (e >> 3) & 31;
-                    const int src = srcs[u >> 1];  // = e >> 8, as ptid < 128
-                    const float *g = Mtc + (size_t)(src >= 0 ? src : 0) * 2 * TC_K + 4 * k4;
-                    const uint32_t nb = src >= 0 ? 16u : 0u;  // 0: zero-fill (padding rows)
-                    const uint32_t off = 4u * (uint32_t)tc_off(n, 4 * k4);
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bh + off), "l"(g), "r"(nb));
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bl + off), "l"(g + TC_K), "r"(nb));
+                    for (int v = 0; v < TC_ROWS_PER_PROD; ++v) {
+                        const int n = 32 * pw + 4 * v + r4;
+                        const int src = srcs[v];
+                        const float *gsrc = Mtc + (size_t)(src >= 0 ? src : 0) * 2 * TC_K + TC_KB * kb + 4 * gq;
+                        const uint32_t nb = src >= 0 ? 16u : 0u;  // 0: zero-fill (padding rows)
+                        const uint32_t off = (uint32_t)(n * 128 + ((gq ^ (n & 7)) << 4));
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bh + off), "l"(gsrc), "r"(nb));
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bl + off), "l"(gsrc + TC_K), "r"(nb));
+                    }
+                    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&fullB[st])) : "memory");
                 }
-                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&fullB[st])) : "memory");
+                if (fail) break;
                 if (c == 0) {
                     // the item's operator into tensor memory, once the previous
                     // item's MMAs (which read the old one) have completed
@@ -250,12 +267,12 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                     const float *gl = Alo_all + ((size_t)sc.x * TC_K + row) * TC_K;
 #pragma unroll 1
                     for (int part = 0; part < 4; ++part) {
-                        const float *g = (part < 2 ? gh : gl) + (part & 1) * 64;
+                        const float *gp = (part < 2 ? gh : gl) + (part & 1) * 64;
                         const uint32_t col = (part < 2 ? TC_A_HI : TC_A_LO) + (part & 1) * 64;
                         uint32_t v[64];
 #pragma unroll
                         for (int q = 0; q < 64; q += 4) {
-                            const float4 f = __ldg(reinterpret_cast<const float4 *>(g + q));
+                            const float4 f = __ldg(reinterpret_cast<const float4 *>(gp + q));
                             v[q] = __float_as_uint(f.x);
                             v[q + 1] = __float_as_uint(f.y);
                             v[q + 2] = __float_as_uint(f.z);
@@ -281,14 +298,13 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                     mbar_arrive(smem_u32(&aReady));
                 }
 #pragma unroll
-                for (int v = 0; v < NR; ++v) srcs[v] = nxt[v];
+                for (int v = 0; v < TC_ROWS_PER_PROD; ++v) srcs[v] = nxt[v];
             }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == TC_WARP_MMA) {
         // ---------------- MMA issue (one thread)
         if (lane == 0) {
-            const uint32_t SBO = (TC_K / 4) * 128, LBO = 128;
             bool fail = false;
             int t = 0;
             for (int i = 0; !fail; ++i) {
@@ -305,35 +321,42 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const int ntl = (sc.z + TC_BN - 1) / TC_BN;
-                for (int c = 0; c < ntl; ++c, ++t) {
-                    const int st = t % TC_NS, k = t / TC_NS;
+                for (int c = 0; c < ntl && !fail; ++c, ++t) {
                     const int d = t % TC_ND, jd = t / TC_ND;
-                    bool ok = mbar_wait_bounded(smem_u32(&fullB[st]), (uint32_t)(k & 1), budget);
-                    if (ok && jd >= 1) ok = mbar_wait_bounded(smem_u32(&emptyD[d]), (uint32_t)((jd - 1) & 1), budget);
-                    if (!ok) {
+                    if (jd >= 1 && !mbar_wait_bounded(smem_u32(&emptyD[d]), (uint32_t)((jd - 1) & 1), budget)) {
                         atomicExch(err, 1);
                         fail = true;
                         break;
                     }
-                    // the stage was written by cp.async (generic proxy): order it before
-                    // the tensor core's (async proxy) reads
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t bh = smem_u32(Bbuf + (size_t)st * 2 * TC_BN * TC_K);
-                    const uint32_t bl = bh + TC_BN * TC_K * 4;
                     const uint32_t dt = tm + (uint32_t)(TC_D0 + d * TC_BN);
-#pragma unroll 4
-                    for (int ks = 0; ks < TC_K / 8; ++ks) {
-                        const uint32_t ko = (uint32_t)ks * 2 * LBO;
-                        const uint64_t dbh = tc_desc(bh + ko, LBO, SBO), dbl = tc_desc(bl + ko, LBO, SBO);
-                        const uint32_t ah = tm + TC_A_HI + 8u * ks, al = tm + TC_A_LO + 8u * ks;
-                        tc_mma_ts(dt, ah, dbh, ks > 0 ? 1u : 0u);
-                        tc_mma_ts(dt, ah, dbl, 1u);
-                        tc_mma_ts(dt, al, dbh, 1u);
+                    for (int kb = 0; kb < TC_NKB; ++kb) {
+                        const int g = TC_NKB * t + kb;
+                        const int st = g % TC_NS, k = g / TC_NS;
+                        if (!mbar_wait_bounded(smem_u32(&fullB[st]), (uint32_t)(k & 1), budget)) {
+                            atomicExch(err, 1);
+                            fail = true;
+                            break;
+                        }
+                        // the stage was written by cp.async (generic proxy): order it before
+                        // the tensor core's (async proxy) reads
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint32_t bh = sbase + (uint32_t)(st * TC_STAGE_BYTES);
+                        const uint32_t bl = bh + TC_BN * TC_KB * 4;
+#pragma unroll
+                        for (int ks = 0; ks < TC_KB / 8; ++ks) {
+                            const uint64_t dbh = tc_desc_sw128(bh + 32u * ks), dbl = tc_desc_sw128(bl + 32u * ks);
+                            const uint32_t kc = (uint32_t)(TC_KB * kb + 8 * ks);
+                            tc_mma_ts(dt, tm + TC_A_HI + kc, dbh, (kb | ks) ? 1u : 0u);
+                            tc_mma_ts(dt, tm + TC_A_HI + kc, dbl, 1u);
+                            tc_mma_ts(dt, tm + TC_A_LO + kc, dbh, 1u);
+                        }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                         smem_u32(&emptyB[st]))
+                                     : "memory");
+                        nstage_done = g + 1;
                     }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     smem_u32(&emptyB[st]))
-                                 : "memory");
+                    if (fail) break;
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                      smem_u32(&fullD[d]))
                                  : "memory");
@@ -342,10 +365,10 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
             ntile_done = t;
         }
     } else {
-        // ---------------- epilogue: TMEM lane quadrant (warp % 4), 64 pairs per tile
+        // ---------------- epilogue: TMEM lane quadrant (warp % 4), 128 pairs per tile
         const int quad = warp & 3;
         const int row = 32 * quad + lane;
-        const bool issuer = warp == TC_WARP_EPI0;  // its lanes issue the bulk reductions
+        const bool issuer = warp == TC_WARP_EPI0;  // its lanes issue the bulk copies
         bool fail = false;
         int t = 0;
         for (int i = 0; !fail; ++i) {
@@ -378,39 +401,48 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                     fail = true;
                     break;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                uint32_t r[TC_BN];
-#pragma unroll
-                for (int cg = 0; cg < TC_BN; cg += 16) {
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                        : "=r"(r[cg + 0]), "=r"(r[cg + 1]), "=r"(r[cg + 2]), "=r"(r[cg + 3]), "=r"(r[cg + 4]),
-                          "=r"(r[cg + 5]), "=r"(r[cg + 6]), "=r"(r[cg + 7]), "=r"(r[cg + 8]), "=r"(r[cg + 9]),
-                          "=r"(r[cg + 10]), "=r"(r[cg + 11]), "=r"(r[cg + 12]), "=r"(r[cg + 13]),
-                          "=r"(r[cg + 14]), "=r"(r[cg + 15])
-                        : "r"(tm + ((uint32_t)(32 * quad) << 16) + (uint32_t)(TC_D0 + d * TC_BN + cg)));
-                }
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                mbar_arrive(smem_u32(&emptyD[d]));
-                // the previous tile's bulk reductions have finished reading Ct
+                // the previous tile's bulk copies have finished reading Ct
                 if (issuer) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
                 asm volatile("bar.sync 1, %0;" ::"n"(TC_NEPI) : "memory");
-                if (row < cs) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll 1
+                for (int cg = 0; cg < TC_BN; cg += 32) {
+                    uint32_t r[32];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                        : "r"(tm + ((uint32_t)(32 * quad) << 16) + (uint32_t)(TC_D0 + d * TC_BN + cg)));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (row < cs) {
 #pragma unroll
-                    for (int j = 0; j < TC_BN; ++j) Ct[j * cs + row] = __uint_as_float(r[j]);
+                        for (int j = 0; j < 32; ++j) Ct[(cg + j) * cs + row] = __uint_as_float(r[j]);
+                    }
                 }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                mbar_arrive(smem_u32(&emptyD[d]));
                 // generic-proxy writes of Ct before the bulk copies (async proxy) read it
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("bar.sync 1, %0;" ::"n"(TC_NEPI) : "memory");
                 if (issuer) {
                     const int y = sc.y + TC_BN * c, z = min(TC_BN, sc.z - TC_BN * c);
-                    for (int j = lane; j < z; j += 32) {
-                        float *dst = Lout + (size_t)p_out[y + j] * cs;
-                        asm volatile(
-                            "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
-                            "r"(smem_u32(Ct + j * cs)), "r"((uint32_t)cs * 4u)
-                            : "memory");
+                    if (STORE) {
+                        if (lane == 0)
+                            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
+                                             out + (size_t)y * cs),
+                                         "r"(smem_u32(Ct)), "r"((uint32_t)(z * cs * 4))
+                                         : "memory");
+                    } else {
+                        for (int j = lane; j < z; j += 32)
+                            asm volatile(
+                                "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
+                                    out + (size_t)p_out[y + j] * cs),
+                                "r"(smem_u32(Ct + j * cs)), "r"((uint32_t)cs * 4u)
+                                : "memory");
                     }
                     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                 }
@@ -420,21 +452,52 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
     }
     // before the CTA's shared memory and tensor memory go away, every commit
     // arrival must have landed: the MMA thread waits (bounded) for the last
-    // completion of each B stage and of the last accumulator
-    if (warp == TC_WARP_MMA && lane == 0 && ntile_done > 0) {
-        const int nt = ntile_done;
-        for (int st = 0; st < TC_NS && st < nt; ++st) {
-            const int t = st + ((nt - 1 - st) / TC_NS) * TC_NS;  // last tile on stage st
-            mbar_wait_bounded(smem_u32(&emptyB[st]), (uint32_t)((t / TC_NS) & 1));
+    // completion of each B stage (which follows all MMAs issued before it,
+    // also those of a tile left unfinished by a failed wait) and of the last
+    // accumulator
+    if (warp == TC_WARP_MMA && lane == 0 && nstage_done > 0) {
+        const int ng = nstage_done;
+        for (int st = 0; st < TC_NS && st < ng; ++st) {
+            const int g = st + ((ng - 1 - st) / TC_NS) * TC_NS;  // last stage use on st
+            mbar_wait_bounded(smem_u32(&emptyB[st]), (uint32_t)((g / TC_NS) & 1));
         }
-        const int t = nt - 1;
-        mbar_wait_bounded(smem_u32(&fullD[t % TC_ND]), (uint32_t)((t / TC_ND) & 1));
+        if (ntile_done > 0) {
+            const int t = ntile_done - 1;
+            mbar_wait_bounded(smem_u32(&fullD[t % TC_ND]), (uint32_t)((t / TC_ND) & 1));
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(TC_TMEM_COLS));
+}
+
+// L_c = sum of the rows R_j of the M2L pairs j whose target is cell c, in
+// increasing j (one warp per cell, float4 lanes); cells without pairs get 0.
+__global__ void k_m2l_sum(const float4 *__restrict__ R, const int *__restrict__ toff,
+                          const int *__restrict__ tpairs, int first, int ncell, int cs4,
+                          float4 *__restrict__ L) {
+    const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (first + w >= ncell) return;
+    const int b = toff[w], e = toff[w + 1];
+    for (int j = lane; j < cs4; j += 32) {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        int q = b;
+        for (; q + 4 <= e; q += 4) {
+            const float4 u0 = R[(size_t)tpairs[q] * cs4 + j], u1 = R[(size_t)tpairs[q + 1] * cs4 + j];
+            const float4 u2 = R[(size_t)tpairs[q + 2] * cs4 + j], u3 = R[(size_t)tpairs[q + 3] * cs4 + j];
+            a.x += u0.x; a.y += u0.y; a.z += u0.z; a.w += u0.w;
+            a.x += u1.x; a.y += u1.y; a.z += u1.z; a.w += u1.w;
+            a.x += u2.x; a.y += u2.y; a.z += u2.z; a.w += u2.w;
+            a.x += u3.x; a.y += u3.y; a.z += u3.z; a.w += u3.w;
+        }
+        for (; q < e; ++q) {
+            const float4 u = R[(size_t)tpairs[q] * cs4 + j];
+            a.x += u.x; a.y += u.y; a.z += u.z; a.w += u.w;
+        }
+        L[(size_t)(first + w) * cs4 + j] = a;
+    }
 }
 
 // ---------------------------------------------------------------- host side
@@ -474,11 +537,12 @@ bool tc_m2l_available(const Mesh &m) {
     return m.opt.precision == BEM_MIXED && (m.opt.p + 1) * (m.opt.p + 1) <= TC_K;
 }
 
-size_t tc_smem_bytes() { return (size_t)(2 * TC_NS * TC_BN * TC_K + TC_BN * TC_K) * sizeof(float); }
+// dynamic shared memory: alignment slack, the B stages, the transposed tile
+size_t tc_smem_bytes() { return 1024 + (size_t)TC_NS * TC_STAGE_BYTES + (size_t)TC_BN * TC_K * sizeof(float); }
 
 // Work items of the persistent kernel: (offset class, first pair, number of
-// pairs), up to TC_CHUNKS_PER_ITEM consecutive 64-pair chunks of one class,
-// largest first.
+// pairs), up to TC_CHUNKS_PER_ITEM consecutive 64-pair chunks of one class
+// (tiles of 128 pairs), largest first.
 void build_tc_super(Tree &t, const std::vector<int4> &chunks_m2l, cudaStream_t s) {
     std::vector<int4> sup;
     int i = 0;
@@ -510,29 +574,62 @@ __global__ void k_split_m(const float *M, int first, int ncell, int nc, int cs, 
     }
 }
 
+bool m2l_store_fits(int64_t npairs, int p) {
+    return npairs > 0 && (double)npairs * cell_stride(p) * sizeof(float) <= (double)TC_STORE_MAX_BYTES;
+}
+
+// L (levels >= 2) = sum over the M2L pairs of T_o M_s.  STORE: per-pair rows
+// into the mesh's buffer, then a fixed-order sum per target (deterministic);
+// otherwise L is cleared and the rows are added by bulk reductions.
 void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L) {
-    if (t.tc_nsuper == 0) return;
     const int nc = (m.opt.p + 1) * (m.opt.p + 1);
     const int cs = cell_stride(m.opt.p);
-    if (m.Mtc.n < (size_t)t.ncell * 2 * TC_K) throw Error(BEM_ECUDA, "tensor-core staging buffer too small");
     const int first = t.lvl_off[2];
+    const bool store = t.m2l_store && m.m2lR.n >= (size_t)t.nm2l * cs;
+    if (!store)
+        BEM_CUDA(cudaMemsetAsync(L + (size_t)first * cs, 0, (size_t)(t.ncell - first) * cs * sizeof(float), m.stream));
+    if (t.tc_nsuper == 0) {
+        if (store) BEM_CUDA(cudaMemsetAsync(L + (size_t)first * cs, 0, (size_t)(t.ncell - first) * cs * sizeof(float), m.stream));
+        return;
+    }
+    if (m.Mtc.n < (size_t)t.ncell * 2 * TC_K) throw Error(BEM_ECUDA, "tensor-core staging buffer too small");
     k_split_m<<<t.ncell - first, 128, 0, m.stream>>>(M, first, t.ncell, nc, cs, m.Mtc.p);
     BEM_CHECK_LAUNCH();
     const size_t sm = tc_smem_bytes();
-    ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc), sm);
     int dev = 0, nsm = 0;
     BEM_CUDA(cudaGetDevice(&dev));
     BEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int grid = std::max(1, std::min(t.tc_nsuper, nsm));
     BEM_CUDA(cudaMemsetAsync(m.dev_err.p + 1, 0, sizeof(int), m.stream));  // work-item counter
-    k_m2l_tc<<<grid, TC_THREADS, sm, m.stream>>>(m.tab->Tc_hi.p, m.tab->Tc_lo.p, t.tc_super.p, t.tc_nsuper,
-                                                 m.dev_err.p + 1, t.g_out.p, t.g_in.p, cs, m.Mtc.p, L,
-                                                 m.dev_err.p, m.wait_budget);
-    BEM_CHECK_LAUNCH();
+    if (store) {
+        ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc<true>), sm);
+        k_m2l_tc<true><<<grid, TC_THREADS, sm, m.stream>>>(m.tab->Tc_hi.p, m.tab->Tc_lo.p, t.tc_super.p, t.tc_nsuper,
+                                                           m.dev_err.p + 1, t.g_out.p, t.g_in.p, cs, m.Mtc.p,
+                                                           m.m2lR.p, m.dev_err.p, m.wait_budget);
+        BEM_CHECK_LAUNCH();
+        const int ncl = t.ncell - first;
+        k_m2l_sum<<<cdiv((int64_t)ncl * 32, 256), 256, 0, m.stream>>>(
+            reinterpret_cast<const float4 *>(m.m2lR.p), t.m2l_toff.p, t.m2l_tpairs.p, first, t.ncell, cs / 4,
+            reinterpret_cast<float4 *>(L));
+        BEM_CHECK_LAUNCH();
+    } else {
+        ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc<false>), sm);
+        k_m2l_tc<false><<<grid, TC_THREADS, sm, m.stream>>>(m.tab->Tc_hi.p, m.tab->Tc_lo.p, t.tc_super.p, t.tc_nsuper,
+                                                            m.dev_err.p + 1, t.g_out.p, t.g_in.p, cs, m.Mtc.p, L,
+                                                            m.dev_err.p, m.wait_budget);
+        BEM_CHECK_LAUNCH();
+    }
 }
 
 size_t tc_staging_floats(const Mesh &m) {
     return (size_t)std::max(m.tp.ncell, m.tc.ncell) * 2 * TC_K;
+}
+
+size_t m2l_store_floats(const Mesh &m) {
+    size_t n = 0;
+    for (const Tree *t : {&m.tp, &m.tc})
+        if (t->m2l_store) n = std::max(n, (size_t)t->nm2l * cell_stride(m.opt.p));
+    return n;
 }
 
 }  // namespace bem
