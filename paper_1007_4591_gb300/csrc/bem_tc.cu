@@ -263,16 +263,18 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const float *gh = Ahi_all + ((size_t)sc.x * TC_K + row) * TC_K;
-                    const float *gl = Alo_all + ((size_t)sc.x * TC_K + row) * TC_K;
+                    // operator layout [k / 4][row][k % 4]: the warp's rows read 512
+                    // contiguous bytes per load
+                    const float4 *gh = reinterpret_cast<const float4 *>(Ahi_all + (size_t)sc.x * TC_K * TC_K) + row;
+                    const float4 *gl = reinterpret_cast<const float4 *>(Alo_all + (size_t)sc.x * TC_K * TC_K) + row;
 #pragma unroll 1
                     for (int part = 0; part < 4; ++part) {
-                        const float *gp = (part < 2 ? gh : gl) + (part & 1) * 64;
+                        const float4 *gp = (part < 2 ? gh : gl) + (part & 1) * 16 * TC_K;
                         const uint32_t col = (part < 2 ? TC_A_HI : TC_A_LO) + (part & 1) * 64;
                         uint32_t v[64];
 #pragma unroll
                         for (int q = 0; q < 64; q += 4) {
-                            const float4 f = __ldg(reinterpret_cast<const float4 *>(gp + q));
+                            const float4 f = __ldg(gp + (q >> 2) * TC_K);
                             v[q] = __float_as_uint(f.x);
                             v[q + 1] = __float_as_uint(f.y);
                             v[q + 2] = __float_as_uint(f.z);
@@ -512,9 +514,10 @@ static inline float host_tf32(float x) {
     return r;
 }
 
-// hi/lo TF32 parts of the M2L operators, row-major [offset][row = output
-// coefficient][k = input coefficient], zero-padded to 128 x 128 (the kernel
-// writes them into tensor memory lane by lane)
+// hi/lo TF32 parts of the M2L operators, [offset][k / 4][row = output
+// coefficient][k % 4] (k = input coefficient), zero-padded to 128 x 128: the
+// kernel writes row r into tensor-memory lane r, and the 32 rows of a warp
+// read 4 consecutive coefficients each from 512 contiguous bytes
 void build_tc_tables(int p, const std::vector<double> &om2l, int nops, std::vector<float> &hi,
                      std::vector<float> &lo) {
     const int nc = (p + 1) * (p + 1);
@@ -527,8 +530,9 @@ void build_tc_tables(int p, const std::vector<double> &om2l, int nops, std::vect
             for (int k = 0; k < nc; ++k) {
                 const float x = (float)T[(size_t)k * nc + row];
                 const float h = host_tf32(x);
-                H[(size_t)row * TC_K + k] = h;
-                L[(size_t)row * TC_K + k] = host_tf32(x - h);
+                const size_t at = ((size_t)(k >> 2) * TC_K + row) * 4 + (k & 3);
+                H[at] = h;
+                L[at] = host_tf32(x - h);
             }
     }
 }
