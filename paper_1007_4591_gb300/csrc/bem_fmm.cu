@@ -1176,9 +1176,9 @@ void build_tables(Mesh &m) {
 // shared memory, 8 x 4 outputs per thread, then scattered with coalesced
 // atomic adds (a warp adds 32 consecutive coefficients of one cell).
 constexpr int TR_BM = 128, TR_THREADS = 256;
-constexpr int TR_THREADS_TREE = 128;  // k_translate for M2M / L2L chunks of 16 pairs
+constexpr int TR_THREADS_TREE = 256;  // M2M / L2L kernels (chunks of TR_BN_TREE pairs)
 constexpr int TR_BN_M2L = 64;  // pairs per chunk for M2L (many pairs per offset class)
-constexpr int TR_BN_TREE = 16; // pairs per chunk for M2M / L2L (8 operators per level)
+constexpr int TR_BN_TREE = 32; // pairs per chunk for M2M / L2L (8 operators per level)
 template <class T> struct TrBK;
 template <> struct TrBK<float> { static constexpr int v = 32; };
 template <> struct TrBK<double> { static constexpr int v = 16; };
@@ -1311,6 +1311,107 @@ k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ 
         for (int r = lane; r < rows; r += 32) atomicAdd(o + r, cj[r]);
     }
 }
+
+// M2M / L2L: out[p_out[j]] += Op[octant] . in[p_in[j]] for a chunk of up to
+// BN pairs of one operator.  The level's few thousand translations are
+// latency-bound, so the CTA copies the whole operator block (nc x TR_BM) and
+// the chunk's BN input rows to shared memory in one round of 16-byte
+// cp.async, then each thread forms 8 rows x (BN / 16) pair columns (columns
+// strided by 16; input rows padded to 4 mod 32 words: at most 2-way bank
+// conflicts) and the results leave as coalesced atomic adds.
+template <class T, int BN, int NTH>
+__global__ void __launch_bounds__(NTH)
+k_tree_translate(const T *__restrict__ ops, int nc, int cs, int ldb, const int4 *__restrict__ chunks,
+                 const int *__restrict__ p_out, const int *__restrict__ p_in, const T *__restrict__ in,
+                 T *__restrict__ out) {
+    constexpr int NTY = TR_BM / 8;  // row groups of 8
+    constexpr int NTX = NTH / NTY;  // column groups
+    constexpr int CPT = BN / NTX;   // columns per thread
+    static_assert(NTH % NTY == 0 && BN % NTX == 0, "tree translate tiling");
+    constexpr int VEC = 16 / (int)sizeof(T);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *As = reinterpret_cast<T *>(smraw);  // [nc][TR_BM]
+    T *Bs = As + (size_t)nc * TR_BM;       // [BN][ldb]
+    T *Cs = As;                            // [BN][TR_BM + 1] (epilogue)
+    __shared__ int s_in[BN], s_out[BN];
+    const int4 ch = chunks[blockIdx.x];
+    const T *Tt = ops + (size_t)ch.x * nc * cs;
+    const int rb = blockIdx.y * TR_BM;
+    const int tid = threadIdx.x, ty = tid / NTX, tx = tid - ty * NTX;
+    if (tid < BN) {
+        s_in[tid] = tid < ch.z ? p_in[ch.y + tid] : -1;
+        s_out[tid] = tid < ch.z ? p_out[ch.y + tid] : -1;
+    }
+    __syncthreads();
+    for (int e = tid; e < nc * (TR_BM / VEC); e += NTH) {
+        const int k = e / (TR_BM / VEC), r = (e - k * (TR_BM / VEC)) * VEC;
+        const bool ok = rb + r < cs;  // cs % VEC == 0: a copy never crosses a row
+        cp_async_16(As + (size_t)k * TR_BM + r, ok ? Tt + (size_t)k * cs + rb + r : Tt, ok);
+    }
+    const int cv = cs / VEC;
+    for (int e = tid; e < BN * cv; e += NTH) {
+        const int j = e / cv, q = (e - j * cv) * VEC;
+        const int src = s_in[j];
+        cp_async_16(Bs + (size_t)j * ldb + q, src >= 0 ? in + (size_t)src * cs + q : in, src >= 0);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    T acc[8][CPT];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) acc[r][c] = 0;
+#pragma unroll 4
+    for (int k = 0; k < nc; ++k) {
+        T a[8], b[CPT];
+#pragma unroll
+        for (int q = 0; q < 8; q += VEC) {
+            if constexpr (sizeof(T) == 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(As + (size_t)k * TR_BM + ty * 8 + q);
+                a[q] = v.x;
+                a[q + 1] = v.y;
+                a[q + 2] = v.z;
+                a[q + 3] = v.w;
+            } else {
+                const double2 v = *reinterpret_cast<const double2 *>(As + (size_t)k * TR_BM + ty * 8 + q);
+                a[q] = v.x;
+                a[q + 1] = v.y;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) b[c] = Bs[(size_t)(tx + NTX * c) * ldb + k];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) Cs[(tx + NTX * c) * (TR_BM + 1) + ty * 8 + r] = acc[r][c];
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    const int rows = min(TR_BM, nc - rb);
+    for (int j = warp; j < ch.z; j += NTH / 32) {
+        T *o = out + (size_t)s_out[j] * cs + rb;
+        const T *cj = Cs + j * (TR_BM + 1);
+        for (int r = lane; r < rows; r += 32) atomicAdd(o + r, cj[r]);
+    }
+}
+
+// input-row pitch of k_tree_translate (4 mod 32 words) and its shared memory
+template <class T>
+static int tree_ldb(int cs) {
+    return (int)(((cs * sizeof(T) + 127) / 128 * 128 + 16) / sizeof(T));
+}
+template <class T>
+static size_t tree_translate_smem(int nc, int cs) {
+    const size_t ab = ((size_t)nc * TR_BM + (size_t)TR_BN_TREE * tree_ldb<T>(cs)) * sizeof(T);
+    return std::max(ab, (size_t)TR_BN_TREE * (TR_BM + 1) * sizeof(T));
+}
+constexpr size_t TREE_SMEM_MAX = 200 * 1024;  // above: the pipelined k_translate
 
 template <class T, int BN>
 static size_t translate_smem() {
@@ -1525,6 +1626,27 @@ static void ev_rec(Mesh &m, bool timed, int k) {
     if (timed && m.tm.on) BEM_CUDA(cudaEventRecord(m.tm.ev[k], m.stream));
 }
 
+// one level of M2M or L2L: the chunks [chunk0, chunk0 + nchunk) of the
+// grouped tree translations
+template <class T>
+static void tree_translate(const T *ops, int nc, int cs, int rblocks, const Tree &t, int chunk0, int nchunk,
+                           const T *in, T *out, cudaStream_t s) {
+    if (nchunk == 0) return;
+    dim3 g(nchunk, rblocks);
+    const size_t sm = tree_translate_smem<T>(nc, cs);
+    if (sm <= TREE_SMEM_MAX) {
+        set_smem<T>(k_tree_translate<T, TR_BN_TREE, TR_THREADS_TREE>, sm);
+        k_tree_translate<T, TR_BN_TREE, TR_THREADS_TREE><<<g, TR_THREADS_TREE, sm, s>>>(
+            ops, nc, cs, tree_ldb<T>(cs), t.g_chunk.p + chunk0, t.g_out.p, t.g_in.p, in, out);
+    } else {
+        const size_t trsm_t = translate_smem<T, TR_BN_TREE>();
+        set_smem<T>(k_translate<T, TR_BN_TREE, TR_THREADS_TREE>, trsm_t);
+        k_translate<T, TR_BN_TREE, TR_THREADS_TREE><<<g, TR_THREADS_TREE, trsm_t, s>>>(
+            ops, nc, cs, t.g_chunk.p + chunk0, t.g_out.p, t.g_in.p, in, out);
+    }
+    BEM_CHECK_LAUNCH();
+}
+
 bool use_tc_m2l(const Mesh &m) {
     if (!tc_m2l_available(m)) return false;
     return m.opt.m2l_mode == BEM_M2L_TC || m.opt.m2l_mode == BEM_M2L_AUTO;
@@ -1602,11 +1724,7 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
         const bool dense = m.opt.m2l_mode != BEM_M2L_DIRECT;
         const int rblocks = cdiv(nc, TR_BM);
         const size_t trsm = translate_smem<T, TR_BN_M2L>();
-        const size_t trsm_t = translate_smem<T, TR_BN_TREE>();
-        if (dense) {
-            set_smem<T>(k_translate<T, TR_BN_M2L, TR_THREADS>, trsm);
-            set_smem<T>(k_translate<T, TR_BN_TREE, TR_THREADS_TREE>, trsm_t);
-        }
+        if (dense) set_smem<T>(k_translate<T, TR_BN_M2L, TR_THREADS>, trsm);
         // P2M
         p2m_leaves<T>(tv, t.nleaf, sk, strec, p, cs, inv_h, M, s);
         ev_rec(m, timed, 1);
@@ -1615,13 +1733,8 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             if (t.L >= 3)
                 BEM_CUDA(cudaMemsetAsync(M + (size_t)t.lvl_off[2] * cs, 0,
                                          (size_t)(t.lvl_off[t.L] - t.lvl_off[2]) * cs * sizeof(T), s));
-            for (int c = t.L; c >= 3; --c) {
-                if (t.m2m_nchunk[c] == 0) continue;
-                dim3 g(t.m2m_nchunk[c], rblocks);
-                k_translate<T, TR_BN_TREE, TR_THREADS_TREE><<<g, TR_THREADS_TREE, trsm_t, s>>>(B::Om2m(m), nc, cs, t.g_chunk.p + t.m2m_chunk0[c],
-                                                            t.g_out.p, t.g_in.p, M, M);
-                BEM_CHECK_LAUNCH();
-            }
+            for (int c = t.L; c >= 3; --c)
+                tree_translate<T>(B::Om2m(m), nc, cs, rblocks, t, t.m2m_chunk0[c], t.m2m_nchunk[c], M, M, s);
         } else {
             const size_t sm = 2 * (size_t)(p + 1) * W * sizeof(cpx<T>);
             set_smem<T>(k_m2m<T>, sm);
@@ -1646,13 +1759,8 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
         ev_rec(m, timed, 3);
         // L2L: children at levels 3..L
         if (dense) {
-            for (int c = 3; c <= t.L; ++c) {
-                if (t.l2l_nchunk[c] == 0) continue;
-                dim3 g(t.l2l_nchunk[c], rblocks);
-                k_translate<T, TR_BN_TREE, TR_THREADS_TREE><<<g, TR_THREADS_TREE, trsm_t, s>>>(B::Ol2l(m), nc, cs, t.g_chunk.p + t.l2l_chunk0[c],
-                                                            t.g_out.p, t.g_in.p, L, L);
-                BEM_CHECK_LAUNCH();
-            }
+            for (int c = 3; c <= t.L; ++c)
+                tree_translate<T>(B::Ol2l(m), nc, cs, rblocks, t, t.l2l_chunk0[c], t.l2l_nchunk[c], L, L, s);
         } else {
             const size_t sm = 2 * (size_t)(p + 1) * W * sizeof(cpx<T>);
             set_smem<T>(k_l2l<T>, sm);
@@ -1965,9 +2073,7 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
         T *M = B::M(m), *L = B::L(m);
         const int rblocks = cdiv(nc, TR_BM);
         const size_t trsm = translate_smem<T, TR_BN_M2L>();
-        const size_t trsm_t = translate_smem<T, TR_BN_TREE>();
         set_smem<T>(k_translate<T, TR_BN_M2L, TR_THREADS>, trsm);
-        set_smem<T>(k_translate<T, TR_BN_TREE, TR_THREADS_TREE>, trsm_t);
         {
             const int th = std::max(32, p2m_threads(p, sizeof(T)));
             const size_t sm = (size_t)th * nc * sizeof(T);
@@ -1978,21 +2084,11 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
         if (t.L >= 3)
             BEM_CUDA(cudaMemsetAsync(M + (size_t)t.lvl_off[2] * cs, 0,
                                      (size_t)(t.lvl_off[t.L] - t.lvl_off[2]) * cs * sizeof(T), s));
-        for (int c = t.L; c >= 3; --c) {
-            if (t.m2m_nchunk[c] == 0) continue;
-            dim3 g(t.m2m_nchunk[c], rblocks);
-            k_translate<T, TR_BN_TREE, TR_THREADS_TREE><<<g, TR_THREADS_TREE, trsm_t, s>>>(B::Om2m(m), nc, cs, t.g_chunk.p + t.m2m_chunk0[c],
-                                                                      t.g_out.p, t.g_in.p, M, M);
-            BEM_CHECK_LAUNCH();
-        }
+        for (int c = t.L; c >= 3; --c)
+            tree_translate<T>(B::Om2m(m), nc, cs, rblocks, t, t.m2m_chunk0[c], t.m2m_nchunk[c], M, M, s);
         m2l_dense<T>(m, t, B::Om2l(m), nc, cs, rblocks, trsm, M, L);
-        for (int c = 3; c <= t.L; ++c) {
-            if (t.l2l_nchunk[c] == 0) continue;
-            dim3 g(t.l2l_nchunk[c], rblocks);
-            k_translate<T, TR_BN_TREE, TR_THREADS_TREE><<<g, TR_THREADS_TREE, trsm_t, s>>>(B::Ol2l(m), nc, cs, t.g_chunk.p + t.l2l_chunk0[c],
-                                                                      t.g_out.p, t.g_in.p, L, L);
-            BEM_CHECK_LAUNCH();
-        }
+        for (int c = 3; c <= t.L; ++c)
+            tree_translate<T>(B::Ol2l(m), nc, cs, rblocks, t, t.l2l_chunk0[c], t.l2l_nchunk[c], L, L, s);
         const size_t sm = (size_t)(p + 1) * (2 * p + 1) * sizeof(cpx<T>);
         auto kern = k_l2p<T, TGT_QUAD_PHI>;
         set_smem<T>(kern, sm);
