@@ -14,32 +14,70 @@ static void leaf_smem(KernelT kern, size_t bytes) {
 }
 
 // ------------------------------------------------------------------- P2M
-// A CTA of `warps` warps owns one leaf; each warp takes 32 points at a time,
-// writes their strength-weighted harmonics into its own row buffer (odd row
-// stride: the column reads below hit 32 different banks) and every lane adds
-// up its columns over the 32 rows in registers.  The warps' column sums are
-// added in a fixed order at the end.  Lanes without a point write zero rows.
-template <class T, int P>
-static constexpr int p2m_row_stride() { return ((P + 1) * (P + 1)) | 1; }
+// A CTA of 4 warps owns one leaf; each warp takes 32 points at a time.  The
+// recurrence emits a point's (p+1)^2 real values in a fixed order (slot k:
+// m = 0 values first, then the re / -im pairs column by column); every 32
+// slots a warp's lanes have written one 32 x 32 block of its row buffer
+// (stride 33: conflict-free both ways), and each lane adds up its column of
+// the block over the 32 points in registers.  The warps' column sums are
+// added in a fixed order at the end.  Lanes without a point write zeros.
+constexpr int P2M_WARPS = 4;
+constexpr int P2M_RS = 33;
+
+// slot of R_n^m (re; im at +1) in the emission order, and its compact index
+template <int P>
+__host__ __device__ constexpr int p2m_slot(int n, int m) {
+    return m == 0 ? n : (P + 1) + (m - 1) * (2 * P + 2 - m) + 2 * (n - m);
+}
+template <int P>
+__device__ constexpr int p2m_compact(int k) {
+    // inverse of p2m_slot, then the compact real layout (n^2, n^2 + 2m - 1 | n^2 + 2m)
+    if (k <= P) return k * k;
+    int m = 1;
+    while (p2m_slot<P>(P, m) + 1 < k) ++m;
+    const int off = k - p2m_slot<P>(m, m);
+    const int n = m + off / 2;
+    return n * n + 2 * m - 1 + (off & 1);
+}
 
 template <class T, int SRC, int P>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(P2M_WARPS * 32)
 k_p2m_c(TreeView tv, const typename V4T<T>::t *rec, int cs, T inv_h, T *M) {
     constexpr int NC = (P + 1) * (P + 1);
-    constexpr int RS = p2m_row_stride<T, P>();
     constexpr int KC = (NC + 31) / 32;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sm = reinterpret_cast<T *>(smraw);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    T *buf = sm + (size_t)w * 32 * RS;
-    T *row = buf + lane * RS;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T *buf = sm + (size_t)w * 32 * P2M_RS;
+    T *row = buf + lane * P2M_RS;
     const int leaf = blockIdx.x;
     const int *beg = SRC == SRC_QUAD ? tv.qp_beg : tv.chg_beg;
     const int b = beg[leaf], e = beg[leaf + 1];
     T acc[KC];
 #pragma unroll
     for (int k = 0; k < KC; ++k) acc[k] = 0;
-    for (int base = b + w * 32; base < e; base += nw * 32) {
+    auto flush = [&](int chunk) {  // column `lane` of block `chunk`, summed over the 32 rows
+        __syncwarp();
+        if (32 * chunk + lane < NC) {
+            T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                s0 += buf[j * P2M_RS + lane];
+                s1 += buf[(j + 1) * P2M_RS + lane];
+                s2 += buf[(j + 2) * P2M_RS + lane];
+                s3 += buf[(j + 3) * P2M_RS + lane];
+            }
+#pragma unroll
+            for (int k = 0; k < KC; ++k)
+                if (k == chunk) acc[k] += (s0 + s1) + (s2 + s3);
+        }
+        __syncwarp();
+    };
+    auto put = [&](int k, T v) {
+        row[k & 31] = v;
+        if ((k & 31) == 31 || k == NC - 1) flush(k >> 5);
+    };
+    for (int base = b + w * 32; base < e; base += P2M_WARPS * 32) {
         const int i = base + lane;
         T x = 0, y = 0, z = 0, s = 0;
         if (i < e) {
@@ -50,29 +88,10 @@ k_p2m_c(TreeView tv, const typename V4T<T>::t *rec, int cs, T inv_h, T *M) {
             s = r.w;
         }
         regular_solid_c<T, P>(x, y, z, [&](int n, int m, T re, T im) {
-            if (m == 0) row[n * n] = s * re;
-            else {
-                row[n * n + 2 * m - 1] = s * re;
-                row[n * n + 2 * m] = -s * im;
-            }
+            const int k = p2m_slot<P>(n, m);
+            put(k, s * re);
+            if (m > 0) put(k + 1, -s * im);
         });
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-            const int c = lane + 32 * k;
-            if (c < NC) {
-                T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-#pragma unroll
-                for (int j = 0; j < 32; j += 4) {
-                    s0 += buf[j * RS + c];
-                    s1 += buf[(j + 1) * RS + c];
-                    s2 += buf[(j + 2) * RS + c];
-                    s3 += buf[(j + 3) * RS + c];
-                }
-                acc[k] += (s0 + s1) + (s2 + s3);
-            }
-        }
-        __syncwarp();
     }
     __syncthreads();
 #pragma unroll
@@ -82,10 +101,15 @@ k_p2m_c(TreeView tv, const typename V4T<T>::t *rec, int cs, T inv_h, T *M) {
     }
     __syncthreads();
     T *out = M + (size_t)(tv.leaf0 + leaf) * cs;
-    for (int c = threadIdx.x; c < NC; c += blockDim.x) {
-        T a = 0;
-        for (int v = 0; v < nw; ++v) a += sm[v * NC + c];
-        out[c] = a;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const int c = threadIdx.x + P2M_WARPS * 32 * k;
+        if (c < NC) {
+            T a = 0;
+#pragma unroll
+            for (int v = 0; v < P2M_WARPS; ++v) a += sm[v * NC + c];
+            out[p2m_compact<P>(c)] = a;
+        }
     }
 }
 
@@ -94,13 +118,11 @@ k_p2m_c(TreeView tv, const typename V4T<T>::t *rec, int cs, T inv_h, T *M) {
 template <class T, int SRC, int P>
 static void p2m_launch_c(const TreeView &tv, int nleaf, const typename V4T<T>::t *src, int cs, T inv_h,
                          T *M, cudaStream_t s) {
-    // as many warps per CTA (up to 4) as keep the row buffers within 96 KB
-    constexpr size_t row = (size_t)32 * p2m_row_stride<T, P>() * sizeof(T);
-    const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (96 * 1024) / row));
-    const size_t sm = warps * row;
+    constexpr int NC = (P + 1) * (P + 1);
+    const size_t sm = std::max<size_t>((size_t)P2M_WARPS * 32 * P2M_RS, (size_t)P2M_WARPS * NC) * sizeof(T);
     auto kern = k_p2m_c<T, SRC, P>;
     leaf_smem(kern, sm);
-    kern<<<nleaf, warps * 32, sm, s>>>(tv, src, cs, inv_h, M);
+    kern<<<nleaf, P2M_WARPS * 32, sm, s>>>(tv, src, cs, inv_h, M);
     BEM_CHECK_LAUNCH();
 }
 
