@@ -132,7 +132,7 @@ size_t Mesh::bytes() const {
          ntT_val.bytes() + qp_of_panel.bytes();
     if (tab) b += tab->bytes();
     b += Mf.bytes() + Lf.bytes() + Md.bytes() + Ld.bytes();
-    b += Mtc.bytes() + m2lR.bytes() + str32.bytes() + str64.bytes() + dpart_f.bytes() + dpart_d.bytes();
+    b += Mtc.bytes() + m2lR.bytes() + ctq.bytes() + str32.bytes() + str64.bytes() + dpart_f.bytes() + dpart_d.bytes();
     b += xs.bytes() + ys.bytes() + zs.bytes() + far_f.bytes() + near_f.bytes() + far_d.bytes() +
          near_d.bytes() + io_a.bytes() + io_b.bytes() + red.bytes();
     b += dev_err.bytes();
@@ -280,6 +280,7 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
         build_translation_groups(*m, m->tc);
         alloc_work(*m);
         if (m->opt.near_table) build_near_table(*m, dp);
+        build_ctq(*m);
         sync(*m);
         m->ms_build = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     });
@@ -338,6 +339,7 @@ int bem_set_charges(bem_mesh *m, const double *charges, int64_t n_c) {
         rebuild_charge_tree(*m, dc);
         build_translation_groups(*m, m->tc);
         alloc_work(*m);
+        build_ctq(*m);
         m->have_sigma = false;
         sync(*m);
     });
@@ -442,6 +444,7 @@ int bem_solve(bem_mesh *m, const double *x0, double *sigma, bem_solve_stats *st)
 
 static double energy_sorted(Mesh &m, const double *sig_s, double *phi_user) {
     if (m.nc == 0) return 0.0;
+    if (!phi_user && m.ctq_ok) return energy_from_ctq(m, sig_s);
     double *phi_s = m.zs.p;  // n_c <= 3 * max(n_p, n_c)
     charge_pass(m, SRC_QUAD, TGT_CHG_PHI, sig_s, phi_s);
     const double dG = energy_from_phi(m, phi_s);

@@ -111,7 +111,7 @@ template <class T>
 static void direct_impl(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, double *out,
                         DArray<T> &part) {
     cudaStream_t s = m.stream;
-    const int64_t ntgt = (tk == TGT_CEN_DN) ? m.np : (tk == TGT_QUAD_DN ? m.nqp : m.nc);
+    const int64_t ntgt = (tk == TGT_CEN_DN) ? m.np : ((tk == TGT_QUAD_DN || tk == TGT_QUAD_PHI) ? m.nqp : m.nc);
     // Galerkin rows: the values at the quadrature points, then the rule's
     // average over each panel
     double *const final_out = out;
@@ -136,7 +136,7 @@ static void direct_impl(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, dou
     if (part.n < need) part.alloc(need);
     const double ox = m.root_min[0] + 0.5 * m.side, oy = m.root_min[1] + 0.5 * m.side,
                  oz = m.root_min[2] + 0.5 * m.side;
-    const double *tpos = (tk == TGT_CEN_DN) ? m.cen64.p : (tk == TGT_QUAD_DN ? m.qpg64.p : m.chgg64.p);
+    const double *tpos = (tk == TGT_CEN_DN) ? m.cen64.p : ((tk == TGT_QUAD_DN || tk == TGT_QUAD_PHI) ? m.qpg64.p : m.chgg64.p);
     const double *spos = (sk == SRC_QUAD) ? m.qpg64.p : m.chgg64.p;
     const double *sw = (sk == SRC_QUAD) ? m.qw64.p : m.q64.p;
     dim3 grid(tblocks, nsplit);
@@ -152,7 +152,10 @@ static void direct_impl(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, dou
     else if (sk == SRC_CHARGE && tk == TGT_QUAD_DN)
         k_direct<T, SRC_CHARGE, TGT_QUAD_DN><<<grid, DIRECT_THREADS, 0, s>>>(
             ntgt, nsrc, chunk, tpos, m.nrmq64.p, spos, sw, nullptr, dens, ox, oy, oz, part.p);
-    else if (sk == SRC_QUAD && tk == TGT_QUAD_DN)
+    else if (sk == SRC_CHARGE && tk == TGT_QUAD_PHI)
+        k_direct<T, SRC_CHARGE, TGT_QUAD_PHI><<<grid, DIRECT_THREADS, 0, s>>>(
+            ntgt, nsrc, chunk, tpos, nullptr, spos, sw, nullptr, dens, ox, oy, oz, part.p);
+    else if (sk == SRC_QUAD && (tk == TGT_QUAD_DN || tk == TGT_QUAD_PHI))
         throw Error(BEM_EUNSUPPORTED, "direct quadrature-to-quadrature sums not built");
     else
         k_direct<T, SRC_CHARGE, TGT_CHG_PHI><<<grid, DIRECT_THREADS, 0, s>>>(
@@ -165,6 +168,36 @@ static void direct_impl(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, dou
                                                     m.np, final_out);
         BEM_CHECK_LAUNCH();
     }
+}
+
+// out_j = sum_q qw_jq v_jq (the rule's weights include the panel area)
+__global__ void k_panel_wsum(const double *v, const int *qp_of_panel, const double *qw, int nq, int64_t np,
+                             double *out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    double a = 0.0;
+    for (int q = 0; q < nq; ++q) {
+        const int k = qp_of_panel[j * nq + q];
+        a += qw[k] * v[k];
+    }
+    out[j] = a;
+}
+
+// C^T q in the sorted panel order: (C^T q)_j = sum_q A_j w_q psi(y_jq) with
+// psi(y) = sum_k q_k G(x_k, y), so that q . (C sigma) = (C^T q) . sigma and
+// the solvation energy of any sigma is one dot product (Eq. energy).  Built
+// in the product's precision for meshes whose charge sums are direct.
+void build_ctq(Mesh &m) {
+    m.ctq_ok = false;
+    if (m.nc == 0 || !charge_direct(m)) return;
+    if (m.ctq.n < (size_t)m.np) m.ctq.alloc(m.np);
+    DArray<double> psi;
+    psi.alloc(m.nqp);
+    direct_pass(m, SRC_CHARGE, TGT_QUAD_PHI, nullptr, psi.p);
+    k_panel_wsum<<<cdiv(m.np, 256), 256, 0, m.stream>>>(psi.p, m.qp_of_panel.p, m.qw64.p, (int)m.nq, m.np, m.ctq.p);
+    BEM_CHECK_LAUNCH();
+    BEM_CUDA(cudaStreamSynchronize(m.stream));
+    m.ctq_ok = true;
 }
 
 void direct_pass(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, double *out) {

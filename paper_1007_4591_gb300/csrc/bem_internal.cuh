@@ -215,6 +215,8 @@ struct Mesh {
     DArray<double4> nrmq64r;
     DArray<double> nrmq64;
     DArray<double> gq_tmp;             // [nqp] Galerkin scratch (direct sums at the quadrature points)
+    DArray<double> ctq;                // [np] C^T q (sorted panels), valid when ctq_ok
+    bool ctq_ok = false;
     DArray<uint64_t> cen_key;
     // sorted quadrature points (sources)
     DArray<int> qp_panel;        // sorted quad point -> sorted panel
@@ -323,6 +325,8 @@ bool is_near_field_kernel(const void *func);
 void charge_pass(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, double *out);
 bool charge_direct(const Mesh &m);
 void direct_pass(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, double *out);
+void build_ctq(Mesh &m);
+double energy_from_ctq(Mesh &m, const double *sig_s);
 
 // solver pieces (bem_solver.cu)
 void matvec_sorted(Mesh &m, const double *xs, double *ys);

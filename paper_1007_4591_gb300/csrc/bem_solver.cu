@@ -387,6 +387,20 @@ int gmres_solve(Mesh &m, const double *b, double *x, bool transpose, bem_solve_s
     return conv ? BEM_OK : BEM_ENOCONV;
 }
 
+// dG = 4 pi 332.0637 / (2 eps_in) * (C^T q) . sigma
+double energy_from_ctq(Mesh &m, const double *sig_s) {
+    const int64_t n = m.np;
+    const int nch = nchunk_for(n);
+    const int chunk = (int)((n + nch - 1) / nch);
+    dim3 grid(nch, 1);
+    k_dot_parts<<<grid, RED_THREADS, 0, m.stream>>>(m.ctq.p, 0, sig_s, n, chunk, m.part.p);
+    BEM_CHECK_LAUNCH();
+    k_finish<<<1, RED_THREADS, 0, m.stream>>>(m.part.p, nch, m.red.p + 2, 0);
+    BEM_CHECK_LAUNCH();
+    const double ctqs = read_scalar(m, m.red.p + 2);
+    return FOUR_PI * KCAL / (2.0 * m.eps_in) * ctqs;
+}
+
 // dG = 4 pi 332.0637 / (2 eps_in) * q . phi   (phi = C sigma, G = 1/(4 pi r))
 double energy_from_phi(Mesh &m, const double *phi_s) {
     const int64_t n = m.nc;
