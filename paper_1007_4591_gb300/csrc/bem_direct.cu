@@ -126,8 +126,8 @@ static void direct_impl(Mesh &m, SrcKind sk, TgtKind tk, const double *dens, dou
         return;
     }
     const int tblocks = cdiv(ntgt, DIRECT_THREADS);
-    // enough CTAs to fill the GPU several times, at most 4096 sources per split
-    int nsplit = std::max(1, (int)std::min<int64_t>(cdiv(nsrc, 4096), std::max(1, 1216 / tblocks)));
+    // enough CTAs to fill the GPU about twice (16 per SM), splits of at least 512 sources
+    int nsplit = std::max(1, (int)std::min<int64_t>(cdiv(nsrc, 512), std::max(1, 2432 / tblocks)));
     nsplit = std::min(nsplit, 65535);
     int64_t chunk = (nsrc + nsplit - 1) / nsplit;
     chunk = ((chunk + DIRECT_THREADS - 1) / DIRECT_THREADS) * DIRECT_THREADS;
