@@ -5,7 +5,7 @@ oracle computes one by one, or by properties that hold at any size.
   (mixed precision, p = 10, leaf size 64);
 * globular-s7 (327,680 panels): sampled rows of the product, and the energy
   gradients of one autograd call against the FP64 GPU form and central
-  differences;
+  differences in q and x on 20 seeded charges;
 * batch64 (64 uneven molecules, 9.5M panels): batched solve against
   one-at-a-time solves and the BIBEE bounds around every solve;
 * lattice10 (1,000 rotated copies of globular-s6, 81.9M panels): sampled
@@ -68,7 +68,8 @@ def test_globular_s7_rows(pkg):
 def test_globular_s7_gradients(pkg):
     """One autograd call (mixed precision) gives d dG/dq and d dG/dx of all
     2,000 charges; they match the FP64 GPU form, whose own derivatives match
-    central differences (steps 1e-4 e, 1e-4 A) on seeded charges."""
+    central differences (steps 1e-4 e and 1e-4 A, every perturbed solve
+    started from the unperturbed one) on 20 seeded charges."""
     m = synth.globular(7)
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=10, leaf_size=64, precision=0,
                   tol=1e-10) as g:
@@ -80,9 +81,11 @@ def test_globular_s7_gradients(pkg):
         dg_mixed = float(dg.detach())
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=12, leaf_size=64, precision=1,
                   tol=1e-12, max_iter=500) as g:
+        s0, _ = g.solve()
+
         def energy(c):
             g.set_charges(torch.tensor(c).cuda())
-            s, _ = g.solve()
+            s, _ = g.solve(x0=s0)
             return g.energy(s)
         e0 = energy(m.charges)
         dq, dx = g.energy_backward(1.0)
@@ -90,17 +93,19 @@ def test_globular_s7_gradients(pkg):
         assert abs(dg_mixed - e0) < 1e-5 * abs(e0), (dg_mixed, e0)
         assert rel(gq_mixed, dq) < 1e-5, rel(gq_mixed, dq)
         assert rel(gx_mixed, dx) < 1e-4, rel(gx_mixed, dx)
-        for k in np.random.default_rng(3).choice(m.n_c, 2, replace=False):
+        rng = np.random.default_rng(3)
+        for k in rng.choice(m.n_c, 20, replace=False):
             cp, cm = m.charges.copy(), m.charges.copy()
             cp[k, 3] += 1e-4
             cm[k, 3] -= 1e-4
             fd = (energy(cp) - energy(cm)) / 2e-4
             assert abs(fd - dq[k]) < 1e-5 * max(1.0, abs(dq[k])), (k, fd, dq[k])
+            a = int(rng.integers(3))
             cp, cm = m.charges.copy(), m.charges.copy()
-            cp[k, 0] += 1e-4
-            cm[k, 0] -= 1e-4
+            cp[k, a] += 1e-4
+            cm[k, a] -= 1e-4
             fd = (energy(cp) - energy(cm)) / 2e-4
-            assert abs(fd - dx[k, 0]) < 1e-4 * max(1.0, np.abs(dx).max()), (k, fd, dx[k, 0])
+            assert abs(fd - dx[k, a]) < 1e-4 * max(1.0, np.abs(dx).max()), (k, a, fd, dx[k, a])
 
 
 def test_batch64_solve_and_bounds(pkg):
