@@ -440,23 +440,6 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
     const int ntgt = te - tb;
     const v2 EPS2 = P::mk(P2PEps<T>::v, P2PEps<T>::v);
     constexpr int MAXT = (P2PF_THREADS / 4) * P2P_TPT;  // targets per pass (G >= 4)
-    // staged source v (0 <= v < total) in the target leaf's frame, or a zero-weight dummy
-    auto fetch = [&](int v, T &x, T &y, T &z, T &w) {
-        x = y = z = w = 0;
-        if (v < total) {
-            int lo = 0, hi = nn;  // segment k with s_cum[k] <= v < s_cum[k+1]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (s_cum[mid] <= v) lo = mid;
-                else hi = mid;
-            }
-            const V4 r = src[s_beg[lo] + (v - s_cum[lo])];
-            x = r.x + s_off[lo][0];
-            y = r.y + s_off[lo][1];
-            z = r.z + s_off[lo][2];
-            w = r.w;
-        }
-    };
     for (int t0 = 0; t0 < ntgt; t0 += MAXT) {
         const int nt = min(ntgt - t0, MAXT);
         const int ngroups = (nt + P2P_TPT - 1) / P2P_TPT;
@@ -491,17 +474,32 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
         }
         for (int vb = 0; vb < total; vb += P2PF_TILE) {
             __syncthreads();
-#pragma unroll
-            for (int f = 0; f < P2PF_PAIRS / P2PF_THREADS; ++f) {
-                const int pi = threadIdx.x + f * P2PF_THREADS;
-                T x0, y0, z0, w0, x1, y1, z1, w1;
-                fetch(vb + 2 * pi, x0, y0, z0, w0);
-                fetch(vb + 2 * pi + 1, x1, y1, z1, w1);
-                V4 a, b;
-                a.x = x0; a.y = x1; a.z = y0; a.w = y1;
-                b.x = z0; b.y = z1; b.z = w0; b.w = w1;
-                shA[pi] = a;
-                shB[pi] = b;
+            // the tile [vb, ve) walks the neighbour segments it overlaps; the
+            // threads copy each overlap as one contiguous run (source v to
+            // slot v - vb: pair (v - vb) / 2, lane (v - vb) % 2)
+            const int ve = min(vb + P2PF_TILE, total);
+            int k = 0;
+            while (s_cum[k + 1] <= vb) ++k;
+            for (; k < nn && s_cum[k] < ve; ++k) {
+                const int lo = max(s_cum[k], vb), hi = min(s_cum[k + 1], ve);
+                const int sb = s_beg[k] - s_cum[k];
+                const T ox = s_off[k][0], oy = s_off[k][1], oz = s_off[k][2];
+                for (int v = lo + threadIdx.x; v < hi; v += P2PF_THREADS) {
+                    const V4 r = src[sb + v];
+                    const int u = v - vb;
+                    T *a = reinterpret_cast<T *>(shA + (u >> 1)) + (u & 1);
+                    T *b = reinterpret_cast<T *>(shB + (u >> 1)) + (u & 1);
+                    a[0] = r.x + ox;
+                    a[2] = r.y + oy;
+                    b[0] = r.z + oz;
+                    b[2] = r.w;
+                }
+            }
+            if (((ve - vb) & 1) && threadIdx.x == 0) {  // odd tail: a zero-weight partner
+                const int u = ve - vb;
+                T *a = reinterpret_cast<T *>(shA + (u >> 1)) + 1;
+                T *b = reinterpret_cast<T *>(shB + (u >> 1)) + 1;
+                a[0] = a[2] = b[0] = b[2] = 0;
             }
             __syncthreads();
             const int npair = min(P2PF_PAIRS, (total - vb + 1) >> 1);
