@@ -73,6 +73,10 @@ extern "C" {
 #define BEM_FLAG_CHECK_CHARGES 8u /* bem_mesh_create rejects (BEM_EINVAL) a charge the surface
                                      does not enclose (winding number from the panels' solid
                                      angles; checked when n_c x n_p x 7 <= 4e10, skipped above) */
+#define BEM_FLAG_M2L_REDUCE 16u   /* tensor-core M2L: add each pair's row into its target with a
+                                     bulk reduction even where the per-pair rows (store, then a
+                                     fixed-order sum per target) would fit; the form used for
+                                     problems whose rows exceed 1 GiB */
 
 /* bem_options.near_table */
 #define BEM_NEAR_QUADRATURE 1

@@ -1514,7 +1514,7 @@ void build_translation_groups(Mesh &m, Tree &t) {
         t.m2l_nchunk = (int)chunks.size();
         build_tc_super(t, chunks, s);
         // pairs by target cell for the store-then-sum tensor-core M2L
-        t.m2l_store = use_tc_m2l(m) && m2l_store_fits(nm, m.opt.p);
+        t.m2l_store = use_tc_m2l(m) && m2l_store_fits(nm, m.opt.p) && !(m.opt.flags & BEM_FLAG_M2L_REDUCE);
         if (t.m2l_store) {
             const int ncl = last - first;
             std::vector<int> toff(ncl + 1, 0), tp(nm);

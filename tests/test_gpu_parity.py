@@ -75,6 +75,23 @@ def test_tensor_core_m2l_matches_simt(pkg, small4):
     assert rel(ys[1] - x, ys[0] - x) < 2e-6
 
 
+def test_tensor_core_m2l_epilogues_agree(pkg, small4):
+    """The two epilogues of the tensor-core M2L: per-pair rows stored and
+    summed per target in a fixed order (the default), and bulk reductions into
+    the targets (BEM_FLAG_M2L_REDUCE, the form for rows above 1 GiB); both
+    against the dense FP64 oracle."""
+    m, P = small4
+    x = np.random.default_rng(12).standard_normal(m.n_p)
+    ref = P.A(x)
+    ys = []
+    for flags in (0, pkg.BEM_FLAG_M2L_REDUCE):
+        with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=4, p=10, m2l_mode=3,
+                      flags=flags) as g:
+            ys.append(g.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
+        assert rel(ys[-1], ref) < 1e-5, (flags, rel(ys[-1], ref))
+    assert rel(ys[1] - x, ys[0] - x) < 1e-6
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_translation_modes_agree(pkg, small4, precision):
     """The grouped dense operators and the per-target complex sums are the same
@@ -117,13 +134,20 @@ def test_rhs_matches_oracle(pkg, small4):
     assert rel(b, P.rhs()) < 1e-5
 
 
-def test_energy_of_given_sigma(pkg, small4):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_energy_of_given_sigma(pkg, small4, precision):
+    """dG from the dot product with C^T q (built once per charge set) and
+    from phi = C sigma at the charges (the path taken when phi is asked for)
+    both match the oracle, and each other to rounding."""
     m, P = small4
     sig = P.bq()
     dg_ref, phi_ref = P.energy(sig)
-    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=3, p=12) as g:
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=3, p=12, precision=precision) as g:
+        dg_ctq = g.energy(torch.from_numpy(sig).cuda())
         dg, phi = g.energy(torch.from_numpy(sig).cuda(), want_phi=True)
     assert abs(dg - dg_ref) / abs(dg_ref) < 1e-5
+    assert abs(dg_ctq - dg_ref) / abs(dg_ref) < 1e-5
+    assert abs(dg_ctq - dg) / abs(dg_ref) < (1e-6 if precision == 0 else 1e-12), (dg_ctq, dg)
     assert rel(phi.cpu().numpy(), phi_ref / m.eps_in) < 1e-5
 
 
