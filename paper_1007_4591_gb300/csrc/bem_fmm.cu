@@ -1317,11 +1317,12 @@ k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ 
 // cp.async, then each thread forms 8 rows x (BN / 16) pair columns (columns
 // strided by 16; input rows padded to 4 mod 32 words: at most 2-way bank
 // conflicts) and the results leave as coalesced atomic adds.
-template <class T, int BN, int NTH>
+template <class T, int BN, int NTH, int BM>
 __global__ void __launch_bounds__(NTH)
 k_tree_translate(const T *__restrict__ ops, int nc, int cs, int ldb, const int4 *__restrict__ chunks,
                  const int *__restrict__ p_out, const int *__restrict__ p_in, const T *__restrict__ in,
                  T *__restrict__ out) {
+    constexpr int TR_BM = BM;       // output rows of this CTA
     constexpr int NTY = TR_BM / 8;  // row groups of 8
     constexpr int NTX = NTH / NTY;  // column groups
     constexpr int CPT = BN / NTX;   // columns per thread
@@ -1335,7 +1336,10 @@ k_tree_translate(const T *__restrict__ ops, int nc, int cs, int ldb, const int4 
     const int4 ch = chunks[blockIdx.x];
     const T *Tt = ops + (size_t)ch.x * nc * cs;
     const int rb = blockIdx.y * TR_BM;
-    const int tid = threadIdx.x, ty = tid / NTX, tx = tid - ty * NTX;
+    // a warp covers 8 pair columns x 4 row groups: its input-row loads hit 8
+    // different banks and its operator loads one 128-byte span
+    static_assert(NTX % 8 == 0, "tree translate thread map");
+    const int tid = threadIdx.x, rest = tid >> 3, ty = rest % NTY, tx = (tid & 7) + 8 * (rest / NTY);
     if (tid < BN) {
         s_in[tid] = tid < ch.z ? p_in[ch.y + tid] : -1;
         s_out[tid] = tid < ch.z ? p_out[ch.y + tid] : -1;
@@ -1404,10 +1408,11 @@ template <class T>
 static int tree_ldb(int cs) {
     return (int)(((cs * sizeof(T) + 127) / 128 * 128 + 16) / sizeof(T));
 }
+constexpr int TREE_BM = 64;  // operator rows per CTA (two CTAs per chunk at p = 10)
 template <class T>
 static size_t tree_translate_smem(int nc, int cs) {
-    const size_t ab = ((size_t)nc * TR_BM + (size_t)TR_BN_TREE * tree_ldb<T>(cs)) * sizeof(T);
-    return std::max(ab, (size_t)TR_BN_TREE * (TR_BM + 1) * sizeof(T));
+    const size_t ab = ((size_t)nc * TREE_BM + (size_t)TR_BN_TREE * tree_ldb<T>(cs)) * sizeof(T);
+    return std::max(ab, (size_t)TR_BN_TREE * (TREE_BM + 1) * sizeof(T));
 }
 constexpr size_t TREE_SMEM_MAX = 200 * 1024;  // above: the pipelined k_translate
 
@@ -1633,8 +1638,9 @@ static void tree_translate(const T *ops, int nc, int cs, int rblocks, const Tree
     dim3 g(nchunk, rblocks);
     const size_t sm = tree_translate_smem<T>(nc, cs);
     if (sm <= TREE_SMEM_MAX) {
-        set_smem<T>(k_tree_translate<T, TR_BN_TREE, TR_THREADS_TREE>, sm);
-        k_tree_translate<T, TR_BN_TREE, TR_THREADS_TREE><<<g, TR_THREADS_TREE, sm, s>>>(
+        dim3 gt(nchunk, cdiv(nc, TREE_BM));
+        set_smem<T>(k_tree_translate<T, TR_BN_TREE, TR_THREADS_TREE, TREE_BM>, sm);
+        k_tree_translate<T, TR_BN_TREE, TR_THREADS_TREE, TREE_BM><<<gt, TR_THREADS_TREE, sm, s>>>(
             ops, nc, cs, tree_ldb<T>(cs), t.g_chunk.p + chunk0, t.g_out.p, t.g_in.p, in, out);
     } else {
         const size_t trsm_t = translate_smem<T, TR_BN_TREE>();
