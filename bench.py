@@ -315,13 +315,19 @@ def run_ours(args):
     # stream (phases run one after another in this mode); the dominant one is
     # the "roofline" entry
     pkg.bem_set_profiling(mesh.h, True)
-    phases = []
+    phases, m2l_k = [], []
     for _ in range(max(3, min(args.steps, 10))):
         flush.fill_(1.0)
         pkg.bem_matvec(mesh.h, x, y)
         phases.append(pkg.bem_last_phase_ms(mesh.h))
+        m2l_k.append(pkg.bem_last_m2l_ms(mesh.h))
     pkg.bem_set_profiling(mesh.h, False)
     ph = {k: float(np.mean([d[k] for d in phases])) for k in phases[0]}
+    # the M2L phase holds three kernels: the multipole split, the tensor-core
+    # kernel and the per-target sum (zeros when the product has no
+    # tensor-core M2L: then the whole phase is the SIMT kernel)
+    mk = {k: float(np.mean([d[k] for d in m2l_k])) for k in m2l_k[0]}
+    t_m2l = mk["tc"] if mk["tc"] > 0 else ph["m2l"]
     peaks, src = _peaks()
     f_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * f_mhz * 1e6 / 1e12
@@ -341,14 +347,28 @@ def run_ours(args):
     m2l_flops = m2l_unit * info["m2l_pairs"]
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
     tf32_peak = bf16 * 1.1 / 2.25
-    rl_m2l = {"kernel": "k_m2l_tc (tensor-core M2L; stage time incl. k_split_m and the L memset)",
-              "bound": "tensor", "achieved": round(m2l_flops / (ph["m2l"] * 1e-3) / 1e12, 3),
+    rl_m2l = {"kernel": "k_m2l_tc (tensor-core M2L)" if mk["tc"] > 0 else "k_translate (M2L phase)",
+              "bound": "tensor", "achieved": round(m2l_flops / (t_m2l * 1e-3) / 1e12, 3),
               "peak": round(tf32_peak, 1), "unit": "TFLOP/s", "traffic": _traffic("k_m2l_tc"),
-              "time_ms": round(ph["m2l"], 4),
+              "time_ms": round(t_m2l, 4),
               "peak_source": f"dense TF32 = bf16 {bf16:.1f} TFLOP/s (MEASURED_PEAKS.json, {src}) x 1.1/2.25",
               "algorithmic": f"{m2l_unit:.0f} flop (rotation-form count, p={p}) x {info['m2l_pairs']} translations"}
     rl_m2l["frac"] = round(rl_m2l["achieved"] / tf32_peak, 4)
-    roofline = dict(rl_m2l if ph["m2l"] >= ph["p2p"] else rl_p2p)
+    # the per-target sum of the M2L rows: HBM bound, 496 B read per
+    # translation (the rows) plus 496 B written per target cell
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    cs = (((p + 1) ** 2 + 3) // 4) * 4
+    sum_bytes = 4 * cs * (info["m2l_pairs"] + info["cells"])
+    rl_sum = None
+    if mk["sum"] > 0:
+        rl_sum = {"kernel": "k_m2l_sum (per-target sum of the M2L rows)", "bound": "hbm",
+                  "achieved": round(sum_bytes / (mk["sum"] * 1e-3) / 1e9, 1), "peak": round(hbm, 1),
+                  "unit": "GB/s", "traffic": None, "time_ms": round(mk["sum"], 4),
+                  "peak_source": f"HBM copy {hbm:.1f} GB/s (MEASURED_PEAKS.json, {src})",
+                  "algorithmic": f"{4 * cs} B x ({info['m2l_pairs']} rows read + {info['cells']} cells written)"}
+        rl_sum["frac"] = round(rl_sum["achieved"] / hbm, 4)
+    # the dominant kernel: the longest single kernel of the product
+    roofline = dict(rl_m2l if t_m2l >= ph["p2p"] else rl_p2p)
     # the whole product: algorithmic flops of every stage / (time x FP32 peak)
     nq = info["source_points"]
     mm_unit = m2l_unit
@@ -390,9 +410,10 @@ def run_ours(args):
 
     L = info["depth"]
     # gather, source strengths, P2P, combine, operator epilogue, scatter;
-    # P2M, multipole split, M2L, L2P and one M2M and one L2L launch per level
-    # from 3 to L (16 kernels at L = 5, as the ncu launch list shows)
-    launches_per = 6 + (4 + 2 * (L - 2) if L >= 2 else 0)
+    # P2M, multipole split, M2L (tensor-core kernel, plus the per-target sum in
+    # the store form), L2P and one M2M and one L2L launch per level from 3 to
+    # L (17 kernels at L = 5, as the ncu launch list shows)
+    launches_per = 6 + ((4 + (1 if mk["sum"] > 0 else 0) + 2 * (L - 2)) if L >= 2 else 0)
     cpu = cpu_baseline(mol, budget_s=args.cpu_budget) if (rank == 0 and not args.no_cpu) else None
     mesh_graph = int(mesh.opt.graph)
     mesh.close()
@@ -407,7 +428,9 @@ def run_ours(args):
             "phases_ms": {k: round(v, 4) for k, v in ph.items()},
             "tree_build_s": round(tree_s, 4),
             "solve_s": round(solve_s, 4), "solve_iters": st["iterations"], "dG_kcal": dg,
-            "roofline": roofline, "roofline_kernels": {"p2p": rl_p2p, "m2l": rl_m2l},
+            "roofline": roofline,
+            "roofline_kernels": {"p2p": rl_p2p, "m2l": rl_m2l, **({"m2l_sum": rl_sum} if rl_sum else {})},
+            "m2l_kernels_ms": {k: round(v, 4) for k, v in mk.items()},
             "matvec_roofline": matvec_roofline, "cpu_baseline": cpu, "e2e": e2e,
             "precision_comparison": prec_cmp,
             "gpu_launches": launches_per * args.steps, "clocks": clocks,

@@ -276,6 +276,13 @@ int bem_set_device_memory_cap(size_t bytes);
 int bem_set_profiling(bem_mesh *mesh, int enable);
 int bem_last_phase_ms(const bem_mesh *mesh, double *times);
 
+/* Inside the M2L phase of the last profiled bem_matvec with the tensor-core
+ * M2L: device time (ms) of the multipole split (k_split_m), of the
+ * tensor-core kernel (k_m2l_tc) and of the per-target sum (k_m2l_sum; 0 in
+ * the reduction form).  times[3]; zeros if the product had no tensor-core M2L.
+ * BEM_EINVAL if profiling is off. */
+int bem_last_m2l_ms(const bem_mesh *mesh, double *times);
+
 /* Message for the calling thread's last error (static storage, never NULL). */
 const char *bem_last_error(void);
 

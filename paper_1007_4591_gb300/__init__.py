@@ -97,6 +97,7 @@ _SIGS = {
     "bem_set_wait_budget": [_vp, ctypes.c_longlong],
     "bem_set_device_memory_cap": [ctypes.c_size_t],
     "bem_last_phase_ms": [_vp, _vp],
+    "bem_last_m2l_ms": [_vp, _vp],
     "bem_last_error": [],
     "bem_batch_solve": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
     "bem_normal_field_noalloc": [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp, _vp],
@@ -258,6 +259,12 @@ def bem_last_phase_ms(h):
     t = np.zeros(7)
     _check(load_library().bem_last_phase_ms(h, _ptr(t)), "bem_last_phase_ms")
     return dict(zip(["p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "epilogue"], t.tolist()))
+
+
+def bem_last_m2l_ms(h):
+    t = np.zeros(3)
+    _check(load_library().bem_last_m2l_ms(h, _ptr(t)), "bem_last_m2l_ms")
+    return dict(zip(["split", "tc", "sum"], t.tolist()))
 
 
 def bem_batch_solve(meshes, threads: int = 8, sigmas=None):

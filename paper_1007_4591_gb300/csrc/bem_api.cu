@@ -309,6 +309,8 @@ int bem_mesh_destroy(bem_mesh *m) {
         if (m->stream) cudaStreamSynchronize(m->stream);
         for (auto &e : m->tm.ev)
             if (e) cudaEventDestroy(e);
+        for (auto &e : m->tm.kev)
+            if (e) cudaEventDestroy(e);
         if (m->h_pinned) cudaFreeHost(m->h_pinned);
         if (m->g_mv) cudaGraphExecDestroy(m->g_mv);
         if (m->stream2) cudaStreamSynchronize(m->stream2);
@@ -570,8 +572,10 @@ int bem_set_device_memory_cap(size_t bytes) {
 int bem_set_profiling(bem_mesh *m, int enable) {
     if (!m) return BEM_EINVAL;
     return guarded([&] {
-        if (enable && !m->tm.ev[0])
+        if (enable && !m->tm.ev[0]) {
             for (auto &e : m->tm.ev) BEM_CUDA(cudaEventCreate(&e));
+            for (auto &e : m->tm.kev) BEM_CUDA(cudaEventCreate(&e));
+        }
         m->tm.on = enable != 0;
     });
 }
@@ -586,6 +590,23 @@ int bem_last_phase_ms(const bem_mesh *m, double *times) {
         float ms = 0;
         if (cudaEventElapsedTime(&ms, m->tm.ev[k], m->tm.ev[k + 1]) != cudaSuccess) {
             cudaGetLastError();
+            ms = 0;
+        }
+        times[k] = ms;
+    }
+    return BEM_OK;
+}
+
+int bem_last_m2l_ms(const bem_mesh *m, double *times) {
+    if (!m || !times) return BEM_EINVAL;
+    if (!m->tm.on || !m->tm.kev[0]) {
+        set_last_error("profiling is off");
+        return BEM_EINVAL;
+    }
+    for (int k = 0; k < 3; ++k) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, m->tm.kev[k], m->tm.kev[k + 1]) != cudaSuccess) {
+            cudaGetLastError();  // not recorded (no tensor-core M2L in the last product)
             ms = 0;
         }
         times[k] = ms;

@@ -1658,7 +1658,7 @@ bool use_tc_m2l(const Mesh &m) {
 
 template <class T>
 static void m2l_dense(Mesh &m, const Tree &t, const T *Oop, int nc, int cs, int rblocks, size_t trsm,
-                      T *M, T *L);
+                      T *M, T *L, bool timed = false);
 
 template <class T>
 static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const double *dens,
@@ -1751,7 +1751,7 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
         ev_rec(m, timed, 2);
         // M2L: every cell at levels 2..L
         if (dense) {
-            m2l_dense<T>(m, t, B::Om2l(m), nc, cs, rblocks, trsm, M, L);
+            m2l_dense<T>(m, t, B::Om2l(m), nc, cs, rblocks, trsm, M, L, timed);
         } else {
             const size_t sm = ((size_t)(p + 1) * W + (size_t)(2 * p + 1) * W2) * sizeof(cpx<T>);
             set_smem<T>(k_m2l<T>, sm);
@@ -2029,11 +2029,11 @@ void build_near_table(Mesh &m, const double *panels) {
 
 template <class T>
 static void m2l_dense(Mesh &m, const Tree &t, const T *Oop, int nc, int cs, int rblocks, size_t trsm,
-                      T *M, T *L) {
+                      T *M, T *L, bool timed) {
     // L at levels >= 2 = the M2L sums (cleared first unless written whole)
     if constexpr (std::is_same<T, float>::value) {
         if (use_tc_m2l(m)) {
-            m2l_tc(m, t, M, L);
+            m2l_tc(m, t, M, L, timed);
             return;
         }
     }

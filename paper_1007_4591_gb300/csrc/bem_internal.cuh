@@ -180,6 +180,7 @@ struct Timers {
     bool on = false;
     cudaEvent_t ev[8] = {};
     double ms[7] = {};
+    cudaEvent_t kev[4] = {};  // inside the tensor-core M2L stage: split | kernel | sum
 };
 
 struct Mesh {
@@ -296,7 +297,7 @@ bool tc_m2l_available(const Mesh &m);
 void build_tc_tables(int p, const std::vector<double> &om2l, int nops, std::vector<float> &hi,
                      std::vector<float> &lo);
 void build_tc_super(Tree &t, const std::vector<int4> &chunks_m2l, cudaStream_t s);
-void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L);
+void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed = false);
 bool use_tc_m2l(const Mesh &m);
 size_t tc_staging_floats(const Mesh &m);
 size_t m2l_store_floats(const Mesh &m);

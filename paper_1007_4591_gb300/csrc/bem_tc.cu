@@ -585,7 +585,7 @@ bool m2l_store_fits(int64_t npairs, int p) {
 // L (levels >= 2) = sum over the M2L pairs of T_o M_s.  STORE: per-pair rows
 // into the mesh's buffer, then a fixed-order sum per target (deterministic);
 // otherwise L is cleared and the rows are added by bulk reductions.
-void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L) {
+void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed) {
     const int nc = (m.opt.p + 1) * (m.opt.p + 1);
     const int cs = cell_stride(m.opt.p);
     const int first = t.lvl_off[2];
@@ -597,6 +597,11 @@ void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L) {
         return;
     }
     if (m.Mtc.n < (size_t)t.ncell * 2 * TC_K) throw Error(BEM_ECUDA, "tensor-core staging buffer too small");
+    const bool tk = timed && m.tm.on && m.tm.kev[0];
+    auto kev = [&](int k) {
+        if (tk) BEM_CUDA(cudaEventRecord(m.tm.kev[k], m.stream));
+    };
+    kev(0);
     k_split_m<<<t.ncell - first, 128, 0, m.stream>>>(M, first, t.ncell, nc, cs, m.Mtc.p);
     BEM_CHECK_LAUNCH();
     const size_t sm = tc_smem_bytes();
@@ -605,23 +610,28 @@ void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L) {
     BEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int grid = std::max(1, std::min(t.tc_nsuper, nsm));
     BEM_CUDA(cudaMemsetAsync(m.dev_err.p + 1, 0, sizeof(int), m.stream));  // work-item counter
+    kev(1);
     if (store) {
         ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc<true>), sm);
         k_m2l_tc<true><<<grid, TC_THREADS, sm, m.stream>>>(m.tab->Tc_hi.p, m.tab->Tc_lo.p, t.tc_super.p, t.tc_nsuper,
                                                            m.dev_err.p + 1, t.g_out.p, t.g_in.p, cs, m.Mtc.p,
                                                            m.m2lR.p, m.dev_err.p, m.wait_budget);
         BEM_CHECK_LAUNCH();
+        kev(2);
         const int ncl = t.ncell - first;
         k_m2l_sum<<<cdiv((int64_t)ncl * 32, 256), 256, 0, m.stream>>>(
             reinterpret_cast<const float4 *>(m.m2lR.p), t.m2l_toff.p, t.m2l_tpairs.p, first, t.ncell, cs / 4,
             reinterpret_cast<float4 *>(L));
         BEM_CHECK_LAUNCH();
+        kev(3);
     } else {
         ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc<false>), sm);
         k_m2l_tc<false><<<grid, TC_THREADS, sm, m.stream>>>(m.tab->Tc_hi.p, m.tab->Tc_lo.p, t.tc_super.p, t.tc_nsuper,
                                                             m.dev_err.p + 1, t.g_out.p, t.g_in.p, cs, m.Mtc.p, L,
                                                             m.dev_err.p, m.wait_budget);
         BEM_CHECK_LAUNCH();
+        kev(2);
+        kev(3);
     }
 }
 
