@@ -171,7 +171,7 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
 int bem_mesh_destroy(bem_mesh *mesh);
 
 /* Replace the point charges (same or different count); the panel tree is kept,
- * the charge tree and lists are rebuilt.  charges [n_c][4] f64. */
+ * the charge tree and lists and C^T q are rebuilt.  charges [n_c][4] f64. */
 int bem_set_charges(bem_mesh *mesh, const double *charges, int64_t n_c);
 
 /* y = A x = x + Ehat K' x  (the BEM operator of Eq. ASC), x, y [n_p] f64.
@@ -197,7 +197,10 @@ int bem_bibee(bem_mesh *mesh, int variant, double *sigma_hat, double *dG_kcal);
 
 /* Solvation energy of a surface charge (Sec. 2.1, Eq. reac):
  *   phi = C sigma / eps_in at the charges (phi_reac [n_c], may be NULL),
- *   dG = 1/2 q.phi * 4 pi 332.0637  [kcal/mol]. */
+ *   dG = 1/2 q.phi * 4 pi 332.0637  [kcal/mol].
+ *   Without phi_reac, dG is formed as (C^T q).sigma with C^T q built once per
+ *   charge set (at bem_mesh_create and bem_set_charges) when the charge sums
+ *   are direct: the same quantity, one dot product per call. */
 int bem_energy(bem_mesh *mesh, const double *sigma, double *dG_kcal, double *phi_reac);
 
 /* Gradient of dG (from the last bem_solve, or a fresh one if none) with
