@@ -56,21 +56,28 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.live = threading.Event()
 
     def start(self):
+        """Start sampling every 20 ms; returns once the first sample has
+        arrived (at most ~2 s), so that the timed region that follows is
+        covered from its start."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            self.live.wait(timeout=2.0)
+            self.lines = []  # keep only the samples taken from here on
         except Exception:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.live.set()
 
     def stop(self):
         if self.proc is None:
