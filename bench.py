@@ -370,7 +370,7 @@ def run_ours(args):
     if mk["sum"] > 0:
         rl_sum = {"kernel": "k_m2l_sum (per-target sum of the M2L rows)", "bound": "hbm",
                   "achieved": round(sum_bytes / (mk["sum"] * 1e-3) / 1e9, 1), "peak": round(hbm, 1),
-                  "unit": "GB/s", "traffic": None, "time_ms": round(mk["sum"], 4),
+                  "unit": "GB/s", "traffic": _traffic("k_m2l_sum"), "time_ms": round(mk["sum"], 4),
                   "peak_source": f"HBM copy {hbm:.1f} GB/s (MEASURED_PEAKS.json, {src})",
                   "algorithmic": f"{4 * cs} B x ({info['m2l_pairs']} rows read + {info['cells']} cells written)"}
         rl_sum["frac"] = round(rl_sum["achieved"] / hbm, 4)
