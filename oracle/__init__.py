@@ -140,6 +140,21 @@ def panel_dn(t, n, tri) -> float:
     return float(lib.oracle_panel_dn(_p(_c(t)), _p(_c(n)), _p(_c(tri))))
 
 
+def normal_field(targets, normals, charges):
+    """Normal derivative of the charges' Coulomb potential at arbitrary points
+    (the B q of Sec. 2.1 with the collocation points and normals replaced by
+    any points and unit vectors):
+    E_i = sum_k q_k [-(t_i - x_k).n_i] / (4 pi |t_i - x_k|^3).
+    targets, normals [n, 3]; charges [nc, 4] (x, y, z, q)."""
+    t = _c(targets).reshape(-1, 3)
+    nv = _c(normals).reshape(-1, 3)
+    ch = _c(charges).reshape(-1, 4)
+    xq, q = _c(ch[:, :3]), _c(ch[:, 3])
+    E = np.empty(t.shape[0])
+    _load().oracle_bq(t.shape[0], _p(t), _p(nv), ch.shape[0], _p(xq), _p(q), _p(E))
+    return E
+
+
 class Problem:
     """Dense discrete operators of one molecule (panels + point charges)."""
 
@@ -248,6 +263,25 @@ class Problem:
         E = np.empty(self.n)
         _load().oracle_bq(self.n, _p(self.cen), _p(self.nrm), self.nc, _p(self.xq), _p(q), _p(E))
         return E
+
+    def bq_rows(self, rows, q=None):
+        """Rows of B q (the normal field at the collocation points `rows`)."""
+        q = self.q if q is None else _c(q)
+        rows = np.asarray(rows, dtype=np.int64)
+        cen, nrm = _c(self.cen[rows]), _c(self.nrm[rows])
+        E = np.empty(rows.shape[0])
+        _load().oracle_bq(rows.shape[0], _p(cen), _p(nrm), self.nc, _p(self.xq), _p(q), _p(E))
+        return E
+
+    def c_rows(self, s, ks):
+        """Entries ks of C s (the potential of the surface charge s at the
+        charges ks, Eq. reac)."""
+        s = _c(s)
+        ks = np.asarray(ks, dtype=np.int64)
+        xk = _c(self.xq[ks])
+        phi = np.empty(ks.shape[0])
+        _load().oracle_c(self.n, self.nq, _p(self.qp), _p(self.qw), ks.shape[0], _p(xk), _p(s), _p(phi))
+        return phi
 
     def bt(self, v):
         v = _c(v)

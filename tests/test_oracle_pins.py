@@ -407,3 +407,47 @@ def test_galerkin_born_energy_and_gauss_law():
     gauss = 1.0 - 1.0 / 80.0
     assert abs((sg * P.area).sum() + gauss) < 4e-3
     assert abs((sg * P.area).sum() + gauss) < 0.2 * abs((sc * P.area).sum() + gauss)
+
+
+# ------------------------------------------- sampled rows and arbitrary points
+def test_normal_field_is_the_normal_derivative_of_the_potential():
+    """oracle.normal_field(t, n, charges) = n . grad phi(t) with phi the
+    Coulomb potential sum_k q_k / (4 pi |t - x_k|), checked by a central
+    difference of that potential along n (computed here from its own
+    definition, independent of the field's formula); a wrong sign, a missing
+    4 pi or a swapped (t - x) fails."""
+    rng = np.random.default_rng(11)
+    ch = np.column_stack([rng.uniform(-2, 2, (30, 3)), rng.uniform(-1, 1, 30)])
+    t = rng.uniform(3, 6, (50, 3)) * rng.choice([-1, 1], (50, 3))
+    n = rng.standard_normal((50, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+
+    def phi(pts):
+        d = np.linalg.norm(pts[:, None, :] - ch[None, :, :3], axis=2)
+        return (ch[None, :, 3] / (4 * np.pi * d)).sum(axis=1)
+    h = 1e-5
+    fd = (phi(t + h * n) - phi(t - h * n)) / (2 * h)
+    E = oracle.normal_field(t, n, ch)
+    np.testing.assert_allclose(E, fd, rtol=1e-7, atol=1e-12)
+
+
+def test_normal_field_of_a_central_charge_on_a_sphere():
+    """A charge q at the centre of a sphere of radius R: at every point of the
+    sphere the outward normal derivative of its potential is -q / (4 pi R^2)."""
+    rng = np.random.default_rng(12)
+    n = rng.standard_normal((40, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    R, q = 3.0, -1.7
+    E = oracle.normal_field(R * n, n, np.array([[0.0, 0.0, 0.0, q]]))
+    np.testing.assert_allclose(E, -q / (4 * np.pi * R * R), rtol=1e-14)
+
+
+def test_sampled_rows_match_the_full_products(small3):
+    """bq_rows / c_rows are the full products restricted to a subset."""
+    m, P = small3
+    rows = np.random.default_rng(13).choice(m.n_p, 37, replace=False)
+    np.testing.assert_array_equal(P.bq_rows(rows), P.bq()[rows])
+    s = np.random.default_rng(14).standard_normal(m.n_p)
+    ks = np.random.default_rng(15).choice(m.n_c, 9, replace=False)
+    np.testing.assert_array_equal(P.c_rows(s, ks), P.c(s)[ks])
+    np.testing.assert_array_equal(oracle.normal_field(P.cen, P.nrm, m.charges), P.bq())
