@@ -242,7 +242,8 @@ int bem_autotune(const double *panels, int64_t n_p, const double *charges, int64
  *   field_i = sum_k q_k [-(t_i - x_k).n_i] / (4 pi |t_i - x_k|^3),
  * so -Ehat * field at the panel centroids is the right-hand side of bem_rhs.
  *   targets [n_t][3], normals [n_t][3] (unit), charges [n_c][4] (x, y, z, q),
- *   field [n_t]: all f64 DEVICE arrays (host pointers: BEM_EINVAL).
+ *   field [n_t]: all f64 arrays in device memory of the current device (or
+ *   managed memory); host pointers and another device's memory: BEM_EINVAL.
  *   stream: cudaStream_t the work is queued on (NULL = legacy default); the
  *   call returns without waiting.
  * Its only scratch is one array inside the library, BEM_NOALLOC_SCRATCH_FLOATS
@@ -250,8 +251,8 @@ int bem_autotune(const double *panels, int64_t n_p, const double *charges, int64
  * n_t > BEM_NOALLOC_SCRATCH_FLOATS is rejected with BEM_EINVAL.  All calls on a
  * device share that array and leave their partial sums in it: calls that
  * overlap on the GPU (two streams, two threads) race and must be serialised.
- * The first call on each device looks the array's address up; make that
- * first call before any stream capture. */
+ * The first call on each device looks the array's address (and the device's
+ * SM count) up; make that first call before any stream capture. */
 #define BEM_NOALLOC_SCRATCH_FLOATS (1 << 21)
 int bem_normal_field_noalloc(const double *targets, const double *normals, int64_t n_t,
                              const double *charges, int64_t n_c, double *field, void *stream);

@@ -305,6 +305,13 @@ def bem_normal_field_noalloc(targets, normals, charges, field, stream=None):
     Queued on `stream` (a raw cudaStream_t, None = legacy default)."""
     n_t = int(targets.shape[0])
     n_c = int(charges.shape[0])
+    for a, name in ((targets, "targets"), (normals, "normals"), (charges, "charges"), (field, "field")):
+        if not getattr(a, "is_cuda", False):
+            raise TypeError(f"{name} must be a CUDA tensor (this entry point takes device memory only)")
+    _check_f64(targets, 3 * n_t, "targets")
+    _check_f64(normals, 3 * n_t, "normals")
+    _check_f64(charges, 4 * n_c, "charges")
+    _check_f64(field, n_t, "field")
     st = ctypes.c_void_p(stream) if stream is not None else None
     return _check(load_library().bem_normal_field_noalloc(_ptr(targets), _ptr(normals), n_t,
                                                           _ptr(charges), n_c, _ptr(field), st),

@@ -20,8 +20,10 @@
 //    but calls that overlap on the GPU (different streams, or different host
 //    threads) race on it and must be serialised by the caller;
 //  * the first call on each device looks up the array's device address
-//    (cudaGetSymbolAddress) and keeps it; make that first call outside any
-//    stream capture.
+//    (cudaGetSymbolAddress) and the device's SM count and keeps them; make
+//    that first call outside any stream capture.
+//  * every array must be device memory of the current device (or managed
+//    memory); memory of another device is rejected.
 #include <cmath>
 #include <mutex>
 
@@ -37,35 +39,44 @@ static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_FLOATS];
 
 static std::mutex g_noalloc_mu;
 static float *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+static int g_noalloc_sms[NOALLOC_MAX_DEVICES] = {};
 
-// The device address of the scratch array on the current device (looked up once per device).
-static float *noalloc_scratch() {
-    int dev = 0;
-    BEM_CUDA(cudaGetDevice(&dev));
+// Set-up of the current device, once: the device address of the scratch
+// array (host code cannot use the array's name as an address) and the SM
+// count that sizes the source splits.
+static float *noalloc_scratch(int dev, int *sms) {
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) throw Error(BEM_EUNSUPPORTED, "device index out of range");
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
         void *p = nullptr;
         BEM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        int n = 0;
+        BEM_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        g_noalloc_sms[dev] = n > 0 ? n : 1;
         g_noalloc_ptr[dev] = static_cast<float *>(p);
     }
+    *sms = g_noalloc_sms[dev];
     return g_noalloc_ptr[dev];
 }
 
-// field_i = sum_k q_k [-(t_i - x_k).n_i] / (4 pi |t_i - x_k|^3): FP32 pairs
-// (FP64 inputs rounded when staged), per-split partial sums in the scratch
-// array, FP64 reduction of the splits.
+// field_i = sum_k q_k [-(t_i - x_k).n_i] / (4 pi |t_i - x_k|^3): FP32 pairs,
+// per-split partial sums in the scratch array, FP64 reduction of the splits.
+// Coordinates enter the FP32 arithmetic relative to the first target of the
+// CTA (the shift is taken in FP64), so that the differences of nearby points
+// keep their precision however far the system lies from the origin.
 __global__ void __launch_bounds__(NOALLOC_THREADS)
 k_nf_partial(const double *tpos, const double *tnrm, int64_t nt, const double *ch, int64_t nc,
              int64_t chunk, float *part) {
     __shared__ float4 sh[NOALLOC_THREADS];
-    const int64_t i = blockIdx.x * (int64_t)NOALLOC_THREADS + threadIdx.x;
+    const int64_t i0 = blockIdx.x * (int64_t)NOALLOC_THREADS;
+    const int64_t i = i0 + threadIdx.x;
     const int64_t s0 = (int64_t)blockIdx.y * chunk, s1 = min(nc, s0 + chunk);
+    const double ox = tpos[3 * i0], oy = tpos[3 * i0 + 1], oz = tpos[3 * i0 + 2];
     float x = 0, y = 0, z = 0, nx = 0, ny = 0, nz = 0;
     if (i < nt) {
-        x = (float)tpos[3 * i];
-        y = (float)tpos[3 * i + 1];
-        z = (float)tpos[3 * i + 2];
+        x = (float)(tpos[3 * i] - ox);
+        y = (float)(tpos[3 * i + 1] - oy);
+        z = (float)(tpos[3 * i + 2] - oz);
         nx = (float)tnrm[3 * i];
         ny = (float)tnrm[3 * i + 1];
         nz = (float)tnrm[3 * i + 2];
@@ -76,7 +87,7 @@ k_nf_partial(const double *tpos, const double *tnrm, int64_t nt, const double *c
         const int64_t k = b + threadIdx.x;
         float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k < s1)
-            r = make_float4((float)ch[4 * k], (float)ch[4 * k + 1], (float)ch[4 * k + 2],
+            r = make_float4((float)(ch[4 * k] - ox), (float)(ch[4 * k + 1] - oy), (float)(ch[4 * k + 2] - oz),
                             (float)ch[4 * k + 3]);
         sh[threadIdx.x] = r;
         __syncthreads();
@@ -104,13 +115,15 @@ __global__ void k_nf_reduce(const float *part, int nsplit, int64_t nt, double *f
     field[i] = s / FOUR_PI;
 }
 
-static bool on_device(const void *p) {
+// Device memory of device `dev`, or managed memory.
+static bool on_device(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace bem
@@ -129,15 +142,22 @@ extern "C" int bem_normal_field_noalloc(const double *targets, const double *nor
                                         " targets (use bem_mesh_create + bem_rhs instead)");
         if (!targets || !normals || !field || (n_c > 0 && !charges))
             throw Error(BEM_EINVAL, "bem_normal_field_noalloc: NULL array");
-        if (!on_device(targets) || !on_device(normals) || !on_device(field) ||
-            (n_c > 0 && !on_device(charges)))
-            throw Error(BEM_EINVAL, "bem_normal_field_noalloc: every array must be device memory");
+        int dev = 0;
+        BEM_CUDA(cudaGetDevice(&dev));
+        const struct { const void *p; const char *name; } args[] = {
+            {targets, "targets"}, {normals, "normals"}, {field, "field"}, {n_c > 0 ? charges : targets, "charges"}};
+        for (const auto &a : args)
+            if (!on_device(a.p, dev))
+                throw Error(BEM_EINVAL, std::string("bem_normal_field_noalloc: ") + a.name +
+                                            " must be device memory of the current device");
         cudaStream_t s = (cudaStream_t)stream;
-        float *part = noalloc_scratch();
+        int sms = 1;
+        float *part = noalloc_scratch(dev, &sms);
         const int tblocks = cdiv(n_t, NOALLOC_THREADS);
         int64_t nsplit = 1;
         if (n_c > 0) {
-            nsplit = std::max<int64_t>(1, std::min<int64_t>(cdiv(n_c, 4096), std::max(1, 1216 / tblocks)));
+            // about 8 CTAs per SM, splits of at least 4096 charges
+            nsplit = std::max<int64_t>(1, std::min<int64_t>(cdiv(n_c, 4096), std::max(1, 8 * sms / tblocks)));
             nsplit = std::min<int64_t>(nsplit, NOALLOC_FLOATS / n_t);
             nsplit = std::min<int64_t>(nsplit, 65535);
         }
