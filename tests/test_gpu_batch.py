@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import rel
+from gpu_util import close, rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -67,8 +67,8 @@ def test_graph_replay_matches_direct_launches(pkg):
             ys.append(y.cpu().numpy())
             s, st = g.solve()
             ys.append(s.cpu().numpy())
-    assert rel(ys[2], ys[0]) < 1e-7
-    assert rel(ys[3], ys[1]) < 1e-7
+    close(ys[2], ys[0], 1e-7, inf=1e-6)
+    close(ys[3], ys[1], 1e-7, inf=1e-6)
 
 
 def test_caller_stream_ordering(pkg):
@@ -83,7 +83,7 @@ def test_caller_stream_ordering(pkg):
         y = g.matvec(x)
     torch.cuda.synchronize()
     P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
-    assert rel(y.cpu().numpy(), P.A(np.ones(m.n_p))) < 1e-5
+    close(y.cpu().numpy(), P.A(np.ones(m.n_p)), 1e-5)
     g.close()
 
 
@@ -95,7 +95,7 @@ def test_autotune_meets_its_target(pkg):
     x = P.bq()
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=opt.p, leaf_size=opt.leaf_size) as g:
         y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
-    assert rel(y, P.A(x)) < 3e-5
+    close(y, P.A(x), 3e-5)
 
 
 def test_autotune_choice_is_cached(pkg, tmp_path):
@@ -120,4 +120,4 @@ def test_solve_resumes_from_a_saved_iterate(pkg):
         s_res, st_res = g.solve(x0=s_cut)
     assert st_res["converged"] == 1
     assert st_res["iterations"] < st_ref["iterations"], (st_res["iterations"], st_ref["iterations"])
-    assert rel(s_res.cpu().numpy(), s_ref.cpu().numpy()) < 1e-6
+    close(s_res.cpu().numpy(), s_ref.cpu().numpy(), 1e-6, inf=1e-5)

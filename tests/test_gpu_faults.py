@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import rel
+from gpu_util import close, rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -33,7 +33,7 @@ def test_wait_budget_timeout_is_reported_and_the_mesh_recovers(pkg):
         assert ei.value.code == pkg.BEM_ETIMEOUT
         pkg.bem_set_wait_budget(g.h, 0)             # back to the default
         y1 = g.matvec(x).cpu().numpy()
-        assert rel(y1, y0) < 1e-6
+        close(y1, y0, 1e-6, inf=1e-5)
     with pytest.raises(pkg.BemError):
         pkg.bem_set_wait_budget(None, 5)
 

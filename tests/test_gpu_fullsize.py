@@ -6,6 +6,8 @@ oracle computes one by one, or by properties that hold at any size.
 * globular-s7 (327,680 panels): sampled rows of the product, and the energy
   gradients of one autograd call against the FP64 GPU form and central
   differences in q and x on 20 seeded charges;
+* globular-s5 (20,480 panels, the same 2,000 charges): the gradients of one
+  autograd call against the oracle's dense adjoint;
 * batch64 (64 uneven molecules, 9.5M panels): batched solve against
   one-at-a-time solves and the BIBEE bounds around every solve;
 * lattice10 (1,000 rotated copies of globular-s6, 81.9M panels): sampled
@@ -16,7 +18,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import rel
+from gpu_util import close, rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -36,9 +38,7 @@ def _rows_check(pkg, m, x, rows, tol, **opts):
     ref = x[rows] + P.ehat * P.kprime_rows(x, rows)
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, **opts) as g:
         y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
-    err = rel(y[rows], ref)
-    assert err < tol, err
-    return err
+    return close(y[rows], ref, tol)
 
 
 def test_globular_s6_bench_configuration_rows(pkg):
@@ -51,7 +51,7 @@ def test_globular_s6_bench_configuration_rows(pkg):
         with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=10, leaf_size=64, precision=0) as g:
             y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
             assert g.info()["depth"] == 5
-        assert rel(y[rows], ref) < 1e-5, rel(y[rows], ref)
+        close(y[rows], ref, 1e-5)
 
 
 def test_globular_s7_rows(pkg):
@@ -62,7 +62,7 @@ def test_globular_s7_rows(pkg):
     ref = x[rows] + P.ehat * P.kprime_rows(x, rows)
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=10, leaf_size=64, precision=0) as g:
         y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
-    assert rel(y[rows], ref) < 1e-5, rel(y[rows], ref)
+    close(y[rows], ref, 1e-5)
 
 
 def test_globular_s7_gradients(pkg):
@@ -91,8 +91,8 @@ def test_globular_s7_gradients(pkg):
         dq, dx = g.energy_backward(1.0)
         dq, dx = dq.cpu().numpy(), dx.cpu().numpy()
         assert abs(dg_mixed - e0) < 1e-5 * abs(e0), (dg_mixed, e0)
-        assert rel(gq_mixed, dq) < 1e-5, rel(gq_mixed, dq)
-        assert rel(gx_mixed, dx) < 1e-4, rel(gx_mixed, dx)
+        close(gq_mixed, dq, 1e-5)
+        close(gx_mixed, dx, 1e-5)
         rng = np.random.default_rng(3)
         for k in rng.choice(m.n_c, 20, replace=False):
             cp, cm = m.charges.copy(), m.charges.copy()
@@ -106,6 +106,23 @@ def test_globular_s7_gradients(pkg):
             cm[k, a] -= 1e-4
             fd = (energy(cp) - energy(cm)) / 2e-4
             assert abs(fd - dx[k, a]) < 1e-4 * max(1.0, np.abs(dx).max()), (k, a, fd, dx[k, a])
+
+
+def test_globular_s5_gradients_match_dense_adjoint(pkg):
+    """d dG/dq and d dG/dx of the 2,000 charges at 20,480 panels (mixed
+    precision, the bench's p = 10 and leaf 64) against the oracle's dense
+    adjoint (solve A^T lam = C^T q, then the gradient formulas)."""
+    m = synth.globular(5)
+    P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+    dg_ref, dq_ref, dx_ref, _, _ = P.gradients(tol=1e-11)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=10, leaf_size=64, precision=0,
+                  tol=1e-10) as g:
+        ch = torch.tensor(m.charges, dtype=torch.float64, device="cuda", requires_grad=True)
+        dg = pkg.solvation_energy(g, ch)
+        dg.backward()
+    assert abs(float(dg.detach()) - dg_ref) < 1e-5 * abs(dg_ref)
+    close(ch.grad[:, 3].cpu().numpy(), dq_ref, 1e-5)
+    close(ch.grad[:, :3].cpu().numpy(), dx_ref, 1e-5)
 
 
 def test_batch64_solve_and_bounds(pkg):

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import rel
+from gpu_util import close, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -47,9 +47,9 @@ def test_near_field_only_matches_dense(pkg, born3, precision, tol):
     x = _x(m.n_p)
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=-1, precision=precision) as g:
         y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
-    assert rel(y, P.A(x)) < tol
+    close(y, P.A(x), tol)
     kx_ref = P.kprime(x)
-    assert rel((y - x) / P.ehat, kx_ref) < 50 * tol
+    close((y - x) / P.ehat, kx_ref, 50 * tol)
 
 
 @pytest.mark.parametrize("depth,p", [(2, 10), (3, 10), (3, 12), (4, 12), (4, 16)])
@@ -61,7 +61,7 @@ def test_fmm_matvec_matches_dense(pkg, small4, depth, p, m2l_mode):
         with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=depth, p=p,
                       m2l_mode=m2l_mode) as g:
             y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
-        assert rel(y, ref) < 1e-5, (depth, p, m2l_mode, rel(y, ref))
+        close(y, ref, 1e-5)
 
 
 def test_tensor_core_m2l_matches_simt(pkg, small4):
@@ -72,7 +72,7 @@ def test_tensor_core_m2l_matches_simt(pkg, small4):
     for mode in (1, 3):
         with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=4, p=10, m2l_mode=mode) as g:
             ys.append(g.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
-    assert rel(ys[1] - x, ys[0] - x) < 2e-6
+    close(ys[1] - x, ys[0] - x, 2e-6, inf=2e-5)
 
 
 def test_tensor_core_m2l_epilogues_agree(pkg, small4):
@@ -88,8 +88,8 @@ def test_tensor_core_m2l_epilogues_agree(pkg, small4):
         with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=4, p=10, m2l_mode=3,
                       flags=flags) as g:
             ys.append(g.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
-        assert rel(ys[-1], ref) < 1e-5, (flags, rel(ys[-1], ref))
-    assert rel(ys[1] - x, ys[0] - x) < 1e-6
+        close(ys[-1], ref, 1e-5)
+    close(ys[1] - x, ys[0] - x, 1e-6, inf=1e-5)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -104,7 +104,8 @@ def test_translation_modes_agree(pkg, small4, precision):
                       m2l_mode=mode, precision=precision) as g:
             ys.append(g.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
     kx = (ys[1] - x)
-    assert rel(ys[0] - x, kx) < (2e-6 if precision == 0 else 1e-12)
+    tol = 2e-6 if precision == 0 else 1e-12
+    close(ys[0] - x, kx, tol, inf=10 * tol)
 
 
 @pytest.mark.parametrize("depth", [2, 3])
@@ -113,7 +114,7 @@ def test_fmm_matvec_fp64_mode(pkg, small4, depth):
     x = P.bq()
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=depth, p=12, precision=1) as g:
         y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
-    assert rel(y, P.A(x)) < 1e-6
+    close(y, P.A(x), 1e-6, inf=1e-5)  # p = 12 truncation: 3.5e-6 of the largest row
 
 
 def test_ragged_open_surface(pkg):
@@ -124,14 +125,14 @@ def test_ragged_open_surface(pkg):
     x = _x(3001, 4)
     with pkg.Mesh(pan, m.charges, m.eps_in, m.eps_out, depth=3, p=12) as g:
         y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
-    assert rel(y, P.A(x)) < 1e-5
+    close(y, P.A(x), 1e-5)
 
 
 def test_rhs_matches_oracle(pkg, small4):
     m, P = small4
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=3, p=12) as g:
         b = g.rhs().cpu().numpy()
-    assert rel(b, P.rhs()) < 1e-5
+    close(b, P.rhs(), 1e-5)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -148,7 +149,7 @@ def test_energy_of_given_sigma(pkg, small4, precision):
     assert abs(dg - dg_ref) / abs(dg_ref) < 1e-5
     assert abs(dg_ctq - dg_ref) / abs(dg_ref) < 1e-5
     assert abs(dg_ctq - dg) / abs(dg_ref) < (1e-6 if precision == 0 else 1e-12), (dg_ctq, dg)
-    assert rel(phi.cpu().numpy(), phi_ref / m.eps_in) < 1e-5
+    close(phi.cpu().numpy(), phi_ref / m.eps_in, 1e-5)
 
 
 def test_solve_and_energy_match_oracle(pkg, small4):
@@ -159,7 +160,7 @@ def test_solve_and_energy_match_oracle(pkg, small4):
         sig, st = g.solve()
         dg = g.energy(sig)
     assert st["converged"] == 1
-    assert rel(sig.cpu().numpy(), sig_ref) < 1e-5
+    close(sig.cpu().numpy(), sig_ref, 1e-5)
     assert abs(dg - dg_ref) / abs(dg_ref) < 1e-5
 
 
@@ -179,7 +180,7 @@ def test_bibee_matches_oracle(pkg, small4, variant, name):
     sh_ref, dg_ref = P.bibee(name)
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=3, p=12) as g:
         dg, sh = g.bibee(variant, want_sigma=True)
-    assert rel(sh.cpu().numpy(), sh_ref) < 1e-5
+    close(sh.cpu().numpy(), sh_ref, 1e-5)
     assert abs(dg - dg_ref) / abs(dg_ref) < 1e-5
 
 
@@ -194,7 +195,7 @@ def test_host_and_device_arguments_agree(pkg, small4):
         yd = torch.empty_like(xd)
         pkg.bem_matvec(h, xd, yd)
         # atomically accumulated translations: equal up to summation order
-        assert rel(y_host, yd.cpu().numpy()) < 1e-7
+        close(y_host, yd.cpu().numpy(), 1e-7, inf=1e-6)
     finally:
         pkg.bem_mesh_destroy(h)
 
@@ -228,7 +229,7 @@ def test_full_size_sampled_rows(pkg):
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=12) as g:
         y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
         info = g.info()
-    assert rel(y[rows], ref) < 1e-5, (rel(y[rows], ref), info["depth"])
+    close(y[rows], ref, 1e-5)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -246,8 +247,7 @@ def test_exact_near_singular_integrals_match_oracle(pkg, precision):
                   near_table=pkg.BEM_NEAR_EXACT) as g:
         y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
         assert g.info()["near_table_nnz"] > 0
-    err = rel(y[rows], ref)
-    assert err < 1e-5, err
+    err, _ = close(y[rows], ref, 1e-5)
     # the two operators really differ (4.5e-5 here), and the product follows
     # the exact one
     assert rel(quad, ref) > max(2e-5, 3 * err), (rel(quad, ref), err)
@@ -262,4 +262,4 @@ def test_exact_near_singular_integrals_full_size(pkg):
     with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=10, leaf_size=64,
                   near_table=pkg.BEM_NEAR_EXACT) as g:
         y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
-    assert rel(y[rows], ref) < 1e-5, rel(y[rows], ref)
+    close(y[rows], ref, 1e-5)
