@@ -131,6 +131,7 @@ size_t Mesh::bytes() const {
     b += nt_off.bytes() + nt_col.bytes() + nt_val.bytes() + ntT_off.bytes() + ntT_col.bytes() +
          ntT_val.bytes() + qp_of_panel.bytes();
     if (tab) b += tab->bytes();
+    if (tab2) b += tab2->bytes();
     b += Mf.bytes() + Lf.bytes() + Md.bytes() + Ld.bytes();
     b += Mtc.bytes() + m2lR.bytes() + ctq.bytes() + str32.bytes() + str64.bytes() + dpart_f.bytes() + dpart_d.bytes();
     b += xs.bytes() + ys.bytes() + zs.bytes() + far_f.bytes() + near_f.bytes() + far_d.bytes() +
@@ -339,6 +340,7 @@ int bem_set_charges(bem_mesh *m, const double *charges, int64_t n_c) {
             m->g_mv = nullptr;
         }
         rebuild_charge_tree(*m, dc);
+        build_tables(*m);  // the charge tree's separation may have changed
         build_translation_groups(*m, m->tc);
         alloc_work(*m);
         build_ctq(*m);

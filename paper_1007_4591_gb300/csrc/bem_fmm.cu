@@ -399,19 +399,22 @@ template <class T> struct P2PFpt;
 template <> struct P2PFpt<float> { static constexpr int v = 8; };
 template <> struct P2PFpt<double> { static constexpr int v = 2; };
 
-template <class T, int SRC, int TGT, int P2PF_THREADS>
+// NB: the most neighbour leaves a leaf has (27 for one-cell separation, 125
+// for the charge tree's two cells).
+template <class T, int SRC, int TGT, int P2PF_THREADS, int NB = 27>
 __global__ void __launch_bounds__(P2PF_THREADS)
 k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
       const typename V4T<T>::t *src, T h, T *out) {
     using V4 = typename V4T<T>::t;
     using P = Pk<T>;
     using v2 = typename P::v;
+    static_assert(NB <= P2PF_THREADS, "one thread per neighbour leaf in the set-up");
     constexpr int P2P_TPT = P2PTpt<T>::v;
     constexpr int P2PF_TILE = P2PF_THREADS * P2PFpt<T>::v;  // sources per tile
     constexpr int P2PF_PAIRS = P2PF_TILE / 2;
     __shared__ V4 shA[P2PF_PAIRS], shB[P2PF_PAIRS];
-    __shared__ int s_beg[28], s_cum[28];
-    __shared__ T s_off[27][3];
+    __shared__ int s_beg[NB + 1], s_cum[NB + 1];
+    __shared__ T s_off[NB][3];
     __shared__ T s_part[P2PF_THREADS * 4];
     const int leaf = tv.p2p_order[blockIdx.x];  // heaviest leaves first
     constexpr bool DN = TGT == TGT_CEN_DN || TGT == TGT_QUAD_DN;  // normal field, else potential
@@ -1040,9 +1043,12 @@ void ensure_smem_attr(const void *func, size_t bytes) {
 }
 
 struct TabKey {
-    int dev, p, prec;
+    int dev, p, prec, ws;
     bool operator<(const TabKey &o) const {
-        return dev != o.dev ? dev < o.dev : (p != o.p ? p < o.p : prec < o.prec);
+        if (dev != o.dev) return dev < o.dev;
+        if (p != o.p) return p < o.p;
+        if (prec != o.prec) return prec < o.prec;
+        return ws < o.ws;
     }
 };
 static std::mutex g_tab_mu;
@@ -1055,11 +1061,13 @@ static void upload(DArray<T> &d, const std::vector<double> &h) {
     BEM_CUDA(cudaMemcpy(d.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
 }
 
-static std::shared_ptr<Tables> make_tables(int p, int prec) {
+static std::shared_ptr<Tables> make_tables(int p, int prec, int ws) {
     auto t = std::make_shared<Tables>();
     const int W = 2 * p + 1, W2 = 4 * p + 1;
     const int nc = (p + 1) * (p + 1);
+    const int NOFFSET = m2l_classes(ws), RO = m2l_radius(ws), WO = 2 * RO + 1;
     t->p = p;
+    t->ws = ws;
     // parent/child offsets: child centre minus parent centre over the parent size
     std::vector<std::vector<double>> r8(8);
     std::vector<double> rtab((size_t)8 * (p + 1) * W * 2);
@@ -1072,9 +1080,15 @@ static std::shared_ptr<Tables> make_tables(int p, int prec) {
     // M2L offsets: target centre minus source centre over the cell size = -(dx,dy,dz)
     const size_t itot = (size_t)(2 * p + 1) * W2 * 2;
     std::vector<double> it((size_t)NOFFSET * itot, 0.0), tmp;
+    auto offset_of = [&](int o, int &dx, int &dy, int &dz) {
+        dx = o / (WO * WO) - RO;
+        dy = (o / WO) % WO - RO;
+        dz = o % WO - RO;
+        return std::abs(dx) > ws || std::abs(dy) > ws || std::abs(dz) > ws;  // a class in use
+    };
     for (int o = 0; o < NOFFSET; ++o) {
-        int dx = o / 49 - 3, dy = (o / 7) % 7 - 3, dz = o % 7 - 3;
-        if (std::abs(dx) <= 1 && std::abs(dy) <= 1 && std::abs(dz) <= 1) continue;
+        int dx, dy, dz;
+        if (!offset_of(o, dx, dy, dz)) continue;
         host_irregular_full(-dx, -dy, -dz, 2 * p, tmp);
         std::memcpy(&it[(size_t)o * itot], tmp.data(), tmp.size() * sizeof(double));
     }
@@ -1082,8 +1096,8 @@ static std::shared_ptr<Tables> make_tables(int p, int prec) {
     const size_t osz = (size_t)nc * nc;
     std::vector<double> om2l((size_t)NOFFSET * osz, 0.0), om2m(8 * osz), ol2l(8 * osz);
     for (int o = 0; o < NOFFSET; ++o) {
-        int dx = o / 49 - 3, dy = (o / 7) % 7 - 3, dz = o % 7 - 3;
-        if (std::abs(dx) <= 1 && std::abs(dy) <= 1 && std::abs(dz) <= 1) continue;
+        int dx, dy, dz;
+        if (!offset_of(o, dx, dy, dz)) continue;
         const double *I = &it[(size_t)o * itot];
         // L_k^l = (-1)^k sum M_n^m I_{n+k}^{m+l}
         real_operator(p, [&](int k, int l, int n, int m, double &re, double &im) {
@@ -1153,19 +1167,30 @@ static std::shared_ptr<Tables> make_tables(int p, int prec) {
     return t;
 }
 
+static std::shared_ptr<Tables> cached_tables(int dev, int p, int prec, int ws) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    TabKey key{dev, p, prec, ws};
+    auto it = g_tab_cache.find(key);
+    if (it != g_tab_cache.end())
+        if (auto sp = it->second.lock()) return sp;
+    auto t = make_tables(p, prec, ws);
+    g_tab_cache[key] = t;
+    return t;
+}
+
+// The panel tree's tables (one-cell separation) and, when the charge tree is
+// separated by two cells, its own set.
 void build_tables(Mesh &m) {
     upload_constants(m.device);
-    std::lock_guard<std::mutex> lk(g_tab_mu);
-    TabKey key{m.device, m.opt.p, m.opt.precision};
-    auto it = g_tab_cache.find(key);
-    if (it != g_tab_cache.end()) {
-        if (auto sp = it->second.lock()) {
-            m.tab = sp;
-            return;
-        }
-    }
-    m.tab = make_tables(m.opt.p, m.opt.precision);
-    g_tab_cache[key] = m.tab;
+    m.tab = cached_tables(m.device, m.opt.p, m.opt.precision, 1);
+    if (m.tc.ws == 2) m.tab2 = cached_tables(m.device, m.opt.p, m.opt.precision, 2);
+    else m.tab2.reset();
+}
+
+const Tables &tables_for(const Mesh &m, const Tree &t) {
+    const Tables *tb = t.ws == 2 ? m.tab2.get() : m.tab.get();
+    if (!tb || tb->ws != t.ws) throw Error(BEM_ECUDA, "translation tables missing for the tree's separation");
+    return *tb;
 }
 
 // ------------------------------------------------- batched dense translations
@@ -1424,6 +1449,32 @@ static size_t translate_smem() {
     return std::max(a, c);
 }
 
+__global__ void k_iota(int *a, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) a[i] = (int)i;
+}
+
+__global__ void k_class_count(const int *key, int64_t n, int *cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(cnt + key[i], 1);
+}
+
+// grouped pair d is list entry e = perm[d]
+__global__ void k_gather_pairs(const int *perm, const int *po, const int *pi, int64_t n, int *g_out, int *g_in,
+                               int *rank) {
+    const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (d >= n) return;
+    const int e = perm[d];
+    g_out[d] = po[e];
+    g_in[d] = pi[e];
+    rank[e] = (int)d;
+}
+
+__global__ void k_shift_offsets(const int *off, int n, int *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = off[i] - off[0];
+}
+
 // Group the translations of a tree by operator and cut them into chunks.
 __global__ void k_m2l_pairs(const int *m2l_off, int first, int last, const int *m2l_src,
                             const int *m2l_ofs, int *out, int *in, int *key) {
@@ -1483,58 +1534,65 @@ void build_translation_groups(Mesh &m, Tree &t) {
     std::vector<int> parent(t.ncell);
     BEM_CUDA(cudaMemcpyAsync(ijk.data(), t.ijk.p, t.ncell * sizeof(int4), cudaMemcpyDeviceToHost, s));
     BEM_CUDA(cudaMemcpyAsync(parent.data(), t.parent.p, t.ncell * sizeof(int), cudaMemcpyDeviceToHost, s));
-    // M2L pairs sorted by offset class (device radix sort, stable)
+    // M2L pairs grouped by offset class on the device: a stable radix sort of
+    // the pair indices (target-major list order) by class, the pairs gathered
+    // into that order, and only the per-class counts copied to the host to cut
+    // the classes into chunks
     const int64_t nm = t.nm2l;
-    std::vector<int> h_out, h_in;
+    const int ncls = m2l_classes(t.ws);
+    int cls_bits = 0;
+    while ((1 << cls_bits) < ncls) ++cls_bits;
     std::vector<int4> chunks;
-    std::vector<int> cnt(NOFFSET, 0);
-    {
-        DArray<int> po, pi, key;
+    std::vector<int> cnt(ncls, 0);
+    DArray<int> rank;  // rank[e] = position of list entry e in the grouped order
+    const int first = t.lvl_off[2], last = t.ncell;
+    if (nm > 0) {
+        DArray<int> po, pi, key, idx, key_s, perm, dcnt;
         po.alloc(nm);
         pi.alloc(nm);
         key.alloc(nm);
-        const int first = t.lvl_off[2], last = t.ncell;
+        idx.alloc(nm);
+        key_s.alloc(nm);
+        perm.alloc(nm);
+        dcnt.alloc(ncls);
+        rank.alloc(nm);
         k_m2l_pairs<<<cdiv(last - first, 256), 256, 0, s>>>(t.m2l_off.p, first, last, t.m2l_src.p,
                                                           t.m2l_ofs.p, po.p, pi.p, key.p);
         BEM_CHECK_LAUNCH();
-        std::vector<int> hk(nm), ho(nm), hi(nm);
-        BEM_CUDA(cudaMemcpyAsync(hk.data(), key.p, nm * sizeof(int), cudaMemcpyDeviceToHost, s));
-        BEM_CUDA(cudaMemcpyAsync(ho.data(), po.p, nm * sizeof(int), cudaMemcpyDeviceToHost, s));
-        BEM_CUDA(cudaMemcpyAsync(hi.data(), pi.p, nm * sizeof(int), cudaMemcpyDeviceToHost, s));
+        k_iota<<<cdiv(nm, 256), 256, 0, s>>>(idx.p, nm);
+        BEM_CHECK_LAUNCH();
+        sort_pairs_int(key.p, idx.p, key_s.p, perm.p, nm, cls_bits, s);
+        BEM_CUDA(cudaMemsetAsync(dcnt.p, 0, ncls * sizeof(int), s));
+        k_class_count<<<cdiv(nm, 256), 256, 0, s>>>(key.p, nm, dcnt.p);
+        BEM_CHECK_LAUNCH();
+        BEM_CUDA(cudaMemcpyAsync(cnt.data(), dcnt.p, ncls * sizeof(int), cudaMemcpyDeviceToHost, s));
+        // the M2L part of the grouped arrays (the tree translations are appended below)
+        t.g_out.alloc(nm);
+        t.g_in.alloc(nm);
+        k_gather_pairs<<<cdiv(nm, 256), 256, 0, s>>>(perm.p, po.p, pi.p, nm, t.g_out.p, t.g_in.p, rank.p);
+        BEM_CHECK_LAUNCH();
         BEM_CUDA(cudaStreamSynchronize(s));
-        for (int64_t e = 0; e < nm; ++e) cnt[hk[e]]++;
-        std::vector<int64_t> start(NOFFSET + 1, 0);
-        for (int o = 0; o < NOFFSET; ++o) start[o + 1] = start[o] + cnt[o];
-        h_out.resize(nm);
-        h_in.resize(nm);
-        std::vector<int64_t> fill(start.begin(), start.end() - 1);
-        for (int64_t e = 0; e < nm; ++e) {
-            const int64_t d = fill[hk[e]]++;
-            h_out[d] = ho[e];
-            h_in[d] = hi[e];
-        }
-        for (int o = 0; o < NOFFSET; ++o)
+        std::vector<int64_t> start(ncls + 1, 0);
+        for (int o = 0; o < ncls; ++o) start[o + 1] = start[o] + cnt[o];
+        for (int o = 0; o < ncls; ++o)
             for (int64_t b = start[o]; b < start[o + 1]; b += TR_BN_M2L)
                 chunks.push_back(make_int4(o, (int)b, (int)std::min<int64_t>(TR_BN_M2L, start[o + 1] - b), 0));
-        t.m2l_nchunk = (int)chunks.size();
-        build_tc_super(t, chunks, s);
-        // pairs by target cell for the store-then-sum tensor-core M2L
-        t.m2l_store = use_tc_m2l(m) && m2l_store_fits(nm, m.opt.p) && !(m.opt.flags & BEM_FLAG_M2L_REDUCE);
-        if (t.m2l_store) {
-            const int ncl = last - first;
-            std::vector<int> toff(ncl + 1, 0), tp(nm);
-            for (int64_t e = 0; e < nm; ++e) toff[h_out[e] - first + 1]++;
-            for (int c = 0; c < ncl; ++c) toff[c + 1] += toff[c];
-            std::vector<int> fill2(toff.begin(), toff.end() - 1);
-            for (int64_t e = 0; e < nm; ++e) tp[fill2[h_out[e] - first]++] = (int)e;
-            t.m2l_toff.alloc(ncl + 1);
-            t.m2l_tpairs.alloc(nm);
-            BEM_CUDA(cudaMemcpyAsync(t.m2l_toff.p, toff.data(), (ncl + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-            BEM_CUDA(cudaMemcpyAsync(t.m2l_tpairs.p, tp.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
-            BEM_CUDA(cudaStreamSynchronize(s));
-        }
+    }
+    t.m2l_nchunk = (int)chunks.size();
+    build_tc_super(t, chunks, s);
+    // pairs by target cell for the store-then-sum tensor-core M2L: the list
+    // is target-major, so the CSR is the list's own offsets and each entry
+    // the pair's grouped position
+    t.m2l_store = use_tc_m2l(m) && m2l_store_fits(nm, m.opt.p) && !(m.opt.flags & BEM_FLAG_M2L_REDUCE);
+    if (t.m2l_store) {
+        const int ncl = last - first;
+        t.m2l_toff.alloc(ncl + 1);
+        k_shift_offsets<<<cdiv(ncl + 1, 256), 256, 0, s>>>(t.m2l_off.p + first, ncl + 1, t.m2l_toff.p);
+        BEM_CHECK_LAUNCH();
+        t.m2l_tpairs = std::move(rank);
     }
     // M2M (out parent, in child) and L2L (out child, in parent) per child level
+    std::vector<int> h_out, h_in;
     for (int c = 3; c <= L; ++c) {
         std::vector<std::vector<int>> byoct(8);
         for (int e = t.lvl_off[c]; e < t.lvl_off[c + 1]; ++e) {
@@ -1544,12 +1602,12 @@ void build_translation_groups(Mesh &m, Tree &t) {
         for (int pass = 0; pass < 2; ++pass) {
             const int c0 = (int)chunks.size();
             for (int o = 0; o < 8; ++o) {
-                const int64_t b0 = (int64_t)h_out.size();
+                const int64_t b0 = nm + (int64_t)h_out.size();
                 for (int e : byoct[o]) {
                     if (pass == 0) { h_out.push_back(parent[e]); h_in.push_back(e); }
                     else { h_out.push_back(e); h_in.push_back(parent[e]); }
                 }
-                const int64_t b1 = (int64_t)h_out.size();
+                const int64_t b1 = nm + (int64_t)h_out.size();
                 for (int64_t b = b0; b < b1; b += TR_BN_TREE)
                     chunks.push_back(make_int4(o, (int)b, (int)std::min<int64_t>(TR_BN_TREE, b1 - b), 0));
             }
@@ -1557,11 +1615,24 @@ void build_translation_groups(Mesh &m, Tree &t) {
             else { t.l2l_chunk0[c] = c0; t.l2l_nchunk[c] = (int)chunks.size() - c0; }
         }
     }
-    t.g_out.alloc(h_out.size());
-    t.g_in.alloc(h_in.size());
+    {
+        const size_t ntot = (size_t)nm + h_out.size();
+        DArray<int> go, gi;
+        go.alloc(ntot);
+        gi.alloc(ntot);
+        if (nm > 0) {
+            BEM_CUDA(cudaMemcpyAsync(go.p, t.g_out.p, nm * sizeof(int), cudaMemcpyDeviceToDevice, s));
+            BEM_CUDA(cudaMemcpyAsync(gi.p, t.g_in.p, nm * sizeof(int), cudaMemcpyDeviceToDevice, s));
+        }
+        if (!h_out.empty()) {
+            BEM_CUDA(cudaMemcpyAsync(go.p + nm, h_out.data(), h_out.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+            BEM_CUDA(cudaMemcpyAsync(gi.p + nm, h_in.data(), h_in.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        }
+        BEM_CUDA(cudaStreamSynchronize(s));
+        t.g_out = std::move(go);
+        t.g_in = std::move(gi);
+    }
     t.g_chunk.alloc(chunks.size());
-    BEM_CUDA(cudaMemcpyAsync(t.g_out.p, h_out.data(), h_out.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    BEM_CUDA(cudaMemcpyAsync(t.g_in.p, h_in.data(), h_in.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     BEM_CUDA(cudaMemcpyAsync(t.g_chunk.p, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
     BEM_CUDA(cudaStreamSynchronize(s));
 }
@@ -1575,11 +1646,11 @@ struct PassBufs<float> {
     static float *L(Mesh &m) { return m.Lf.p; }
     static float *far(Mesh &m) { return m.far_f.p; }
     static float *near(Mesh &m) { return m.near_f.p; }
-    static const cpx<float> *R(Mesh &m) { return reinterpret_cast<const cpx<float> *>(m.tab->Rm2m_f.p); }
-    static const cpx<float> *I(Mesh &m) { return reinterpret_cast<const cpx<float> *>(m.tab->If_f.p); }
-    static const float *Om2l(Mesh &m) { return m.tab->Om2l_f.p; }
-    static const float *Om2m(Mesh &m) { return m.tab->Om2m_f.p; }
-    static const float *Ol2l(Mesh &m) { return m.tab->Ol2l_f.p; }
+    static const cpx<float> *R(const Tables &t) { return reinterpret_cast<const cpx<float> *>(t.Rm2m_f.p); }
+    static const cpx<float> *I(const Tables &t) { return reinterpret_cast<const cpx<float> *>(t.If_f.p); }
+    static const float *Om2l(const Tables &t) { return t.Om2l_f.p; }
+    static const float *Om2m(const Tables &t) { return t.Om2m_f.p; }
+    static const float *Ol2l(const Tables &t) { return t.Ol2l_f.p; }
     static const float4 *cen(Mesh &m) { return m.cen32.p; }
     static const float4 *nrm(Mesh &m) { return m.nrm32.p; }
     static const float4 *nrmq(Mesh &m) { return m.nrmq32.p; }
@@ -1593,11 +1664,11 @@ struct PassBufs<double> {
     static double *L(Mesh &m) { return m.Ld.p; }
     static double *far(Mesh &m) { return m.far_d.p; }
     static double *near(Mesh &m) { return m.near_d.p; }
-    static const cpx<double> *R(Mesh &m) { return reinterpret_cast<const cpx<double> *>(m.tab->Rm2m_d.p); }
-    static const cpx<double> *I(Mesh &m) { return reinterpret_cast<const cpx<double> *>(m.tab->If_d.p); }
-    static const double *Om2l(Mesh &m) { return m.tab->Om2l_d.p; }
-    static const double *Om2m(Mesh &m) { return m.tab->Om2m_d.p; }
-    static const double *Ol2l(Mesh &m) { return m.tab->Ol2l_d.p; }
+    static const cpx<double> *R(const Tables &t) { return reinterpret_cast<const cpx<double> *>(t.Rm2m_d.p); }
+    static const cpx<double> *I(const Tables &t) { return reinterpret_cast<const cpx<double> *>(t.If_d.p); }
+    static const double *Om2l(const Tables &t) { return t.Om2l_d.p; }
+    static const double *Om2m(const Tables &t) { return t.Om2m_d.p; }
+    static const double *Ol2l(const Tables &t) { return t.Ol2l_d.p; }
     static const double4 *cen(Mesh &m) { return m.cen64r.p; }
     static const double4 *nrm(Mesh &m) { return m.nrm64r.p; }
     static const double4 *nrmq(Mesh &m) { return m.nrmq64r.p; }
@@ -1666,6 +1737,7 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
     using B = PassBufs<T>;
     cudaStream_t s = m.stream;
     const TreeView tv = view(t);
+    const Tables &tb = tables_for(m, t);
     const int p = m.opt.p;
     const int nc = (p + 1) * (p + 1);
     const int W = 2 * p + 1, W2 = 4 * p + 1;
@@ -1702,18 +1774,25 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             if (small) k128<<<t.nleaf, 128, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
             else k256<<<t.nleaf, 256, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
         };
+        const bool wide = t.ws == 2;
+        if (t.ws != 1 && t.ws != 2) throw Error(BEM_EUNSUPPORTED, "near field: separation not built");
+        if (wide && (sk == SRC_QUAD && tk == TGT_CEN_DN || sk == SRC_QUAD && tk == TGT_QUAD_DN))
+            throw Error(BEM_EUNSUPPORTED, "the panel tree is separated by one cell");
         if (sk == SRC_QUAD && tk == TGT_CEN_DN)
             go(k_p2p<T, SRC_QUAD, TGT_CEN_DN, 128>, k_p2p<T, SRC_QUAD, TGT_CEN_DN, 256>);
-        else if (sk == SRC_CHARGE && tk == TGT_CEN_DN)
-            go(k_p2p<T, SRC_CHARGE, TGT_CEN_DN, 128>, k_p2p<T, SRC_CHARGE, TGT_CEN_DN, 256>);
-        else if (sk == SRC_QUAD && tk == TGT_CHG_PHI)
-            go(k_p2p<T, SRC_QUAD, TGT_CHG_PHI, 128>, k_p2p<T, SRC_QUAD, TGT_CHG_PHI, 256>);
         else if (sk == SRC_QUAD && tk == TGT_QUAD_DN)
             go(k_p2p<T, SRC_QUAD, TGT_QUAD_DN, 128>, k_p2p<T, SRC_QUAD, TGT_QUAD_DN, 256>);
-        else if (sk == SRC_CHARGE && tk == TGT_QUAD_DN)
-            go(k_p2p<T, SRC_CHARGE, TGT_QUAD_DN, 128>, k_p2p<T, SRC_CHARGE, TGT_QUAD_DN, 256>);
-        else
-            go(k_p2p<T, SRC_CHARGE, TGT_CHG_PHI, 128>, k_p2p<T, SRC_CHARGE, TGT_CHG_PHI, 256>);
+        else if (sk == SRC_CHARGE && tk == TGT_CEN_DN) {
+            if (wide) go(k_p2p<T, SRC_CHARGE, TGT_CEN_DN, 128, 125>, k_p2p<T, SRC_CHARGE, TGT_CEN_DN, 256, 125>);
+            else go(k_p2p<T, SRC_CHARGE, TGT_CEN_DN, 128>, k_p2p<T, SRC_CHARGE, TGT_CEN_DN, 256>);
+        } else if (sk == SRC_QUAD && tk == TGT_CHG_PHI) {
+            if (wide) go(k_p2p<T, SRC_QUAD, TGT_CHG_PHI, 128, 125>, k_p2p<T, SRC_QUAD, TGT_CHG_PHI, 256, 125>);
+            else go(k_p2p<T, SRC_QUAD, TGT_CHG_PHI, 128>, k_p2p<T, SRC_QUAD, TGT_CHG_PHI, 256>);
+        } else if (sk == SRC_CHARGE && tk == TGT_QUAD_DN) {
+            if (wide) go(k_p2p<T, SRC_CHARGE, TGT_QUAD_DN, 128, 125>, k_p2p<T, SRC_CHARGE, TGT_QUAD_DN, 256, 125>);
+            else go(k_p2p<T, SRC_CHARGE, TGT_QUAD_DN, 128>, k_p2p<T, SRC_CHARGE, TGT_QUAD_DN, 256>);
+        } else
+            throw Error(BEM_EUNSUPPORTED, "near field: source/target combination not built");
         BEM_CHECK_LAUNCH();
     };
     if (conc) {
@@ -1738,39 +1817,39 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
                 BEM_CUDA(cudaMemsetAsync(M + (size_t)t.lvl_off[2] * cs, 0,
                                          (size_t)(t.lvl_off[t.L] - t.lvl_off[2]) * cs * sizeof(T), s));
             for (int c = t.L; c >= 3; --c)
-                tree_translate<T>(B::Om2m(m), nc, cs, rblocks, t, t.m2m_chunk0[c], t.m2m_nchunk[c], M, M, s);
+                tree_translate<T>(B::Om2m(tb), nc, cs, rblocks, t, t.m2m_chunk0[c], t.m2m_nchunk[c], M, M, s);
         } else {
             const size_t sm = 2 * (size_t)(p + 1) * W * sizeof(cpx<T>);
             set_smem<T>(k_m2m<T>, sm);
             for (int l = t.L - 1; l >= 2; --l) {
                 const int cnt = t.lvl_off[l + 1] - t.lvl_off[l];
-                if (cnt > 0) k_m2m<T><<<cnt, 160, sm, s>>>(tv, t.lvl_off[l], B::R(m), p, cs, M);
+                if (cnt > 0) k_m2m<T><<<cnt, 160, sm, s>>>(tv, t.lvl_off[l], B::R(tb), p, cs, M);
                 BEM_CHECK_LAUNCH();
             }
         }
         ev_rec(m, timed, 2);
         // M2L: every cell at levels 2..L
         if (dense) {
-            m2l_dense<T>(m, t, B::Om2l(m), nc, cs, rblocks, trsm, M, L, timed);
+            m2l_dense<T>(m, t, B::Om2l(tb), nc, cs, rblocks, trsm, M, L, timed);
         } else {
             const size_t sm = ((size_t)(p + 1) * W + (size_t)(2 * p + 1) * W2) * sizeof(cpx<T>);
             set_smem<T>(k_m2l<T>, sm);
             const int first = t.lvl_off[2];
             const int cnt = t.ncell - first;
-            if (cnt > 0) k_m2l<T><<<cnt, 160, sm, s>>>(tv, first, B::I(m), p, cs, M, L);
+            if (cnt > 0) k_m2l<T><<<cnt, 160, sm, s>>>(tv, first, B::I(tb), p, cs, M, L);
             BEM_CHECK_LAUNCH();
         }
         ev_rec(m, timed, 3);
         // L2L: children at levels 3..L
         if (dense) {
             for (int c = 3; c <= t.L; ++c)
-                tree_translate<T>(B::Ol2l(m), nc, cs, rblocks, t, t.l2l_chunk0[c], t.l2l_nchunk[c], L, L, s);
+                tree_translate<T>(B::Ol2l(tb), nc, cs, rblocks, t, t.l2l_chunk0[c], t.l2l_nchunk[c], L, L, s);
         } else {
             const size_t sm = 2 * (size_t)(p + 1) * W * sizeof(cpx<T>);
             set_smem<T>(k_l2l<T>, sm);
             for (int l = 3; l <= t.L; ++l) {
                 const int cnt = t.lvl_off[l + 1] - t.lvl_off[l];
-                if (cnt > 0) k_l2l<T><<<cnt, 160, sm, s>>>(tv, t.lvl_off[l], B::R(m), p, cs, L);
+                if (cnt > 0) k_l2l<T><<<cnt, 160, sm, s>>>(tv, t.lvl_off[l], B::R(tb), p, cs, L);
                 BEM_CHECK_LAUNCH();
             }
         }
@@ -2052,6 +2131,7 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
     cudaStream_t s = m.stream;
     const Tree &t = m.tp;
     const TreeView tv = view(t);
+    const Tables &tb = tables_for(m, t);
     const int p = m.opt.p;
     const int nc = (p + 1) * (p + 1);
     const int cs = cell_stride(p);
@@ -2089,10 +2169,10 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
             BEM_CUDA(cudaMemsetAsync(M + (size_t)t.lvl_off[2] * cs, 0,
                                      (size_t)(t.lvl_off[t.L] - t.lvl_off[2]) * cs * sizeof(T), s));
         for (int c = t.L; c >= 3; --c)
-            tree_translate<T>(B::Om2m(m), nc, cs, rblocks, t, t.m2m_chunk0[c], t.m2m_nchunk[c], M, M, s);
-        m2l_dense<T>(m, t, B::Om2l(m), nc, cs, rblocks, trsm, M, L);
+            tree_translate<T>(B::Om2m(tb), nc, cs, rblocks, t, t.m2m_chunk0[c], t.m2m_nchunk[c], M, M, s);
+        m2l_dense<T>(m, t, B::Om2l(tb), nc, cs, rblocks, trsm, M, L);
         for (int c = 3; c <= t.L; ++c)
-            tree_translate<T>(B::Ol2l(m), nc, cs, rblocks, t, t.l2l_chunk0[c], t.l2l_nchunk[c], L, L, s);
+            tree_translate<T>(B::Ol2l(tb), nc, cs, rblocks, t, t.l2l_chunk0[c], t.l2l_nchunk[c], L, L, s);
         const size_t sm = (size_t)(p + 1) * (2 * p + 1) * sizeof(cpx<T>);
         auto kern = k_l2p<T, TGT_QUAD_PHI>;
         set_smem<T>(kern, sm);
@@ -2116,16 +2196,14 @@ bool is_near_field_kernel(const void *func) {
         reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CEN_DN, 256>),
         reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CHG_PHI, 128>),
         reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CHG_PHI, 256>),
-        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CHG_PHI, 128>),
-        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CHG_PHI, 256>),
+
         reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CEN_DN, 128>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CEN_DN, 256>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CEN_DN, 128>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CEN_DN, 256>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CHG_PHI, 128>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CHG_PHI, 256>),
-        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CHG_PHI, 128>),
-        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CHG_PHI, 256>),
+
         reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_QUAD_DN, 128>),
         reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_QUAD_DN, 256>),
         reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_QUAD_DN, 128>),
@@ -2134,6 +2212,18 @@ bool is_near_field_kernel(const void *func) {
         reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_QUAD_DN, 256>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_QUAD_DN, 128>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_QUAD_DN, 256>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CEN_DN, 128, 125>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_CEN_DN, 256, 125>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CHG_PHI, 128, 125>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CHG_PHI, 256, 125>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_QUAD_DN, 128, 125>),
+        reinterpret_cast<const void *>(k_p2p<float, SRC_CHARGE, TGT_QUAD_DN, 256, 125>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CEN_DN, 128, 125>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_CEN_DN, 256, 125>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CHG_PHI, 128, 125>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CHG_PHI, 256, 125>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_QUAD_DN, 128, 125>),
+        reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_QUAD_DN, 256, 125>),
         reinterpret_cast<const void *>(k_p2p_t<float>),
         reinterpret_cast<const void *>(k_p2p_t<double>),
     };

@@ -26,7 +26,11 @@ namespace bem {
 
 constexpr int MAXP = 16;           // largest expansion order built
 constexpr int MORTON_BITS = 21;    // bits per axis in a key
-constexpr int NOFFSET = 343;       // (dx,dy,dz) in [-3,3]^3 -> 7*7*7 classes
+// M2L offset classes of a tree whose cells interact once separated by `ws`
+// cells (ws = 1: children of the parent's neighbours not adjacent, offsets
+// in [-3,3]^3 -> 343 classes; ws = 2: offsets in [-5,5]^3 -> 1331 classes)
+inline int m2l_radius(int ws) { return 2 * ws + 1; }
+inline int m2l_classes(int ws) { const int w = 2 * m2l_radius(ws) + 1; return w * w * w; }
 constexpr double PI = 3.14159265358979323846;
 constexpr double FOUR_PI = 12.566370614359172953850573533118;
 constexpr double KCAL = 332.0637;  // e^2/(4 pi eps0 A) in kcal/mol
@@ -104,6 +108,8 @@ struct DArray {
 // Octree over one or more point sets sharing the root cube and leaf level.
 struct Tree {
     int L = 0;                    // leaf level
+    int ws = 1;                   // separation (in cells) of interacting cells: neighbours
+                                  // are the leaves within ws cells, M2L partners lie farther
     std::vector<int> lvl_off;     // cells of level l: [lvl_off[l], lvl_off[l+1])
     int ncell = 0, nleaf = 0, leaf0 = 0;
     DArray<uint64_t> key;         // [ncell] Morton key at the cell's own level
@@ -127,8 +133,9 @@ struct Tree {
     DArray<int> p2p_order;        // leaves by decreasing near-field work (launch order)
     DArray<int4> tc_super;        // tensor-core M2L work items (offset, first chunk, chunks)
     int tc_nsuper = 0;
-    // M2L pairs by target cell (levels >= 2, CSR over cell - lvl_off[2]; pair
-    // indices ascending) for the store-then-sum form of the tensor-core M2L
+    // M2L pairs by target cell (levels >= 2, CSR over cell - lvl_off[2]; each
+    // entry a pair's position in the grouped order) for the store-then-sum
+    // form of the tensor-core M2L
     DArray<int> m2l_toff, m2l_tpairs;
     bool m2l_store = false;
     int m2l_chunk0 = 0, m2l_nchunk = 0;
@@ -167,6 +174,7 @@ struct Mesh;
 //         each [in] row padded with zeros to the cell stride.
 struct Tables {
     int p = 0;
+    int ws = 1;                   // the M2L operators cover the offset classes of this separation
     DArray<float> Rm2m_f, If_f, Om2l_f, Om2m_f, Ol2l_f;
     DArray<double> Rm2m_d, If_d, Om2l_d, Om2m_d, Ol2l_d;
     DArray<float> Tc_hi, Tc_lo;   // M2L operators split for 3xTF32, tensor-core tile order
@@ -243,7 +251,8 @@ struct Mesh {
     int64_t nt_nnz = 0;
     DArray<int> qp_of_panel;           // [np][nq] sorted quadrature points of each sorted panel
 
-    std::shared_ptr<Tables> tab;
+    std::shared_ptr<Tables> tab;       // translations of the panel tree (ws = 1)
+    std::shared_ptr<Tables> tab2;      // of a charge tree separated by two cells (ws = 2)
 
     // expansion buffers (sized for the larger tree)
     DArray<float> Mf, Lf;
@@ -291,6 +300,10 @@ void build_qp_of_panel(Mesh &m);
 // Galerkin form: per-quadrature-point normal records and the scratch it needs
 void build_galerkin_geometry(Mesh &m);
 void build_tables(Mesh &m);
+const Tables &tables_for(const Mesh &m, const Tree &t);
+// stable sort of int keys in [0, 2^bits) with int values, on the device
+void sort_pairs_int(const int *k_in, const int *v_in, int *k_out, int *v_out, int64_t n, int bits,
+                    cudaStream_t s);
 void build_translation_groups(Mesh &m, Tree &t);
 // tensor-core M2L (bem_tc.cu)
 bool tc_m2l_available(const Mesh &m);

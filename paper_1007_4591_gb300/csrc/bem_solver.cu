@@ -190,6 +190,11 @@ __global__ void k_scale_by(double *w, const double *sc, int64_t n) {
     if (r < n) w[r] *= sc[0];
 }
 
+__global__ void k_scale_by_inv(double *w, const double *d, int64_t n) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < n) w[r] /= d[0];
+}
+
 __global__ void k_axpby(double a, const double *x, double b, const double *y, double *out,
                         int64_t n) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -320,12 +325,9 @@ int gmres_solve(Mesh &m, const double *b, double *x, bool transpose, bem_solve_s
             conv = true;
             break;
         }
-        {
-            const double inv = 1.0 / beta;
-            BEM_CUDA(cudaMemcpyAsync(m.red.p + 4, &inv, sizeof(double), cudaMemcpyHostToDevice, s));
-            k_scale_by<<<nb, 256, 0, s>>>(V0, m.red.p + 4, n);
-            BEM_CHECK_LAUNCH();
-        }
+        // V0 /= beta, with beta read on the device (norm2 left it in red[0])
+        k_scale_by_inv<<<nb, 256, 0, s>>>(V0, m.red.p, n);
+        BEM_CHECK_LAUNCH();
         k_set_g<<<1, 64, 0, s>>>(m.gv.p, m1, beta);
         BEM_CHECK_LAUNCH();
         int k = 0;

@@ -586,6 +586,7 @@ bool m2l_store_fits(int64_t npairs, int p) {
 // into the mesh's buffer, then a fixed-order sum per target (deterministic);
 // otherwise L is cleared and the rows are added by bulk reductions.
 void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed) {
+    const Tables &tb = tables_for(m, t);
     const int nc = (m.opt.p + 1) * (m.opt.p + 1);
     const int cs = cell_stride(m.opt.p);
     const int first = t.lvl_off[2];
@@ -613,7 +614,7 @@ void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed) {
     kev(1);
     if (store) {
         ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc<true>), sm);
-        k_m2l_tc<true><<<grid, TC_THREADS, sm, m.stream>>>(m.tab->Tc_hi.p, m.tab->Tc_lo.p, t.tc_super.p, t.tc_nsuper,
+        k_m2l_tc<true><<<grid, TC_THREADS, sm, m.stream>>>(tb.Tc_hi.p, tb.Tc_lo.p, t.tc_super.p, t.tc_nsuper,
                                                            m.dev_err.p + 1, t.g_out.p, t.g_in.p, cs, m.Mtc.p,
                                                            m.m2lR.p, m.dev_err.p, m.wait_budget);
         BEM_CHECK_LAUNCH();
@@ -626,7 +627,7 @@ void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed) {
         kev(3);
     } else {
         ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc<false>), sm);
-        k_m2l_tc<false><<<grid, TC_THREADS, sm, m.stream>>>(m.tab->Tc_hi.p, m.tab->Tc_lo.p, t.tc_super.p, t.tc_nsuper,
+        k_m2l_tc<false><<<grid, TC_THREADS, sm, m.stream>>>(tb.Tc_hi.p, tb.Tc_lo.p, t.tc_super.p, t.tc_nsuper,
                                                             m.dev_err.p + 1, t.g_out.p, t.g_in.p, cs, m.Mtc.p, L,
                                                             m.dev_err.p, m.wait_budget);
         BEM_CHECK_LAUNCH();

@@ -387,9 +387,10 @@ __global__ void k_leaf_csr(const uint64_t *setkey, int64_t n, int shift, const u
     beg[i] = (int)lo;
 }
 
-// P2P neighbour list: the adjacent leaves (and the leaf itself) that exist.
+// P2P neighbour list: the leaves within ws cells (the adjacent ones for
+// ws = 1, and the leaf itself) that exist.
 template <bool FILL>
-__global__ void k_nbr(const uint64_t *key, const int4 *ijk, int leaf0, int nleaf, int L,
+__global__ void k_nbr(const uint64_t *key, const int4 *ijk, int leaf0, int nleaf, int L, int ws,
                       const int *off, int *cnt_or_list) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nleaf) return;
@@ -397,9 +398,9 @@ __global__ void k_nbr(const uint64_t *key, const int4 *ijk, int leaf0, int nleaf
     int lim = 1 << L;
     int n = 0;
     int base = FILL ? off[t] : 0;
-    for (int dx = -1; dx <= 1; ++dx)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dz = -1; dz <= 1; ++dz) {
+    for (int dx = -ws; dx <= ws; ++dx)
+        for (int dy = -ws; dy <= ws; ++dy)
+            for (int dz = -ws; dz <= ws; ++dz) {
                 int a = c.x + dx, b = c.y + dy, e = c.z + dz;
                 if (a < 0 || b < 0 || e < 0 || a >= lim || b >= lim || e >= lim) continue;
                 int f = find_key(key, leaf0, leaf0 + nleaf, morton3(a, b, e));
@@ -411,26 +412,28 @@ __global__ void k_nbr(const uint64_t *key, const int4 *ijk, int leaf0, int nleaf
 }
 
 // M2L list of cell t (level >= 2): children of the neighbours of t's parent
-// that are not adjacent to t.  Offset class = (dx+3)*49 + (dy+3)*7 + (dz+3),
-// (dx,dy,dz) = ijk_source - ijk_target.
+// (the cells within ws of it) that are not neighbours of t.  With
+// R = 2 ws + 1 and W = 2 R + 1 the offset class is
+// (dx+R)*W*W + (dy+R)*W + (dz+R), (dx,dy,dz) = ijk_source - ijk_target in [-R,R]^3.
 template <bool FILL>
 __global__ void k_m2l(const uint64_t *key, const int4 *ijk, const int *parent, const int *cbeg,
-                      const int *cend, const int *lvl_off, int first, int last, const int *off,
+                      const int *cend, const int *lvl_off, int first, int last, int ws, const int *off,
                       int *cnt, int *src, int *ofs) {
     int t = first + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= last) return;
     int4 c = ijk[t];
     int l = c.w;
     int n = 0;
+    const int R = 2 * ws + 1, W = 2 * R + 1;
     if (l >= 2) {
         int P = parent[t];
         int4 pc = ijk[P];
         int lim = 1 << (l - 1);
         int plo = lvl_off[l - 1], phi = lvl_off[l];
         int base = FILL ? off[t] : 0;
-        for (int dx = -1; dx <= 1; ++dx)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dz = -1; dz <= 1; ++dz) {
+        for (int dx = -ws; dx <= ws; ++dx)
+            for (int dy = -ws; dy <= ws; ++dy)
+                for (int dz = -ws; dz <= ws; ++dz) {
                     int a = pc.x + dx, b = pc.y + dy, e = pc.z + dz;
                     if (a < 0 || b < 0 || e < 0 || a >= lim || b >= lim || e >= lim) continue;
                     int f = find_key(key, plo, phi, morton3(a, b, e));
@@ -438,10 +441,10 @@ __global__ void k_m2l(const uint64_t *key, const int4 *ijk, const int *parent, c
                     for (int s = cbeg[f]; s < cend[f]; ++s) {
                         int4 sc = ijk[s];
                         int ddx = sc.x - c.x, ddy = sc.y - c.y, ddz = sc.z - c.z;
-                        if (abs(ddx) <= 1 && abs(ddy) <= 1 && abs(ddz) <= 1) continue;
+                        if (abs(ddx) <= ws && abs(ddy) <= ws && abs(ddz) <= ws) continue;
                         if (FILL) {
                             src[base + n] = s;
-                            ofs[base + n] = (ddx + 3) * 49 + (ddy + 3) * 7 + (ddz + 3);
+                            ofs[base + n] = ((ddx + R) * W + (ddy + R)) * W + (ddz + R);
                         }
                         ++n;
                     }
@@ -484,6 +487,16 @@ static void sort_pairs(uint64_t *k_in, int *v_in, uint64_t *k_out, int *v_out, i
                                              3 * MORTON_BITS, s));
 }
 
+void sort_pairs_int(const int *k_in, const int *v_in, int *k_out, int *v_out, int64_t n, int bits,
+                    cudaStream_t s) {
+    DArray<char> tmp;
+    size_t bytes = 0;
+    BEM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, k_in, k_out, v_in, v_out, (int)n, 0, bits, s));
+    void *t = cub_temp(bytes, tmp);
+    BEM_CUDA(cub::DeviceRadixSort::SortPairs(t, bytes, k_in, k_out, v_in, v_out, (int)n, 0, bits, s));
+    BEM_CUDA(cudaStreamSynchronize(s));  // `tmp` is released on return
+}
+
 static void scan_exclusive(const int *in, int *out, int n, cudaStream_t s) {
     DArray<char> tmp;
     size_t bytes = 0;
@@ -514,9 +527,10 @@ struct SetKeys {
 };
 
 // Build the octree over up to three sorted point sets at leaf level L.
-static void build_tree(Mesh &m, Tree &t, SetKeys cen, SetKeys qp, SetKeys chg) {
+static void build_tree(Mesh &m, Tree &t, SetKeys cen, SetKeys qp, SetKeys chg, int ws) {
     cudaStream_t s = m.stream;
     const int L = m.L;
+    t.ws = ws;
     const int shift = 3 * (MORTON_BITS - L);
     const int64_t total = cen.n + qp.n + chg.n;
     t.L = L;
@@ -627,13 +641,13 @@ static void build_tree(Mesh &m, Tree &t, SetKeys cen, SetKeys qp, SetKeys chg) {
         DArray<int> c;
         c.alloc(nleaf + 1);
         BEM_CUDA(cudaMemsetAsync(c.p, 0, (nleaf + 1) * sizeof(int), s));
-        k_nbr<false><<<cdiv(nleaf, TB), TB, 0, s>>>(t.key.p, t.ijk.p, t.leaf0, nleaf, L, nullptr, c.p);
+        k_nbr<false><<<cdiv(nleaf, TB), TB, 0, s>>>(t.key.p, t.ijk.p, t.leaf0, nleaf, L, ws, nullptr, c.p);
         BEM_CHECK_LAUNCH();
         t.nbr_off.alloc(nleaf + 1);
         scan_exclusive(c.p, t.nbr_off.p, nleaf + 1, s);
         t.nnbr = to_host(t.nbr_off.p + nleaf, s);
         t.nbr.alloc(t.nnbr);
-        k_nbr<true><<<cdiv(nleaf, TB), TB, 0, s>>>(t.key.p, t.ijk.p, t.leaf0, nleaf, L, t.nbr_off.p,
+        k_nbr<true><<<cdiv(nleaf, TB), TB, 0, s>>>(t.key.p, t.ijk.p, t.leaf0, nleaf, L, ws, t.nbr_off.p,
                                                    t.nbr.p);
         BEM_CHECK_LAUNCH();
     }
@@ -647,7 +661,7 @@ static void build_tree(Mesh &m, Tree &t, SetKeys cen, SetKeys qp, SetKeys chg) {
         c.alloc(t.ncell + 1);
         BEM_CUDA(cudaMemsetAsync(c.p, 0, (t.ncell + 1) * sizeof(int), s));
         k_m2l<false><<<cdiv(t.ncell, TB), TB, 0, s>>>(t.key.p, t.ijk.p, t.parent.p, t.child_beg.p,
-                                                      t.child_end.p, loff.p, 0, t.ncell, nullptr,
+                                                      t.child_end.p, loff.p, 0, t.ncell, ws, nullptr,
                                                       c.p, nullptr, nullptr);
         BEM_CHECK_LAUNCH();
         t.m2l_off.alloc(t.ncell + 1);
@@ -656,7 +670,7 @@ static void build_tree(Mesh &m, Tree &t, SetKeys cen, SetKeys qp, SetKeys chg) {
         t.m2l_src.alloc(t.nm2l);
         t.m2l_ofs.alloc(t.nm2l);
         k_m2l<true><<<cdiv(t.ncell, TB), TB, 0, s>>>(t.key.p, t.ijk.p, t.parent.p, t.child_beg.p,
-                                                     t.child_end.p, loff.p, 0, t.ncell, t.m2l_off.p,
+                                                     t.child_end.p, loff.p, 0, t.ncell, ws, t.m2l_off.p,
                                                      nullptr, t.m2l_src.p, t.m2l_ofs.p);
         BEM_CHECK_LAUNCH();
         BEM_CUDA(cudaStreamSynchronize(s));
@@ -752,7 +766,12 @@ static void build_charges(Mesh &m, const double *d_charges) {
     }
     m.tc = Tree();
     SetKeys cen{m.cen_key.p, m.np}, qp{m.qp_key.p, m.nqp}, ch{m.chg_key.p, m.nc};
-    build_tree(m, m.tc, cen, qp, ch);
+    // Point charges sit anywhere in their cells (on a corner, as the Born
+    // ion's does), where a one-cell separation converges only like
+    // (sqrt(3)/2)^p; when the products with the charges run as fast
+    // multipole passes their tree interacts at two cells' separation
+    // (ratio sqrt(3)/3): 5^3 neighbour leaves, offsets in [-5,5]^3.
+    build_tree(m, m.tc, cen, qp, ch, charge_direct(m) ? 1 : 2);
 }
 
 void build_geometry_and_trees(Mesh &m, const double *d_panels, const double *d_charges) {
@@ -895,7 +914,7 @@ void build_geometry_and_trees(Mesh &m, const double *d_panels, const double *d_c
 
     // 6. trees
     SetKeys sc{m.cen_key.p, np}, sq{m.qp_key.p, nqp}, none{};
-    build_tree(m, m.tp, sc, sq, none);
+    build_tree(m, m.tp, sc, sq, none, 1);
     build_charges(m, d_charges);
     BEM_CUDA(cudaStreamSynchronize(s));
 }
