@@ -133,7 +133,8 @@ size_t Mesh::bytes() const {
     if (tab) b += tab->bytes();
     if (tab2) b += tab2->bytes();
     b += Mf.bytes() + Lf.bytes() + Md.bytes() + Ld.bytes();
-    b += Mtc.bytes() + m2lR.bytes() + ctq.bytes() + str32.bytes() + str64.bytes() + dpart_f.bytes() + dpart_d.bytes();
+    b += Mtc.bytes() + m2lR.bytes() + ctq.bytes() + str32.bytes() + str64.bytes() + near64.bytes() + dpart_f.bytes() +
+         dpart_d.bytes();
     b += xs.bytes() + ys.bytes() + zs.bytes() + far_f.bytes() + near_f.bytes() + far_d.bytes() +
          near_d.bytes() + io_a.bytes() + io_b.bytes() + red.bytes();
     b += dev_err.bytes();
@@ -163,13 +164,14 @@ static void alloc_work(Mesh &m) {
         ensure(m.far_d, nt);
         ensure(m.near_d, nt);
     }
-    const size_t nsrc = (size_t)std::max<int64_t>(m.nqp, m.nc);
     if (tc_m2l_available(m)) {
         ensure(m.Mtc, tc_staging_floats(m));
         ensure(m.m2lR, m2l_store_floats(m));
     }
+    const size_t nsrc = (size_t)std::max<int64_t>(m.nqp, m.nc);
     if (m.opt.precision == BEM_MIXED) ensure(m.str32, nsrc);
     else ensure(m.str64, nsrc);
+    ensure(m.near64, (size_t)m.np);
     const size_t nv = (size_t)std::max<int64_t>(m.np, m.nc);
     ensure(m.xs, nv);
     ensure(m.ys, nv);
@@ -588,9 +590,16 @@ int bem_last_phase_ms(const bem_mesh *m, double *times) {
         set_last_error("profiling is off");
         return BEM_EINVAL;
     }
+    // phase k spans events beg[k] .. beg[k] + 1; with the near field run
+    // before the fused L2P + epilogue, L2P is 5-6 and P2P 4-5
+    int beg[7] = {0, 1, 2, 3, 4, 5, 6};
+    if (m->tm.near_before_l2p) {
+        beg[4] = 5;
+        beg[5] = 4;
+    }
     for (int k = 0; k < 7; ++k) {
         float ms = 0;
-        if (cudaEventElapsedTime(&ms, m->tm.ev[k], m->tm.ev[k + 1]) != cudaSuccess) {
+        if (cudaEventElapsedTime(&ms, m->tm.ev[beg[k]], m->tm.ev[beg[k] + 1]) != cudaSuccess) {
             cudaGetLastError();
             ms = 0;
         }

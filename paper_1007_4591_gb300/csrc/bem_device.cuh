@@ -11,6 +11,27 @@ template <class T> struct V4T;
 template <> struct V4T<float> { using t = float4; };
 template <> struct V4T<double> { using t = double4; };
 
+// Strength of source i of a pass: the record's weight times the density
+// (A_j w_q dens[panel] for a quadrature point; dens[k], or the charge stored
+// in the record when dens is null, for a charge).
+// A null dens means the records already hold the strengths.
+template <class T, int SRC>
+__device__ __forceinline__ T src_strength(T w, int64_t i, const int *qpanel, const double *dens) {
+    if (!dens) return w;
+    if constexpr (SRC == SRC_QUAD) return w * (T)dens[qpanel[i]];
+    else return (T)dens[i];
+}
+
+// The operator's epilogue y = x + Ehat (far + near) / (4 pi), fused into
+// the last kernel of the collocation K' product (the near field already
+// carries the near-singular table's FP64 correction, times 4 pi).
+struct ApplyEpi {
+    const double *x;       // the product's input (sorted order)
+    const double *near64;  // near field + 4 pi table x (null: no near field)
+    double *y;             // output; null: no epilogue
+    double ehat;
+};
+
 template <class T>
 struct cpx {
     T x, y;
@@ -74,8 +95,18 @@ __device__ __forceinline__ void regular_solid_c(T x, T y, T z, F &&emit) {
 // P2M of every leaf with the expansion order dispatched to a compile-time
 // instance (p in 1..MAXP); one CTA per leaf, queued on `s`:
 //   M[leaf]_n^m = sum over the leaf's sources of s_i conj(R_n^m(y_i - z)) / h^n
+// with s_i = src_strength(record weight, i, qpanel, dens).
 template <class T>
-void p2m_leaves(const TreeView &tv, int nleaf, SrcKind sk, const typename V4T<T>::t *src, int p,
-                int cs, T inv_h, T *M, cudaStream_t s);
+void p2m_leaves(const TreeView &tv, int nleaf, SrcKind sk, const typename V4T<T>::t *src, const int *qpanel,
+                const double *dens, int p, int cs, T inv_h, T *M, cudaStream_t s);
+
+// L2P of every leaf with a compile-time expansion order (p in {6, 8, 10,
+// 12}); one CTA of nth threads per leaf, queued on `s`.  Returns false (and
+// launches nothing) for other orders.  With epi.y set (collocation targets)
+// it writes the operator's output y instead of the far field.
+template <class T>
+bool l2p_leaves_c(const TreeView &tv, int nleaf, int nth, TgtKind tk, int p, const typename V4T<T>::t *tgt,
+                  const typename V4T<T>::t *nrm, int cs, T inv_h, const T *L, T *out, cudaStream_t s,
+                  ApplyEpi epi = ApplyEpi{nullptr, nullptr, nullptr, 0.0});
 
 }  // namespace bem

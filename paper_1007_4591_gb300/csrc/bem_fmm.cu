@@ -343,18 +343,30 @@ __device__ __forceinline__ void dn_pair(T dx, T dy, T dz, T nx, T ny, T nz, T &n
     ri3 = ri * ri * ri;
 }
 
-// Source strengths of one pass, s = A_j w_q dens[panel] for quadrature
-// points or s = q_k (or dens[k]) for charges, written next to the
-// leaf-relative coordinates so that P2M and P2P read one record per source.
+// Strength records of a pass's near field, s = A_j w_q dens[panel] for
+// quadrature points or s = q_k (or dens[k]) for charges, next to the
+// leaf-relative coordinates: the near-field kernel stages one record per
+// source (P2M forms the same products itself).
 template <class T, int SRC>
 __global__ void k_strength(const typename V4T<T>::t *rec, const int *qpanel, const double *dens,
                            int64_t n, typename V4T<T>::t *out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     typename V4T<T>::t r = rec[i];
-    if (SRC == SRC_QUAD) r.w = r.w * (T)dens[qpanel[i]];
-    else if (dens) r.w = (T)dens[i];
+    r.w = src_strength<T, SRC>(r.w, i, qpanel, dens);
     out[i] = r;
+}
+
+// y = x + Ehat (far + near64) / (4 pi), near64 already holding the table's
+// correction: the collocation product's epilogue where L2P cannot carry it.
+template <class T>
+__global__ void k_apply_far_near(const double *x, const T *far, const double *near64, double ehat, int64_t n,
+                                 double *y) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = near64 ? near64[i] : 0.0;
+    if (far) v += (double)far[i];
+    y[i] = x[i] + ehat * (v * (1.0 / FOUR_PI));
 }
 
 // Two lanes of T: packed FP32 instructions on sm_100+ (per component the
@@ -399,12 +411,21 @@ template <class T> struct P2PFpt;
 template <> struct P2PFpt<float> { static constexpr int v = 8; };
 template <> struct P2PFpt<double> { static constexpr int v = 2; };
 
+// With tab.out64 set (the collocation K' product) each target's value goes
+// out in FP64 together with 4 pi times its row of the near-singular table
+// applied to tab.x: out64_i = near_i + 4 pi sum_e val_e x[col_e].
+struct NearTab {
+    const int *off, *col;
+    const double *val, *x;
+    double *out64;
+};
+
 // NB: the most neighbour leaves a leaf has (27 for one-cell separation, 125
 // for the charge tree's two cells).
 template <class T, int SRC, int TGT, int P2PF_THREADS, int NB = 27>
 __global__ void __launch_bounds__(P2PF_THREADS)
 k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
-      const typename V4T<T>::t *src, T h, T *out) {
+      const typename V4T<T>::t *src, const int *qpanel, const double *dens, T h, T *out, NearTab tab) {
     using V4 = typename V4T<T>::t;
     using P = Pk<T>;
     using v2 = typename P::v;
@@ -495,7 +516,7 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
                     a[0] = r.x + ox;
                     a[2] = r.y + oy;
                     b[0] = r.z + oz;
-                    b[2] = r.w;
+                    b[2] = src_strength<T, SRC>(r.w, sb + v, qpanel, dens);
                 }
             }
             if (((ve - vb) & 1) && threadIdx.x == 0) {  // odd tail: a zero-weight partner
@@ -541,7 +562,15 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
             const int gr = threadIdx.x / P2P_TPT, q = threadIdx.x - gr * P2P_TPT;
             T a = 0;
             for (int k = 0; k < G; ++k) a += s_part[(gr * G + k) * P2P_TPT + q];
-            out[tb + t0 + threadIdx.x] = DN ? -a : a;
+            const int i = tb + t0 + threadIdx.x;
+            if (tab.out64) {
+                double c = 0.0;
+                if (tab.off)
+                    for (int e = tab.off[i]; e < tab.off[i + 1]; ++e) c = fma(tab.val[e], tab.x[tab.col[e]], c);
+                tab.out64[i] = (double)(DN ? -a : a) + FOUR_PI * c;
+            } else {
+                out[i] = DN ? -a : a;
+            }
         }
     }
 }
@@ -1343,24 +1372,21 @@ k_translate(const T *__restrict__ ops, int nc, int cs, const int4 *__restrict__ 
 // strided by 16; input rows padded to 4 mod 32 words: at most 2-way bank
 // conflicts) and the results leave as coalesced atomic adds.
 template <class T, int BN, int NTH, int BM>
-__global__ void __launch_bounds__(NTH)
-k_tree_translate(const T *__restrict__ ops, int nc, int cs, int ldb, const int4 *__restrict__ chunks,
-                 const int *__restrict__ p_out, const int *__restrict__ p_in, const T *__restrict__ in,
-                 T *__restrict__ out) {
+__device__ __forceinline__ void tree_translate_block(const T *__restrict__ ops, int nc, int cs, int ldb, int4 ch,
+                                                     int rb, const int *__restrict__ p_out,
+                                                     const int *__restrict__ p_in, const T *__restrict__ in,
+                                                     T *__restrict__ out, unsigned char *smraw, int *s_in,
+                                                     int *s_out) {
     constexpr int TR_BM = BM;       // output rows of this CTA
     constexpr int NTY = TR_BM / 8;  // row groups of 8
     constexpr int NTX = NTH / NTY;  // column groups
     constexpr int CPT = BN / NTX;   // columns per thread
     static_assert(NTH % NTY == 0 && BN % NTX == 0, "tree translate tiling");
     constexpr int VEC = 16 / (int)sizeof(T);
-    extern __shared__ __align__(16) unsigned char smraw[];
     T *As = reinterpret_cast<T *>(smraw);  // [nc][TR_BM]
     T *Bs = As + (size_t)nc * TR_BM;       // [BN][ldb]
     T *Cs = As;                            // [BN][TR_BM + 1] (epilogue)
-    __shared__ int s_in[BN], s_out[BN];
-    const int4 ch = chunks[blockIdx.x];
     const T *Tt = ops + (size_t)ch.x * nc * cs;
-    const int rb = blockIdx.y * TR_BM;
     // a warp covers 8 pair columns x 4 row groups: its input-row loads hit 8
     // different banks and its operator loads one 128-byte span
     static_assert(NTX % 8 == 0, "tree translate thread map");
@@ -1426,6 +1452,17 @@ k_tree_translate(const T *__restrict__ ops, int nc, int cs, int ldb, const int4 
         const T *cj = Cs + j * (TR_BM + 1);
         for (int r = lane; r < rows; r += 32) atomicAdd(o + r, cj[r]);
     }
+}
+
+template <class T, int BN, int NTH, int BM>
+__global__ void __launch_bounds__(NTH)
+k_tree_translate(const T *__restrict__ ops, int nc, int cs, int ldb, const int4 *__restrict__ chunks,
+                 const int *__restrict__ p_out, const int *__restrict__ p_in, const T *__restrict__ in,
+                 T *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int s_in[BN], s_out[BN];
+    tree_translate_block<T, BN, NTH, BM>(ops, nc, cs, ldb, chunks[blockIdx.x], blockIdx.y * BM, p_out, p_in, in, out,
+                                         smraw, s_in, s_out);
 }
 
 // input-row pitch of k_tree_translate (4 mod 32 words) and its shared memory
@@ -1722,6 +1759,21 @@ static void tree_translate(const T *ops, int nc, int cs, int rblocks, const Tree
     BEM_CHECK_LAUNCH();
 }
 
+// One sweep of tree translations: M2M over the child levels L .. 3, or L2L
+// over 3 .. L, one launch per level.  (Measured: one launch for all levels,
+// with CTAs taking items in level order and waiting on per-level counters,
+// took 55 instead of 38 us for the M2M sweep of the 81,920-panel molecule:
+// a level's time is its items' own latency, not the launch gaps.)
+template <class T>
+static void tree_sweep(Mesh &m, const T *ops, int nc, int cs, const Tree &t, bool up, const T *in, T *out,
+                       cudaStream_t s) {
+    for (int k = 0; k + 3 <= t.L; ++k) {
+        const int c = up ? t.L - k : 3 + k;
+        tree_translate<T>(ops, nc, cs, cdiv(nc, TR_BM), t, up ? t.m2m_chunk0[c] : t.l2l_chunk0[c],
+                          up ? t.m2m_nchunk[c] : t.l2l_nchunk[c], in, out, s);
+    }
+}
+
 bool use_tc_m2l(const Mesh &m) {
     if (!tc_m2l_available(m)) return false;
     return m.opt.m2l_mode == BEM_M2L_TC || m.opt.m2l_mode == BEM_M2L_AUTO;
@@ -1731,9 +1783,16 @@ template <class T>
 static void m2l_dense(Mesh &m, const Tree &t, const T *Oop, int nc, int cs, int rblocks, size_t trsm,
                       T *M, T *L, bool timed = false);
 
+// With `apply` set (the collocation K' product), the pass ends in the
+// operator's epilogue y = x + Ehat (K'x + table x) instead of writing K'x.
+struct ApplyA {
+    const double *x;
+    double *y;
+};
+
 template <class T>
 static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const double *dens,
-                     double *out, bool timed) {
+                     double *out, bool timed, const ApplyA *apply = nullptr) {
     using B = PassBufs<T>;
     cudaStream_t s = m.stream;
     const TreeView tv = view(t);
@@ -1752,27 +1811,37 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
     if (tk == TGT_QUAD_DN && !nrec) throw Error(BEM_EUNSUPPORTED, "quadrature-point normals not built (galerkin = 0)");
     T *far_b = B::far(m), *near_b = B::near(m);
     ev_rec(m, timed, 0);
-    // strength records of this pass
-    typename V4T<T>::t *strec = B::str(m);
-    {
-        const int64_t ns = (sk == SRC_QUAD) ? m.nqp : m.nc;
-        if (sk == SRC_QUAD)
-            k_strength<T, SRC_QUAD><<<cdiv(ns, 256), 256, 0, s>>>(srec, m.qp_panel.p, dens, ns, strec);
-        else
-            k_strength<T, SRC_CHARGE><<<cdiv(ns, 256), 256, 0, s>>>(srec, nullptr, dens, ns, strec);
-        BEM_CHECK_LAUNCH();
-    }
+    const int *qpanel = m.qp_panel.p;
     // The near field (compute bound) runs on a second stream next to the far
     // field's chain of small, latency-bound launches; with phase timing on,
     // everything stays on one stream so each phase is timed alone.
     const bool conc = near && m.stream2 && !(timed && m.tm.on);
+    bool near_done = false, joined = false, epi_done = false;
+    if (timed) m.tm.near_before_l2p = false;
+    // The collocation product's epilogue: the near field carries the FP64
+    // near-singular table (out in FP64), L2P (or a last elementwise kernel)
+    // writes y = x + Ehat K' x.
+    const bool tab_on = apply && m.nt_nnz > 0 && !(m.opt.flags & (BEM_FLAG_NO_NEARTAB | BEM_FLAG_NO_NEAR));
+    NearTab ntab{nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (apply && near) {
+        if (m.near64.n < (size_t)m.np) throw Error(BEM_ECUDA, "near-field FP64 buffer missing");
+        ntab = NearTab{tab_on ? m.nt_off.p : nullptr, m.nt_col.p, m.nt_val.p, apply->x, m.near64.p};
+    }
     auto launch_near = [&](cudaStream_t ss) {
         const T hh = (T)h;
+        // strength records (P2M forms its own strengths)
+        typename V4T<T>::t *strec = B::str(m);
+        const int64_t ns = (sk == SRC_QUAD) ? m.nqp : m.nc;
+        if (ns > 0) {
+            if (sk == SRC_QUAD) k_strength<T, SRC_QUAD><<<cdiv(ns, 256), 256, 0, ss>>>(srec, qpanel, dens, ns, strec);
+            else k_strength<T, SRC_CHARGE><<<cdiv(ns, 256), 256, 0, ss>>>(srec, nullptr, dens, ns, strec);
+            BEM_CHECK_LAUNCH();
+        }
         // 128-thread CTAs when the average leaf holds at most 32 targets
         const bool small = ntgt <= (int64_t)32 * t.nleaf;
         auto go = [&](auto k128, auto k256) {
-            if (small) k128<<<t.nleaf, 128, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
-            else k256<<<t.nleaf, 256, 0, ss>>>(tv, trec, nrec, strec, hh, near_b);
+            if (small) k128<<<t.nleaf, 128, 0, ss>>>(tv, trec, nrec, strec, nullptr, nullptr, hh, near_b, ntab);
+            else k256<<<t.nleaf, 256, 0, ss>>>(tv, trec, nrec, strec, nullptr, nullptr, hh, near_b, ntab);
         };
         const bool wide = t.ws == 2;
         if (t.ws != 1 && t.ws != 2) throw Error(BEM_EUNSUPPORTED, "near field: separation not built");
@@ -1809,15 +1878,14 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
         const size_t trsm = translate_smem<T, TR_BN_M2L>();
         if (dense) set_smem<T>(k_translate<T, TR_BN_M2L, TR_THREADS>, trsm);
         // P2M
-        p2m_leaves<T>(tv, t.nleaf, sk, strec, p, cs, inv_h, M, s);
+        p2m_leaves<T>(tv, t.nleaf, sk, srec, qpanel, dens, p, cs, inv_h, M, s);
         ev_rec(m, timed, 1);
         // M2M: parents at levels L-1 .. 2
         if (dense) {
             if (t.L >= 3)
                 BEM_CUDA(cudaMemsetAsync(M + (size_t)t.lvl_off[2] * cs, 0,
                                          (size_t)(t.lvl_off[t.L] - t.lvl_off[2]) * cs * sizeof(T), s));
-            for (int c = t.L; c >= 3; --c)
-                tree_translate<T>(B::Om2m(tb), nc, cs, rblocks, t, t.m2m_chunk0[c], t.m2m_nchunk[c], M, M, s);
+            tree_sweep<T>(m, B::Om2m(tb), nc, cs, t, true, M, M, s);
         } else {
             const size_t sm = 2 * (size_t)(p + 1) * W * sizeof(cpx<T>);
             set_smem<T>(k_m2m<T>, sm);
@@ -1842,8 +1910,7 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
         ev_rec(m, timed, 3);
         // L2L: children at levels 3..L
         if (dense) {
-            for (int c = 3; c <= t.L; ++c)
-                tree_translate<T>(B::Ol2l(tb), nc, cs, rblocks, t, t.l2l_chunk0[c], t.l2l_nchunk[c], L, L, s);
+            tree_sweep<T>(m, B::Ol2l(tb), nc, cs, t, false, L, L, s);
         } else {
             const size_t sm = 2 * (size_t)(p + 1) * W * sizeof(cpx<T>);
             set_smem<T>(k_l2l<T>, sm);
@@ -1854,8 +1921,24 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             }
         }
         ev_rec(m, timed, 4);
-        // L2P
-        {
+        // L2P, carrying the epilogue when the product asks for it; the near
+        // field must then be complete (with phase timing on it runs here)
+        bool done = false;
+        if (apply) {
+            if (near && !conc) {
+                launch_near(s);
+                near_done = true;
+                ev_rec(m, timed, 5);
+                m.tm.near_before_l2p = true;
+            }
+            if (near && conc) BEM_CUDA(cudaStreamWaitEvent(s, m.ev_join, 0));
+            joined = true;
+            const ApplyEpi epi{apply->x, near ? m.near64.p : nullptr, apply->y, m.ehat};
+            done = epi_done = l2p_leaves_c<T>(tv, t.nleaf, l2p_threads(ntgt, t.nleaf), tk, p, trec, nrec, cs,
+                                              inv_h, L, far_b, s, epi);
+        }
+        if (!done && !l2p_leaves_c<T>(tv, t.nleaf, l2p_threads(ntgt, t.nleaf), tk, p, trec, nrec, cs, inv_h, L,
+                                      far_b, s)) {
             const size_t sm = (size_t)(p + 1) * W * sizeof(cpx<T>);
             if (tk == TGT_CEN_DN) {
                 auto kern = k_l2p<T, TGT_CEN_DN>;
@@ -1872,14 +1955,19 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
             }
             BEM_CHECK_LAUNCH();
         }
-        ev_rec(m, timed, 5);
+        ev_rec(m, timed, near_done ? 6 : 5);
     } else {
         for (int k = 1; k <= 5; ++k) ev_rec(m, timed, k);
     }
-    if (near && !conc) launch_near(s);
-    ev_rec(m, timed, 6);
-    if (near && conc) BEM_CUDA(cudaStreamWaitEvent(s, m.ev_join, 0));
-    if (tk == TGT_QUAD_DN) {
+    if (near && !conc && !near_done) launch_near(s);
+    if (!near_done) ev_rec(m, timed, 6);
+    if (near && conc && !joined) BEM_CUDA(cudaStreamWaitEvent(s, m.ev_join, 0));
+    if (epi_done) {
+        // y was written by L2P
+    } else if (apply) {
+        k_apply_far_near<T><<<cdiv(m.np, 256), 256, 0, s>>>(apply->x, far ? far_b : nullptr, near ? m.near64.p : nullptr,
+                                                            m.ehat, m.np, apply->y);
+    } else if (tk == TGT_QUAD_DN) {
         // Galerkin rows: the rule's average over each panel of its points' values
         build_qp_of_panel(m);
         k_panel_reduce<T><<<cdiv(m.np, 256), 256, 0, s>>>(far ? far_b : nullptr, near ? near_b : nullptr,
@@ -2168,16 +2256,17 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
         if (t.L >= 3)
             BEM_CUDA(cudaMemsetAsync(M + (size_t)t.lvl_off[2] * cs, 0,
                                      (size_t)(t.lvl_off[t.L] - t.lvl_off[2]) * cs * sizeof(T), s));
-        for (int c = t.L; c >= 3; --c)
-            tree_translate<T>(B::Om2m(tb), nc, cs, rblocks, t, t.m2m_chunk0[c], t.m2m_nchunk[c], M, M, s);
+        tree_sweep<T>(m, B::Om2m(tb), nc, cs, t, true, M, M, s);
         m2l_dense<T>(m, t, B::Om2l(tb), nc, cs, rblocks, trsm, M, L);
-        for (int c = 3; c <= t.L; ++c)
-            tree_translate<T>(B::Ol2l(tb), nc, cs, rblocks, t, t.l2l_chunk0[c], t.l2l_nchunk[c], L, L, s);
-        const size_t sm = (size_t)(p + 1) * (2 * p + 1) * sizeof(cpx<T>);
-        auto kern = k_l2p<T, TGT_QUAD_PHI>;
-        set_smem<T>(kern, sm);
-        kern<<<t.nleaf, l2p_threads(m.nqp, t.nleaf), sm, s>>>(tv, B::qp(m), B::nrm(m), p, cs, inv_h, L, far_b);
-        BEM_CHECK_LAUNCH();
+        tree_sweep<T>(m, B::Ol2l(tb), nc, cs, t, false, L, L, s);
+        if (!l2p_leaves_c<T>(tv, t.nleaf, l2p_threads(m.nqp, t.nleaf), TGT_QUAD_PHI, p, B::qp(m), B::nrm(m), cs,
+                             inv_h, L, far_b, s)) {
+            const size_t sm = (size_t)(p + 1) * (2 * p + 1) * sizeof(cpx<T>);
+            auto kern = k_l2p<T, TGT_QUAD_PHI>;
+            set_smem<T>(kern, sm);
+            kern<<<t.nleaf, l2p_threads(m.nqp, t.nleaf), sm, s>>>(tv, B::qp(m), B::nrm(m), p, cs, inv_h, L, far_b);
+            BEM_CHECK_LAUNCH();
+        }
     }
     if (near && !conc) launch_near(s);
     if (near && conc) BEM_CUDA(cudaStreamWaitEvent(s, m.ev_join, 0));
@@ -2187,7 +2276,8 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
 }
 
 // Whether a kernel (host stub address, as kernel graph nodes report it) is
-// one of the near-field kernels that run on the second, low-priority stream.
+// one of the near-field kernels (strength records, P2P) that run on the
+// second, low-priority stream.
 bool is_near_field_kernel(const void *func) {
     static const void *const near_kernels[] = {
         reinterpret_cast<const void *>(k_p2p<float, SRC_QUAD, TGT_CEN_DN, 128>),
@@ -2224,6 +2314,10 @@ bool is_near_field_kernel(const void *func) {
         reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CHG_PHI, 256, 125>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_QUAD_DN, 128, 125>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_QUAD_DN, 256, 125>),
+        reinterpret_cast<const void *>(k_strength<float, SRC_QUAD>),
+        reinterpret_cast<const void *>(k_strength<float, SRC_CHARGE>),
+        reinterpret_cast<const void *>(k_strength<double, SRC_QUAD>),
+        reinterpret_cast<const void *>(k_strength<double, SRC_CHARGE>),
         reinterpret_cast<const void *>(k_p2p_t<float>),
         reinterpret_cast<const void *>(k_p2p_t<double>),
     };
@@ -2235,6 +2329,12 @@ bool is_near_field_kernel(const void *func) {
 void fmm_pass_t(Mesh &m, const double *lam, double *out) {
     if (m.opt.precision == BEM_MIXED) run_pass_t<float>(m, lam, out);
     else run_pass_t<double>(m, lam, out);
+}
+
+void kprime_apply(Mesh &m, const double *xs, double *ys) {
+    const ApplyA a{xs, ys};
+    if (m.opt.precision == BEM_MIXED) run_pass<float>(m, m.tp, SRC_QUAD, TGT_CEN_DN, xs, nullptr, true, &a);
+    else run_pass<double>(m, m.tp, SRC_QUAD, TGT_CEN_DN, xs, nullptr, true, &a);
 }
 
 void fmm_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const double *dens, double *out,

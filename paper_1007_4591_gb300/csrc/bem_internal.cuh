@@ -186,6 +186,9 @@ struct Tables {
 
 struct Timers {
     bool on = false;
+    // the last timed product ran its near field before L2P (the epilogue
+    // fused into L2P): events 4-5 bracket P2P and 5-6 L2P
+    bool near_before_l2p = false;
     cudaEvent_t ev[8] = {};
     double ms[7] = {};
     cudaEvent_t kev[4] = {};  // inside the tensor-core M2L stage: split | kernel | sum
@@ -260,14 +263,15 @@ struct Mesh {
 
     // work vectors
     DArray<double> xs, ys, zs;         // sorted-order f64 vectors
+    DArray<double> near64;             // near field + 4 pi x near-singular table x (collocation product)
+    DArray<float4> str32;              // per-pass near-field source strength records (mixed)
+    DArray<double4> str64;             // (fp64 mode)
     DArray<float> far_f, near_f;       // per-target partial results (mixed)
     DArray<double> far_d, near_d;      // (fp64 mode)
     DArray<double> io_a, io_b;         // staging for host or unsorted arguments
     DArray<double> red;                // reduction scratch
     DArray<float> Mtc;                 // multipoles split hi|lo for the tensor-core M2L
     DArray<float> m2lR;                // per-pair M2L rows of the store-then-sum form
-    DArray<float4> str32;              // per-pass source strength records (mixed)
-    DArray<double4> str64;             // (fp64 mode)
     DArray<float> dpart_f;             // direct-sum partials (mixed)
     DArray<double> dpart_d;            // direct-sum partials (fp64)
     double *h_pinned = nullptr;        // small pinned host buffer
@@ -327,6 +331,9 @@ void compute_bbox(const double *d, int64_t n, int stride, double *lo, double *hi
 //   TGT_CHG_PHI: s / (4 pi |x_k - y|)
 void fmm_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const double *dens, double *out,
               bool timed);
+// The collocation operator product y = x + Ehat (K' x + table x) (sorted
+// order): the K' pass with its epilogue fused into the last kernel.
+void kprime_apply(Mesh &m, const double *xs, double *ys);
 // Transposed K' pass: out[j] = (K'^T lam)_j without the near-singular table
 // (dipoles lam_i n_i at the collocation points, potential at the quadrature
 // points, weighted sum over each panel's points).

@@ -78,11 +78,15 @@ __global__ void k_apply_A(const double *x, const double *kx, const int *nt_off, 
 }
 
 static void matvec_launch(Mesh &m, const double *xs, double *ys) {
-    const bool nt = m.nt_nnz > 0 && !(m.opt.flags & (BEM_FLAG_NO_NEARTAB | BEM_FLAG_NO_NEAR));
-    fmm_pass(m, m.tp, SRC_QUAD, m.opt.galerkin ? TGT_QUAD_DN : TGT_CEN_DN, xs, m.zs.p, true);
-    k_apply_A<<<cdiv(4 * m.np, 256), 256, 0, m.stream>>>(xs, m.zs.p, nt ? m.nt_off.p : nullptr,
-                                                      m.nt_col.p, m.nt_val.p, m.ehat, m.np, ys);
-    BEM_CHECK_LAUNCH();
+    if (!m.opt.galerkin) {
+        kprime_apply(m, xs, ys);  // the pass ends in the epilogue itself
+    } else {
+        const bool nt = m.nt_nnz > 0 && !(m.opt.flags & (BEM_FLAG_NO_NEARTAB | BEM_FLAG_NO_NEAR));
+        fmm_pass(m, m.tp, SRC_QUAD, TGT_QUAD_DN, xs, m.zs.p, true);
+        k_apply_A<<<cdiv(4 * m.np, 256), 256, 0, m.stream>>>(xs, m.zs.p, nt ? m.nt_off.p : nullptr,
+                                                          m.nt_col.p, m.nt_val.p, m.ehat, m.np, ys);
+        BEM_CHECK_LAUNCH();
+    }
     if (m.tm.on) BEM_CUDA(cudaEventRecord(m.tm.ev[7], m.stream));
 }
 
