@@ -73,10 +73,9 @@ extern "C" {
 #define BEM_FLAG_CHECK_CHARGES 8u /* bem_mesh_create rejects (BEM_EINVAL) a charge the surface
                                      does not enclose (winding number from the panels' solid
                                      angles; checked when n_c x n_p x 7 <= 4e10, skipped above) */
-#define BEM_FLAG_M2L_REDUCE 16u   /* tensor-core M2L: add each pair's row into its target with a
-                                     bulk reduction even where the per-pair rows (store, then a
-                                     fixed-order sum per target) would fit; the form used for
-                                     problems whose rows exceed 1 GiB */
+#define BEM_FLAG_M2L_REDUCE 16u   /* accepted for compatibility, no effect: the tensor-core M2L
+                                     always adds each pair's row into its target cell with
+                                     vector reductions (no per-pair buffer) */
 
 /* bem_options.near_table */
 #define BEM_NEAR_QUADRATURE 1
@@ -282,10 +281,18 @@ int bem_last_phase_ms(const bem_mesh *mesh, double *times);
 
 /* Inside the M2L phase of the last profiled bem_matvec with the tensor-core
  * M2L: device time (ms) of the multipole split (k_split_m), of the
- * tensor-core kernel (k_m2l_tc) and of the per-target sum (k_m2l_sum; 0 in
- * the reduction form).  times[3]; zeros if the product had no tensor-core M2L.
- * BEM_EINVAL if profiling is off. */
+ * tensor-core kernel (k_m2l_tc, which adds the rows into their targets) and
+ * a third entry kept at 0 (there is no separate summation kernel).
+ * times[3]; zeros if the product had no tensor-core M2L.  BEM_EINVAL if
+ * profiling is off. */
 int bem_last_m2l_ms(const bem_mesh *mesh, double *times);
+
+/* Inside the P2P phase of the last profiled bem_matvec: device time (ms) of
+ * the near field's source strength records (k_strength) and of the
+ * near-field kernel itself (k_p2p, with the near-singular table of the
+ * collocation product).  times[2]; zeros if the product had no near field.
+ * BEM_EINVAL if profiling is off. */
+int bem_last_near_ms(const bem_mesh *mesh, double *times);
 
 /* Message for the calling thread's last error (static storage, never NULL). */
 const char *bem_last_error(void);

@@ -98,6 +98,7 @@ _SIGS = {
     "bem_set_device_memory_cap": [ctypes.c_size_t],
     "bem_last_phase_ms": [_vp, _vp],
     "bem_last_m2l_ms": [_vp, _vp],
+    "bem_last_near_ms": [_vp, _vp],
     "bem_last_error": [],
     "bem_batch_solve": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
     "bem_normal_field_noalloc": [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp, _vp],
@@ -264,7 +265,13 @@ def bem_last_phase_ms(h):
 def bem_last_m2l_ms(h):
     t = np.zeros(3)
     _check(load_library().bem_last_m2l_ms(h, _ptr(t)), "bem_last_m2l_ms")
-    return dict(zip(["split", "tc", "sum"], t.tolist()))
+    return dict(zip(["split", "tc"], t.tolist()[:2]))
+
+
+def bem_last_near_ms(h):
+    t = np.zeros(2)
+    _check(load_library().bem_last_near_ms(h, _ptr(t)), "bem_last_near_ms")
+    return dict(zip(["strength", "p2p"], t.tolist()))
 
 
 def bem_batch_solve(meshes, threads: int = 8, sigmas=None):

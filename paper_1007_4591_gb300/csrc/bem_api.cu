@@ -133,7 +133,7 @@ size_t Mesh::bytes() const {
     if (tab) b += tab->bytes();
     if (tab2) b += tab2->bytes();
     b += Mf.bytes() + Lf.bytes() + Md.bytes() + Ld.bytes();
-    b += Mtc.bytes() + m2lR.bytes() + ctq.bytes() + str32.bytes() + str64.bytes() + near64.bytes() + dpart_f.bytes() +
+    b += Mtc.bytes() + ctq.bytes() + str32.bytes() + str64.bytes() + near64.bytes() + dpart_f.bytes() +
          dpart_d.bytes();
     b += xs.bytes() + ys.bytes() + zs.bytes() + far_f.bytes() + near_f.bytes() + far_d.bytes() +
          near_d.bytes() + io_a.bytes() + io_b.bytes() + red.bytes();
@@ -166,7 +166,6 @@ static void alloc_work(Mesh &m) {
     }
     if (tc_m2l_available(m)) {
         ensure(m.Mtc, tc_staging_floats(m));
-        ensure(m.m2lR, m2l_store_floats(m));
     }
     const size_t nsrc = (size_t)std::max<int64_t>(m.nqp, m.nc);
     if (m.opt.precision == BEM_MIXED) ensure(m.str32, nsrc);
@@ -313,6 +312,8 @@ int bem_mesh_destroy(bem_mesh *m) {
         for (auto &e : m->tm.ev)
             if (e) cudaEventDestroy(e);
         for (auto &e : m->tm.kev)
+            if (e) cudaEventDestroy(e);
+        for (auto &e : m->tm.nev)
             if (e) cudaEventDestroy(e);
         if (m->h_pinned) cudaFreeHost(m->h_pinned);
         if (m->g_mv) cudaGraphExecDestroy(m->g_mv);
@@ -579,6 +580,7 @@ int bem_set_profiling(bem_mesh *m, int enable) {
         if (enable && !m->tm.ev[0]) {
             for (auto &e : m->tm.ev) BEM_CUDA(cudaEventCreate(&e));
             for (auto &e : m->tm.kev) BEM_CUDA(cudaEventCreate(&e));
+            for (auto &e : m->tm.nev) BEM_CUDA(cudaEventCreate(&e));
         }
         m->tm.on = enable != 0;
     });
@@ -618,6 +620,23 @@ int bem_last_m2l_ms(const bem_mesh *m, double *times) {
         float ms = 0;
         if (cudaEventElapsedTime(&ms, m->tm.kev[k], m->tm.kev[k + 1]) != cudaSuccess) {
             cudaGetLastError();  // not recorded (no tensor-core M2L in the last product)
+            ms = 0;
+        }
+        times[k] = ms;
+    }
+    return BEM_OK;
+}
+
+int bem_last_near_ms(const bem_mesh *m, double *times) {
+    if (!m || !times) return BEM_EINVAL;
+    if (!m->tm.on || !m->tm.nev[0]) {
+        set_last_error("profiling is off");
+        return BEM_EINVAL;
+    }
+    for (int k = 0; k < 2; ++k) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, m->tm.nev[k], m->tm.nev[k + 1]) != cudaSuccess) {
+            cudaGetLastError();  // not recorded (no near field in the last product)
             ms = 0;
         }
         times[k] = ms;

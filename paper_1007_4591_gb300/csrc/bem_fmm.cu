@@ -1497,20 +1497,14 @@ __global__ void k_class_count(const int *key, int64_t n, int *cnt) {
 }
 
 // grouped pair d is list entry e = perm[d]
-__global__ void k_gather_pairs(const int *perm, const int *po, const int *pi, int64_t n, int *g_out, int *g_in,
-                               int *rank) {
+__global__ void k_gather_pairs(const int *perm, const int *po, const int *pi, int64_t n, int *g_out, int *g_in) {
     const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (d >= n) return;
     const int e = perm[d];
     g_out[d] = po[e];
     g_in[d] = pi[e];
-    rank[e] = (int)d;
 }
 
-__global__ void k_shift_offsets(const int *off, int n, int *out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = off[i] - off[0];
-}
 
 // Group the translations of a tree by operator and cut them into chunks.
 __global__ void k_m2l_pairs(const int *m2l_off, int first, int last, const int *m2l_src,
@@ -1581,7 +1575,6 @@ void build_translation_groups(Mesh &m, Tree &t) {
     while ((1 << cls_bits) < ncls) ++cls_bits;
     std::vector<int4> chunks;
     std::vector<int> cnt(ncls, 0);
-    DArray<int> rank;  // rank[e] = position of list entry e in the grouped order
     const int first = t.lvl_off[2], last = t.ncell;
     if (nm > 0) {
         DArray<int> po, pi, key, idx, key_s, perm, dcnt;
@@ -1592,7 +1585,6 @@ void build_translation_groups(Mesh &m, Tree &t) {
         key_s.alloc(nm);
         perm.alloc(nm);
         dcnt.alloc(ncls);
-        rank.alloc(nm);
         k_m2l_pairs<<<cdiv(last - first, 256), 256, 0, s>>>(t.m2l_off.p, first, last, t.m2l_src.p,
                                                           t.m2l_ofs.p, po.p, pi.p, key.p);
         BEM_CHECK_LAUNCH();
@@ -1606,7 +1598,7 @@ void build_translation_groups(Mesh &m, Tree &t) {
         // the M2L part of the grouped arrays (the tree translations are appended below)
         t.g_out.alloc(nm);
         t.g_in.alloc(nm);
-        k_gather_pairs<<<cdiv(nm, 256), 256, 0, s>>>(perm.p, po.p, pi.p, nm, t.g_out.p, t.g_in.p, rank.p);
+        k_gather_pairs<<<cdiv(nm, 256), 256, 0, s>>>(perm.p, po.p, pi.p, nm, t.g_out.p, t.g_in.p);
         BEM_CHECK_LAUNCH();
         BEM_CUDA(cudaStreamSynchronize(s));
         std::vector<int64_t> start(ncls + 1, 0);
@@ -1617,17 +1609,6 @@ void build_translation_groups(Mesh &m, Tree &t) {
     }
     t.m2l_nchunk = (int)chunks.size();
     build_tc_super(t, chunks, s);
-    // pairs by target cell for the store-then-sum tensor-core M2L: the list
-    // is target-major, so the CSR is the list's own offsets and each entry
-    // the pair's grouped position
-    t.m2l_store = use_tc_m2l(m) && m2l_store_fits(nm, m.opt.p) && !(m.opt.flags & BEM_FLAG_M2L_REDUCE);
-    if (t.m2l_store) {
-        const int ncl = last - first;
-        t.m2l_toff.alloc(ncl + 1);
-        k_shift_offsets<<<cdiv(ncl + 1, 256), 256, 0, s>>>(t.m2l_off.p + first, ncl + 1, t.m2l_toff.p);
-        BEM_CHECK_LAUNCH();
-        t.m2l_tpairs = std::move(rank);
-    }
     // M2M (out parent, in child) and L2L (out child, in parent) per child level
     std::vector<int> h_out, h_in;
     for (int c = 3; c <= L; ++c) {
@@ -1832,11 +1813,14 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
         // strength records (P2M forms its own strengths)
         typename V4T<T>::t *strec = B::str(m);
         const int64_t ns = (sk == SRC_QUAD) ? m.nqp : m.nc;
+        const bool tn = timed && m.tm.on && m.tm.nev[0];
+        if (tn) BEM_CUDA(cudaEventRecord(m.tm.nev[0], ss));
         if (ns > 0) {
             if (sk == SRC_QUAD) k_strength<T, SRC_QUAD><<<cdiv(ns, 256), 256, 0, ss>>>(srec, qpanel, dens, ns, strec);
             else k_strength<T, SRC_CHARGE><<<cdiv(ns, 256), 256, 0, ss>>>(srec, nullptr, dens, ns, strec);
             BEM_CHECK_LAUNCH();
         }
+        if (tn) BEM_CUDA(cudaEventRecord(m.tm.nev[1], ss));
         // 128-thread CTAs when the average leaf holds at most 32 targets
         const bool small = ntgt <= (int64_t)32 * t.nleaf;
         auto go = [&](auto k128, auto k256) {
@@ -1863,6 +1847,7 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
         } else
             throw Error(BEM_EUNSUPPORTED, "near field: source/target combination not built");
         BEM_CHECK_LAUNCH();
+        if (tn) BEM_CUDA(cudaEventRecord(m.tm.nev[2], ss));
     };
     if (conc) {
         BEM_CUDA(cudaEventRecord(m.ev_fork, s));

@@ -133,11 +133,6 @@ struct Tree {
     DArray<int> p2p_order;        // leaves by decreasing near-field work (launch order)
     DArray<int4> tc_super;        // tensor-core M2L work items (offset, first chunk, chunks)
     int tc_nsuper = 0;
-    // M2L pairs by target cell (levels >= 2, CSR over cell - lvl_off[2]; each
-    // entry a pair's position in the grouped order) for the store-then-sum
-    // form of the tensor-core M2L
-    DArray<int> m2l_toff, m2l_tpairs;
-    bool m2l_store = false;
     int m2l_chunk0 = 0, m2l_nchunk = 0;
     std::vector<int> m2m_chunk0, m2m_nchunk, l2l_chunk0, l2l_nchunk; // indexed by child level
     size_t bytes() const;
@@ -191,7 +186,8 @@ struct Timers {
     bool near_before_l2p = false;
     cudaEvent_t ev[8] = {};
     double ms[7] = {};
-    cudaEvent_t kev[4] = {};  // inside the tensor-core M2L stage: split | kernel | sum
+    cudaEvent_t kev[4] = {};  // inside the tensor-core M2L stage: split | kernel | (unused)
+    cudaEvent_t nev[3] = {};  // inside the near-field phase: strength records | near-field kernel
 };
 
 struct Mesh {
@@ -271,7 +267,6 @@ struct Mesh {
     DArray<double> io_a, io_b;         // staging for host or unsorted arguments
     DArray<double> red;                // reduction scratch
     DArray<float> Mtc;                 // multipoles split hi|lo for the tensor-core M2L
-    DArray<float> m2lR;                // per-pair M2L rows of the store-then-sum form
     DArray<float> dpart_f;             // direct-sum partials (mixed)
     DArray<double> dpart_d;            // direct-sum partials (fp64)
     double *h_pinned = nullptr;        // small pinned host buffer
@@ -317,10 +312,6 @@ void build_tc_super(Tree &t, const std::vector<int4> &chunks_m2l, cudaStream_t s
 void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed = false);
 bool use_tc_m2l(const Mesh &m);
 size_t tc_staging_floats(const Mesh &m);
-size_t m2l_store_floats(const Mesh &m);
-// the per-pair rows of the store-then-sum M2L stay below this size
-constexpr size_t TC_STORE_MAX_BYTES = (size_t)1 << 30;
-bool m2l_store_fits(int64_t npairs, int p);
 void compute_bbox(const double *d, int64_t n, int stride, double *lo, double *hi, cudaStream_t s);
 
 // fast multipole passes (bem_fmm.cu).  `dens` is indexed in sorted panel

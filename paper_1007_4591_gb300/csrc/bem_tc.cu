@@ -13,11 +13,12 @@
 // 128-byte swizzle, so that a warp's copy instruction reads four whole
 // 128-byte rows from global memory.  A persistent, warp-specialised kernel
 // runs the pairs of one class as a stream of 128-pair tiles (producers, one
-// MMA thread, epilogue; see k_m2l_tc).  The epilogue either stores each
-// tile's 128 local-expansion rows with one bulk copy into a per-pair buffer
-// that k_m2l_sum then adds up per target cell in a fixed order (no atomics;
-// used while that buffer fits), or adds each row into its target with a
-// bulk asynchronous reduction.  Every wait is bounded: the pipeline waits by
+// MMA thread, epilogue; see k_m2l_tc).  The epilogue adds each pair's
+// local-expansion row into its target cell with vector reductions
+// (red.global.add.v4.f32): the targets' local expansions (a few MB) stay in
+// L2, which absorbs the reductions at about the rate HBM would take the rows
+// (measured 4.9 TB/s against 5.5 TB/s for plain stores), and no per-pair
+// buffer is written or read back.  Every wait is bounded: the pipeline waits by
 // the mesh's wait budget (bem_set_wait_budget), after which the kernel
 // raises an error flag; the last wait for its own MMAs (always about a
 // second) comes before it frees its tensor memory and returns.
@@ -136,10 +137,8 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *g, uint32_t bytes) 
 //    last K-block it commits to fullD.
 //  * epilogue (warps 1-4): reads its TMEM lane quadrant, frees the
 //    accumulator, transposes the tile into shared memory rows (one local
-//    expansion row of cs floats per pair) and either stores the 128 rows
-//    with one bulk copy at the tile's first pair in `out` (STORE) or adds
-//    each row into its target cell of `out` with one bulk reduction.
-template <bool STORE>
+//    expansion row of cs floats per pair), then the 128 threads add the rows
+//    into their target cells of `out`, four coefficients per reduction.
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
          const int4 *__restrict__ items, int nitems, int *__restrict__ next_item,
@@ -370,7 +369,8 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
         // ---------------- epilogue: TMEM lane quadrant (warp % 4), 128 pairs per tile
         const int quad = warp & 3;
         const int row = 32 * quad + lane;
-        const bool issuer = warp == TC_WARP_EPI0;  // its lanes issue the bulk copies
+        const int etid = tid - TC_WARP_EPI0 * 32;  // 0 .. TC_NEPI - 1
+        __shared__ int s_tgt[TC_BN];               // target cells of the tile's pairs
         bool fail = false;
         int t = 0;
         for (int i = 0; !fail; ++i) {
@@ -403,10 +403,11 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                     fail = true;
                     break;
                 }
-                // the previous tile's bulk copies have finished reading Ct
-                if (issuer) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                // every thread has left the previous tile's reductions (Ct, s_tgt free)
                 asm volatile("bar.sync 1, %0;" ::"n"(TC_NEPI) : "memory");
                 asm volatile("tcgen05.fence::after_thread_sync;");
+                const int y = sc.y + TC_BN * c, z = min(TC_BN, sc.z - TC_BN * c);
+                if (etid < z) s_tgt[etid] = p_out[y + etid];
 #pragma unroll 1
                 for (int cg = 0; cg < TC_BN; cg += 32) {
                     uint32_t r[32];
@@ -427,30 +428,19 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 mbar_arrive(smem_u32(&emptyD[d]));
-                // generic-proxy writes of Ct before the bulk copies (async proxy) read it
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("bar.sync 1, %0;" ::"n"(TC_NEPI) : "memory");
-                if (issuer) {
-                    const int y = sc.y + TC_BN * c, z = min(TC_BN, sc.z - TC_BN * c);
-                    if (STORE) {
-                        if (lane == 0)
-                            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
-                                             out + (size_t)y * cs),
-                                         "r"(smem_u32(Ct)), "r"((uint32_t)(z * cs * 4))
-                                         : "memory");
-                    } else {
-                        for (int j = lane; j < z; j += 32)
-                            asm volatile(
-                                "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
-                                    out + (size_t)p_out[y + j] * cs),
-                                "r"(smem_u32(Ct + j * cs)), "r"((uint32_t)cs * 4u)
-                                : "memory");
-                    }
-                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                // every pair's row added into its target cell, four coefficients per
+                // vector reduction, spread over the epilogue threads
+                const int q4 = cs >> 2;
+                for (int idx = etid; idx < z * q4; idx += TC_NEPI) {
+                    const int j = idx / q4, q = idx - j * q4;
+                    const float4 v = *reinterpret_cast<const float4 *>(Ct + j * cs + 4 * q);
+                    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(out + (size_t)s_tgt[j] * cs + 4 * q),
+                                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                                 : "memory");
                 }
             }
         }
-        if (issuer) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     // before the CTA's shared memory and tensor memory go away, every commit
     // arrival must have landed: the MMA thread waits (bounded) for the last
@@ -473,33 +463,6 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(TC_TMEM_COLS));
-}
-
-// L_c = sum of the rows R_j of the M2L pairs j whose target is cell c, in
-// increasing j (one warp per cell, float4 lanes); cells without pairs get 0.
-__global__ void k_m2l_sum(const float4 *__restrict__ R, const int *__restrict__ toff,
-                          const int *__restrict__ tpairs, int first, int ncell, int cs4,
-                          float4 *__restrict__ L) {
-    const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (first + w >= ncell) return;
-    const int b = toff[w], e = toff[w + 1];
-    for (int j = lane; j < cs4; j += 32) {
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        int q = b;
-        for (; q + 4 <= e; q += 4) {
-            const float4 u0 = R[(size_t)tpairs[q] * cs4 + j], u1 = R[(size_t)tpairs[q + 1] * cs4 + j];
-            const float4 u2 = R[(size_t)tpairs[q + 2] * cs4 + j], u3 = R[(size_t)tpairs[q + 3] * cs4 + j];
-            a.x += u0.x; a.y += u0.y; a.z += u0.z; a.w += u0.w;
-            a.x += u1.x; a.y += u1.y; a.z += u1.z; a.w += u1.w;
-            a.x += u2.x; a.y += u2.y; a.z += u2.z; a.w += u2.w;
-            a.x += u3.x; a.y += u3.y; a.z += u3.z; a.w += u3.w;
-        }
-        for (; q < e; ++q) {
-            const float4 u = R[(size_t)tpairs[q] * cs4 + j];
-            a.x += u.x; a.y += u.y; a.z += u.z; a.w += u.w;
-        }
-        L[(size_t)(first + w) * cs4 + j] = a;
-    }
 }
 
 // ---------------------------------------------------------------- host side
@@ -578,25 +541,16 @@ __global__ void k_split_m(const float *M, int first, int ncell, int nc, int cs, 
     }
 }
 
-bool m2l_store_fits(int64_t npairs, int p) {
-    return npairs > 0 && (double)npairs * cell_stride(p) * sizeof(float) <= (double)TC_STORE_MAX_BYTES;
-}
-
-// L (levels >= 2) = sum over the M2L pairs of T_o M_s.  STORE: per-pair rows
-// into the mesh's buffer, then a fixed-order sum per target (deterministic);
-// otherwise L is cleared and the rows are added by bulk reductions.
+// L (levels >= 2) = sum over the M2L pairs of T_o M_s: L cleared, the
+// multipoles split hi | lo, then the persistent kernel adds every pair's row
+// into its target.
 void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed) {
     const Tables &tb = tables_for(m, t);
     const int nc = (m.opt.p + 1) * (m.opt.p + 1);
     const int cs = cell_stride(m.opt.p);
     const int first = t.lvl_off[2];
-    const bool store = t.m2l_store && m.m2lR.n >= (size_t)t.nm2l * cs;
-    if (!store)
-        BEM_CUDA(cudaMemsetAsync(L + (size_t)first * cs, 0, (size_t)(t.ncell - first) * cs * sizeof(float), m.stream));
-    if (t.tc_nsuper == 0) {
-        if (store) BEM_CUDA(cudaMemsetAsync(L + (size_t)first * cs, 0, (size_t)(t.ncell - first) * cs * sizeof(float), m.stream));
-        return;
-    }
+    BEM_CUDA(cudaMemsetAsync(L + (size_t)first * cs, 0, (size_t)(t.ncell - first) * cs * sizeof(float), m.stream));
+    if (t.tc_nsuper == 0) return;
     if (m.Mtc.n < (size_t)t.ncell * 2 * TC_K) throw Error(BEM_ECUDA, "tensor-core staging buffer too small");
     const bool tk = timed && m.tm.on && m.tm.kev[0];
     auto kev = [&](int k) {
@@ -612,39 +566,17 @@ void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed) {
     const int grid = std::max(1, std::min(t.tc_nsuper, nsm));
     BEM_CUDA(cudaMemsetAsync(m.dev_err.p + 1, 0, sizeof(int), m.stream));  // work-item counter
     kev(1);
-    if (store) {
-        ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc<true>), sm);
-        k_m2l_tc<true><<<grid, TC_THREADS, sm, m.stream>>>(tb.Tc_hi.p, tb.Tc_lo.p, t.tc_super.p, t.tc_nsuper,
-                                                           m.dev_err.p + 1, t.g_out.p, t.g_in.p, cs, m.Mtc.p,
-                                                           m.m2lR.p, m.dev_err.p, m.wait_budget);
-        BEM_CHECK_LAUNCH();
-        kev(2);
-        const int ncl = t.ncell - first;
-        k_m2l_sum<<<cdiv((int64_t)ncl * 32, 256), 256, 0, m.stream>>>(
-            reinterpret_cast<const float4 *>(m.m2lR.p), t.m2l_toff.p, t.m2l_tpairs.p, first, t.ncell, cs / 4,
-            reinterpret_cast<float4 *>(L));
-        BEM_CHECK_LAUNCH();
-        kev(3);
-    } else {
-        ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc<false>), sm);
-        k_m2l_tc<false><<<grid, TC_THREADS, sm, m.stream>>>(tb.Tc_hi.p, tb.Tc_lo.p, t.tc_super.p, t.tc_nsuper,
-                                                            m.dev_err.p + 1, t.g_out.p, t.g_in.p, cs, m.Mtc.p, L,
-                                                            m.dev_err.p, m.wait_budget);
-        BEM_CHECK_LAUNCH();
-        kev(2);
-        kev(3);
-    }
+    ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc), sm);
+    k_m2l_tc<<<grid, TC_THREADS, sm, m.stream>>>(tb.Tc_hi.p, tb.Tc_lo.p, t.tc_super.p, t.tc_nsuper, m.dev_err.p + 1,
+                                                 t.g_out.p, t.g_in.p, cs, m.Mtc.p, L, m.dev_err.p, m.wait_budget);
+    BEM_CHECK_LAUNCH();
+    kev(2);
+    kev(3);
 }
 
 size_t tc_staging_floats(const Mesh &m) {
     return (size_t)std::max(m.tp.ncell, m.tc.ncell) * 2 * TC_K;
 }
 
-size_t m2l_store_floats(const Mesh &m) {
-    size_t n = 0;
-    for (const Tree *t : {&m.tp, &m.tc})
-        if (t->m2l_store) n = std::max(n, (size_t)t->nm2l * cell_stride(m.opt.p));
-    return n;
-}
 
 }  // namespace bem

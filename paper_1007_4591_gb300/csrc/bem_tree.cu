@@ -691,7 +691,7 @@ size_t Tree::bytes() const {
     return g_out.bytes() + g_in.bytes() + g_chunk.bytes() + p2p_order.bytes() + tc_super.bytes() +
            key.bytes() + ijk.bytes() + parent.bytes() + child_beg.bytes() + child_end.bytes() +
            cen_beg.bytes() + qp_beg.bytes() + chg_beg.bytes() + nbr_off.bytes() + nbr.bytes() +
-           m2l_off.bytes() + m2l_src.bytes() + m2l_ofs.bytes() + m2l_toff.bytes() + m2l_tpairs.bytes();
+           m2l_off.bytes() + m2l_src.bytes() + m2l_ofs.bytes();
 }
 
 TreeView view(const Tree &t) {

@@ -75,11 +75,11 @@ def test_tensor_core_m2l_matches_simt(pkg, small4):
     close(ys[1] - x, ys[0] - x, 2e-6, inf=2e-5)
 
 
-def test_tensor_core_m2l_epilogues_agree(pkg, small4):
-    """The two epilogues of the tensor-core M2L: per-pair rows stored and
-    summed per target in a fixed order (the default), and bulk reductions into
-    the targets (BEM_FLAG_M2L_REDUCE, the form for rows above 1 GiB); both
-    against the dense FP64 oracle."""
+def test_tensor_core_m2l_repeats_to_summation_order(pkg, small4):
+    """The tensor-core M2L adds every pair's row into its target with vector
+    reductions (and BEM_FLAG_M2L_REDUCE, kept for compatibility, changes
+    nothing): repeated products agree to the order of the FP32 additions, and
+    both match the dense FP64 oracle."""
     m, P = small4
     x = np.random.default_rng(12).standard_normal(m.n_p)
     ref = P.A(x)
@@ -88,8 +88,10 @@ def test_tensor_core_m2l_epilogues_agree(pkg, small4):
         with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=4, p=10, m2l_mode=3,
                       flags=flags) as g:
             ys.append(g.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
+            ys.append(g.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
         close(ys[-1], ref, 1e-5)
-    close(ys[1] - x, ys[0] - x, 1e-6, inf=1e-5)
+    for y in ys[1:]:
+        close(y - x, ys[0] - x, 1e-6, inf=1e-5)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
