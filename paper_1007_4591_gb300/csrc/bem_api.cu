@@ -72,16 +72,17 @@ static void enter(Mesh &m) {
     BEM_CUDA(cudaStreamWaitEvent(m.stream, m.ev_enter, 0));
 }
 
-// Synchronise the mesh's stream and report a bounded device wait that ran out.
+// Synchronise the mesh's stream and report a bounded device wait that ran
+// out (the error word comes back in the same synchronisation).
 static void sync(Mesh &m) {
+    int *flag = reinterpret_cast<int *>(m.h_pinned + 7);  // the pinned buffer's last 8 bytes
+    if (m.dev_err.p) BEM_CUDA(cudaMemcpyAsync(flag, m.dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, m.stream));
     BEM_CUDA(cudaStreamSynchronize(m.stream));
-    if (m.dev_err.p) {
-        int e = 0;
-        BEM_CUDA(cudaMemcpy(&e, m.dev_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-        if (e) {
-            BEM_CUDA(cudaMemset(m.dev_err.p, 0, sizeof(int)));
-            throw Error(BEM_ETIMEOUT, "a bounded device wait ran out (tensor-core M2L)");
-        }
+    if (m.dev_err.p && *flag) {
+        *flag = 0;
+        BEM_CUDA(cudaMemsetAsync(m.dev_err.p, 0, sizeof(int), m.stream));
+        BEM_CUDA(cudaStreamSynchronize(m.stream));
+        throw Error(BEM_ETIMEOUT, "a bounded device wait ran out (tensor-core M2L)");
     }
 }
 
