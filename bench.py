@@ -45,6 +45,69 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (the driver's
+    libnvidia-ml, read-only queries) every ~0.5 ms in a background thread:
+    the timed region of the product is milliseconds long, shorter than
+    nvidia-smi's sampling period.  The device is matched to the CUDA device
+    by its UUID."""
+
+    # clock event reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x40: "sw_thermal_slowdown",
+               0x80: "hw_thermal_slowdown", 0x100: "hw_power_brake_slowdown"}
+
+    def __init__(self, uuid):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.dev)) != 0:
+            raise RuntimeError("no NVML device for " + uuid)
+        self.get_reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, ctypes.byref(mx)) == 0 \
+            else None
+        self.samples, self.reasons, self.run = [], 0, False
+
+    def _loop(self):
+        c = self.ct.c_uint()
+        r = self.ct.c_ulonglong()
+        while self.run:
+            if self.lib.nvmlDeviceGetClockInfo(self.dev, 1, self.ct.byref(c)) == 0:
+                self.samples.append(float(c.value))
+            if self.get_reasons(self.dev, self.ct.byref(r)) == 0:
+                self.reasons |= int(r.value)
+            time.sleep(0.0005)
+
+    def start(self):
+        self.run = True
+        self.t = threading.Thread(target=self._loop, daemon=True)
+        self.t.start()
+        while not self.samples and self.t.is_alive():
+            time.sleep(0.0002)
+
+    def stop(self):
+        self.run = False
+        self.t.join(timeout=2)
+        self.lib.nvmlShutdown()
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(v for k, v in self.REASONS.items() if self.reasons & k),
+                "samples": len(self.samples), "source": "NVML, every ~0.5 ms during the timed region"}
+
+
+def clock_sampler(local):
+    """NVML sampling when the driver library answers, else nvidia-smi."""
+    try:
+        import torch
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        return NvmlSampler(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+    except Exception:
+        return ClockSampler(local)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -353,7 +416,7 @@ def run_ours(args):
         pkg.bem_matvec(mesh.h, x, y)
     torch.cuda.synchronize()
     # timed region: K products, L2 flushed between products (outside the events)
-    clk = ClockSampler(local)
+    clk = clock_sampler(local)
     clk.start()
     _barrier(ws)
     torch.cuda.synchronize()

@@ -161,7 +161,9 @@ int bem_options_default(bem_options *opt);
  * Computes panel geometry and quadrature points, Morton keys and sort, the
  * octree, neighbour and interaction lists, translation tables and the FP64
  * near-singular table, all on the device.  Errors: BEM_EINVAL for NaN/Inf
- * coordinates, zero-area panels, eps <= 0, n_p <= 0, bad options. */
+ * coordinates, zero-area panels, eps <= 0, n_p <= 0, bad options.  With the
+ * environment variable BEM_TIMING=1 the build steps' wall times are printed
+ * to stderr (diagnostics). */
 int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, int64_t n_c,
                     double eps_in, double eps_out, const bem_options *opt, void *stream,
                     bem_mesh **out);

@@ -185,6 +185,7 @@ __global__ void k_apply_At(const double *x, const double *ktx, const int *off, c
 void matvec_t_sorted(Mesh &m, const double *xs, double *ys) {
     if (m.opt.galerkin) throw Error(BEM_EUNSUPPORTED, "the transposed product is not built for the Galerkin form");
     const bool nt = m.nt_nnz > 0 && !(m.opt.flags & (BEM_FLAG_NO_NEARTAB | BEM_FLAG_NO_NEAR));
+    if (nt) transpose_near_table(m);
     fmm_pass_t(m, xs, m.zs.p);
     k_apply_At<<<cdiv(4 * m.np, 256), 256, 0, m.stream>>>(xs, m.zs.p, nt ? m.ntT_off.p : nullptr,
                                                        m.ntT_col.p, m.ntT_val.p, m.ehat, m.np, ys);

@@ -6,6 +6,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <cstdio>
+#include <cstdlib>
 #include <string>
 
 #include <atomic>
@@ -274,17 +276,27 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
         m->ehat = 2.0 * (eps_in - eps_out) / (eps_in + eps_out);
         BEM_CUDA(cudaMallocHost((void **)&m->h_pinned, 64));
         DArray<double> sp, sc;
+        // BEM_TIMING=1: the build steps' wall times on stderr (diagnostics)
+        StepTimer st(m->stream);
         const double *dp = dev_in(*m, panels, (size_t)n_p * 9, sp);
         const double *dc = n_c > 0 ? dev_in(*m, charges, (size_t)n_c * 4, sc) : nullptr;
+        st.mark("inputs to the device");
         build_geometry_and_trees(*m, dp, dc);
+        st.mark("geometry, Morton sort, trees, lists");
         if (m->opt.galerkin) build_galerkin_geometry(*m);
         build_tables(*m);
+        st.mark("translation tables");
         build_translation_groups(*m, m->tp);
+        st.mark("panel tree: translation groups, near-field order");
         build_translation_groups(*m, m->tc);
+        st.mark("charge tree: translation groups, near-field order");
         alloc_work(*m);
+        st.mark("work buffers");
         if (m->opt.near_table) build_near_table(*m, dp);
+        st.mark("near-singular table");
         build_ctq(*m);
         sync(*m);
+        st.mark("C^T q");
         m->ms_build = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     });
     if (rc != BEM_OK) {

@@ -797,94 +797,118 @@ __device__ double tri_normal_field_4pi(const double t[3], const double n[3], con
     return -d3(n, f);
 }
 
-template <class T, bool FILL>
-__global__ void k_near_table(int64_t np, int nq, const int *nbr_off, const int *nbr,
-                             const int *cen_beg, const int4 *ijk, int leaf0, const uint64_t *cen_key,
-                             const uint64_t *qp_key, int shift, double h, const double *cen64,
-                             const double *nrm64, const double *area64, const double *qpg64,
-                             const double *qw64, const int *qp_of_panel,
-                             const typename V4T<T>::t *trec, const typename V4T<T>::t *nrec,
-                             const typename V4T<T>::t *srec, const int *leaf_of_cen,
-                             const int *off, int *cnt, int *col, double *val,
-                             const double *pan, const int *perm) {
-    using V4 = typename V4T<T>::t;
+// Near-singular candidates of collocation point i: the panels j of the
+// leaves adjacent to i's leaf with |c_i - c_j| <= 2.5 sqrt(A_i).  Far
+// candidates are rejected in FP32 with a relative margin of 1e-3 on the
+// squared distance (far above its rounding error), the rest decided in FP64,
+// so the set is exactly the FP64 rule's.  Writes the count (cnt) or, with
+// off set, the columns and rows of i's entries.
+__global__ void k_near_pairs(int64_t np, const int *nbr_off, const int *nbr, const int *cen_beg,
+                             const double *cen64, const double *area64, const int *leaf_of_cen, const int *off,
+                             int *cnt, int *col, int *row) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= np) return;
     const int T_ = leaf_of_cen[i];
-    const int4 ct = ijk[leaf0 + T_];
     const double ci[3] = {cen64[3 * i], cen64[3 * i + 1], cen64[3 * i + 2]};
-    const double ni[3] = {nrm64[3 * i], nrm64[3 * i + 1], nrm64[3 * i + 2]};
-    const double tau = 2.5 * sqrt(area64[i]);
-    const V4 tr = trec[i], nr = nrec[i];
+    const double tau2 = 6.25 * area64[i];
+    const float cx = (float)ci[0], cy = (float)ci[1], cz = (float)ci[2];
+    const float lo = (float)(tau2 * 0.999), hi = (float)(tau2 * 1.001);
     int n = 0;
-    const int base = FILL ? off[i] : 0;
+    const int base = off ? off[i] : 0;
     for (int e = nbr_off[T_]; e < nbr_off[T_ + 1]; ++e) {
         const int S = nbr[e];
         for (int j = cen_beg[S]; j < cen_beg[S + 1]; ++j) {
-            const double dx = ci[0] - cen64[3 * j], dy = ci[1] - cen64[3 * j + 1],
-                         dz = ci[2] - cen64[3 * j + 2];
-            if (dx * dx + dy * dy + dz * dz > tau * tau) continue;
-            if (FILL) {
-                double exact = 0.0, rep = 0.0;
-                for (int q = 0; q < nq; ++q) {
-                    const int k = qp_of_panel[(int64_t)j * nq + q];
-                    int a, b, c;
-                    {
-                        uint64_t key = qp_key[k] >> shift;
-                        // decode leaf coordinates of the source point
-                        uint64_t x = key;
-                        auto cb = [](uint64_t v) {
-                            v &= 0x1249249249249249ull;
-                            v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
-                            v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
-                            v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
-                            v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
-                            v = (v ^ (v >> 32)) & 0x1fffffull;
-                            return (int)v;
-                        };
-                        a = cb(x);
-                        b = cb(x >> 1);
-                        c = cb(x >> 2);
-                    }
-                    if (abs(a - ct.x) > 1 || abs(b - ct.y) > 1 || abs(c - ct.z) > 1) continue;
-                    if (j != i) {
-                        const double ex = ci[0] - qpg64[3 * k], ey = ci[1] - qpg64[3 * k + 1],
-                                     ez = ci[2] - qpg64[3 * k + 2];
-                        const double r2 = ex * ex + ey * ey + ez * ez;
-                        const double r = sqrt(r2);
-                        exact += -qw64[k] * (ex * ni[0] + ey * ni[1] + ez * ni[2]) / (r2 * r);
-                    }
-                    // replay of the near-field kernel for this point
-                    V4 y = srec[k];
-                    const double hT = (double)(T)h;  // the P2P kernel receives h in T
-                    y.x += (T)((double)(a - ct.x) * hT);
-                    y.y += (T)((double)(b - ct.y) * hT);
-                    y.z += (T)((double)(c - ct.z) * hT);
-                    T nd, ri3;
-                    dn_pair<T>(tr.x - y.x, tr.y - y.y, tr.z - y.z, nr.x, nr.y, nr.z, nd, ri3);
-                    rep += -(double)y.w * (double)nd * (double)ri3;
-                }
-                // with the exact panel integrals (pan != nullptr) the pair's whole
-                // value, near and far points alike, becomes the exact integral:
-                // add it and take out the 7-point value of all the panel's points
-                if (pan && j != i) {
-                    double quad = 0.0;
-                    for (int q = 0; q < nq; ++q) {
-                        const int k = qp_of_panel[(int64_t)j * nq + q];
-                        const double ex = ci[0] - qpg64[3 * k], ey = ci[1] - qpg64[3 * k + 1],
-                                     ez = ci[2] - qpg64[3 * k + 2];
-                        const double r2 = ex * ex + ey * ey + ez * ez;
-                        quad += -qw64[k] * (ex * ni[0] + ey * ni[1] + ez * ni[2]) / (r2 * sqrt(r2));
-                    }
-                    exact += tri_normal_field_4pi(ci, ni, pan + 9 * (int64_t)perm[j]) - quad;
-                }
+            const float fx = cx - (float)cen64[3 * j], fy = cy - (float)cen64[3 * j + 1],
+                        fz = cz - (float)cen64[3 * j + 2];
+            const float f2 = fx * fx + fy * fy + fz * fz;
+            if (f2 > hi) continue;
+            if (f2 >= lo) {
+                const double dx = ci[0] - cen64[3 * j], dy = ci[1] - cen64[3 * j + 1], dz = ci[2] - cen64[3 * j + 2];
+                if (dx * dx + dy * dy + dz * dz > tau2) continue;
+            }
+            if (off) {
                 col[base + n] = j;
-                val[base + n] = (exact - rep) / FOUR_PI;
+                row[base + n] = (int)i;
             }
             ++n;
         }
     }
-    if (!FILL) cnt[i] = n;
+    if (!off) cnt[i] = n;
+}
+
+// 1/sqrt(x) in FP64 by Newton's iteration y <- y (3 - x y^2) / 2 from the
+// FP32 hardware estimate (about 22 correct bits; two steps reach the FP64
+// rounding level): cheaper on this GPU than an FP64 divide and square root.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * fma(-0.5 * x, y * y, 1.5);
+    y = y * fma(-0.5 * x, y * y, 1.5);
+    return y;
+}
+
+// FP64 correction of table entry e = (i, j):
+//   D_ij = 1/(4 pi) sum_q [ -A_j w_q (c_i - y_jq).n_i / |c_i - y_jq|^3 ]_FP64
+//        - (the value the near-field kernel produces for the same points, per unit x_j),
+// over the points of j the near-field kernel visits (those in leaves adjacent
+// to i's leaf; for j = i the exact value is zero: a flat panel).  Adding D x
+// after the near field replaces the FP32 (or FP64) values of these pairs by
+// their FP64 quadrature.  With pan set (the exact flat-panel integrals) the
+// pair's whole value, near and far points alike, becomes the exact integral.
+// NQ: the rule's points (7 or 1), fixed so that their loads issue together.
+template <class T, int NQ>
+__global__ void k_near_values(int64_t nnz, const int *col, const int *row, const int4 *ijk, int leaf0,
+                              const uint64_t *qp_key, int shift, double h, const double *cen64,
+                              const double *nrm64, const double *qpg64, const double *qw64, const int *qp_of_panel,
+                              const typename V4T<T>::t *trec, const typename V4T<T>::t *nrec,
+                              const typename V4T<T>::t *srec, const int *leaf_of_cen, double *val,
+                              const double *pan, const int *perm) {
+    using V4 = typename V4T<T>::t;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    const int i = row[e], j = col[e];
+    int kk[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) kk[q] = qp_of_panel[(int64_t)j * NQ + q];
+    const int4 ct = ijk[leaf0 + leaf_of_cen[i]];
+    const double ci[3] = {cen64[3 * i], cen64[3 * i + 1], cen64[3 * i + 2]};
+    const double ni[3] = {nrm64[3 * i], nrm64[3 * i + 1], nrm64[3 * i + 2]};
+    const V4 tr = trec[i], nr = nrec[i];
+    auto cb = [](uint64_t v) {  // one coordinate of a Morton key
+        v &= 0x1249249249249249ull;
+        v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+        v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+        v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+        v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+        v = (v ^ (v >> 32)) & 0x1fffffull;
+        return (int)v;
+    };
+    const double hT = (double)(T)h;  // the near-field kernel receives h in T
+    double exact = 0.0, rep = 0.0, quad = 0.0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int k = kk[q];
+        const double ex = ci[0] - qpg64[3 * k], ey = ci[1] - qpg64[3 * k + 1], ez = ci[2] - qpg64[3 * k + 2];
+        double term = 0.0;
+        if (j != i) {
+            const double ri = rsqrt_newton(ex * ex + ey * ey + ez * ez);
+            term = -qw64[k] * (ex * ni[0] + ey * ni[1] + ez * ni[2]) * (ri * ri * ri);
+        }
+        quad += term;
+        const uint64_t kq = qp_key[k] >> shift;
+        const int a = cb(kq), b = cb(kq >> 1), c = cb(kq >> 2);
+        if (abs(a - ct.x) > 1 || abs(b - ct.y) > 1 || abs(c - ct.z) > 1) continue;
+        exact += term;
+        // replay of the near-field kernel for this point
+        V4 y = srec[k];
+        y.x += (T)((double)(a - ct.x) * hT);
+        y.y += (T)((double)(b - ct.y) * hT);
+        y.z += (T)((double)(c - ct.z) * hT);
+        T nd, ri3;
+        dn_pair<T>(tr.x - y.x, tr.y - y.y, tr.z - y.z, nr.x, nr.y, nr.z, nd, ri3);
+        rep += -(double)y.w * (double)nd * (double)ri3;
+    }
+    if (pan && j != i) exact += tri_normal_field_4pi(ci, ni, pan + 9 * (int64_t)perm[j]) - quad;
+    val[e] = (exact - rep) / FOUR_PI;
 }
 
 __global__ void k_leaf_of(const int *beg, int nleaf, int *leaf_of) {
@@ -1983,82 +2007,116 @@ static void near_table_impl(Mesh &m, const double *exact_pan) {
     const Tree &t = m.tp;
     const int64_t np = m.np;
     const int nq = (int)m.nq;
-    DArray<int> leaf_of, slot, cnt;
-    DArray<int> &qop = m.qp_of_panel;
+    if (nq != 1 && nq != 7) throw Error(BEM_EUNSUPPORTED, "near-singular table: rule of 1 or 7 points");
+    DArray<int> leaf_of, cnt, row;
+    StepTimer st(s);
     leaf_of.alloc(np);
-    slot.alloc(np);
     cnt.alloc(np + 1);
     k_leaf_of<<<t.nleaf, 128, 0, s>>>(t.cen_beg.p, t.nleaf, leaf_of.p);
     BEM_CHECK_LAUNCH();
     build_qp_of_panel(m);
     BEM_CUDA(cudaMemsetAsync(cnt.p, 0, (np + 1) * sizeof(int), s));
-    const int shift = 3 * (MORTON_BITS - t.L);
-    const double h = m.side / (double)(1 << t.L);
-    k_near_table<T, false><<<cdiv(np, 128), 128, 0, s>>>(
-        np, nq, t.nbr_off.p, t.nbr.p, t.cen_beg.p, t.ijk.p, t.leaf0, m.cen_key.p, m.qp_key.p, shift, h,
-        m.cen64.p, m.nrm64.p, m.area64.p, m.qpg64.p, m.qw64.p, qop.p, B::cen(m), B::nrm(m), B::qp(m),
-        leaf_of.p, nullptr, cnt.p, nullptr, nullptr, nullptr, nullptr);
+    k_near_pairs<<<cdiv(np, 128), 128, 0, s>>>(np, t.nbr_off.p, t.nbr.p, t.cen_beg.p, m.cen64.p, m.area64.p,
+                                               leaf_of.p, nullptr, cnt.p, nullptr, nullptr);
     BEM_CHECK_LAUNCH();
     m.nt_off.alloc(np + 1);
     exclusive_scan_int(cnt.p, m.nt_off.p, (int)np + 1, s);
     int nnz = 0;
     BEM_CUDA(cudaMemcpyAsync(&nnz, m.nt_off.p + np, sizeof(int), cudaMemcpyDeviceToHost, s));
     BEM_CUDA(cudaStreamSynchronize(s));
+    st.mark("  near-singular table: pairs counted");
     m.nt_nnz = nnz;
     m.nt_col.alloc(nnz);
     m.nt_val.alloc(nnz);
-    k_near_table<T, true><<<cdiv(np, 128), 128, 0, s>>>(
-        np, nq, t.nbr_off.p, t.nbr.p, t.cen_beg.p, t.ijk.p, t.leaf0, m.cen_key.p, m.qp_key.p, shift, h,
-        m.cen64.p, m.nrm64.p, m.area64.p, m.qpg64.p, m.qw64.p, qop.p, B::cen(m), B::nrm(m), B::qp(m),
-        leaf_of.p, m.nt_off.p, nullptr, m.nt_col.p, m.nt_val.p, exact_pan, m.cen_perm.p);
+    row.alloc(nnz);
+    k_near_pairs<<<cdiv(np, 128), 128, 0, s>>>(np, t.nbr_off.p, t.nbr.p, t.cen_beg.p, m.cen64.p, m.area64.p,
+                                               leaf_of.p, m.nt_off.p, nullptr, m.nt_col.p, row.p);
     BEM_CHECK_LAUNCH();
-    BEM_CUDA(cudaStreamSynchronize(s));
-}
-
-void build_qp_of_panel(Mesh &m) {
-    if (m.qp_of_panel.n >= (size_t)m.nqp && m.nqp > 0) return;
-    // the points of each panel in the order of the sorted quadrature array
-    std::vector<int> qpanel(m.nqp), fill(m.np, 0), qop(m.nqp);
-    BEM_CUDA(cudaMemcpyAsync(qpanel.data(), m.qp_panel.p, m.nqp * sizeof(int), cudaMemcpyDeviceToHost, m.stream));
-    BEM_CUDA(cudaStreamSynchronize(m.stream));
-    for (int64_t k = 0; k < m.nqp; ++k) {
-        const int j = qpanel[k];
-        qop[(int64_t)j * m.nq + fill[j]++] = (int)k;
-    }
-    m.qp_of_panel.alloc(m.nqp);
-    BEM_CUDA(cudaMemcpyAsync(m.qp_of_panel.p, qop.data(), m.nqp * sizeof(int), cudaMemcpyHostToDevice, m.stream));
-    BEM_CUDA(cudaStreamSynchronize(m.stream));
-}
-
-// CSR transpose of the near-singular table (for K'^T).
-static void transpose_near_table(Mesh &m) {
-    const int64_t np = m.np, nnz = m.nt_nnz;
-    std::vector<int> off(np + 1), col(nnz > 0 ? nnz : 1), toff(np + 1, 0), tcol(nnz > 0 ? nnz : 1);
-    std::vector<double> val(nnz > 0 ? nnz : 1), tval(nnz > 0 ? nnz : 1);
-    BEM_CUDA(cudaMemcpyAsync(off.data(), m.nt_off.p, (np + 1) * sizeof(int), cudaMemcpyDeviceToHost, m.stream));
+    const int shift = 3 * (MORTON_BITS - t.L);
+    const double h = m.side / (double)(1 << t.L);
     if (nnz > 0) {
-        BEM_CUDA(cudaMemcpyAsync(col.data(), m.nt_col.p, nnz * sizeof(int), cudaMemcpyDeviceToHost, m.stream));
-        BEM_CUDA(cudaMemcpyAsync(val.data(), m.nt_val.p, nnz * sizeof(double), cudaMemcpyDeviceToHost, m.stream));
+        auto kern = nq == 7 ? k_near_values<T, 7> : k_near_values<T, 1>;
+        kern<<<cdiv(nnz, 128), 128, 0, s>>>((int64_t)nnz, m.nt_col.p, row.p, t.ijk.p, t.leaf0, m.qp_key.p, shift, h,
+                                            m.cen64.p, m.nrm64.p, m.qpg64.p, m.qw64.p, m.qp_of_panel.p, B::cen(m),
+                                            B::nrm(m), B::qp(m), leaf_of.p, m.nt_val.p, exact_pan, m.cen_perm.p);
+        BEM_CHECK_LAUNCH();
     }
-    BEM_CUDA(cudaStreamSynchronize(m.stream));
-    for (int64_t e = 0; e < nnz; ++e) toff[col[e] + 1]++;
-    for (int64_t i = 0; i < np; ++i) toff[i + 1] += toff[i];
-    std::vector<int> fill(toff.begin(), toff.end() - 1);
-    for (int64_t i = 0; i < np; ++i)
-        for (int e = off[i]; e < off[i + 1]; ++e) {
-            const int d = fill[col[e]]++;
-            tcol[d] = (int)i;
-            tval[d] = val[e];
+    BEM_CUDA(cudaStreamSynchronize(s));  // the temporaries are released on return
+    st.mark("  near-singular table: values");
+}
+
+// The quadrature points of each sorted panel, in the rule's order, as
+// positions in the sorted quadrature array (built with the geometry; see
+// build_geometry_and_trees).
+void build_qp_of_panel(Mesh &m) {
+    if (m.qp_of_panel.n < (size_t)m.nqp || m.nqp == 0)
+        throw Error(BEM_ECUDA, "the quadrature points of the panels were not built");
+}
+
+// CSR transpose of the near-singular table (for K'^T), on the device:
+// column counts, their scan, a fill with one cursor per column, then each
+// column's entries put in increasing row order (a few dozen per column), so
+// that the transposed product adds them in a fixed order.
+__global__ void k_col_count(const int *col, int64_t nnz, int *cnt) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < nnz) atomicAdd(cnt + col[e], 1);
+}
+
+__global__ void k_col_fill(const int *off, const int *col, const double *val, int64_t np, int *cursor, int *tcol,
+                           double *tval) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    for (int e = off[i]; e < off[i + 1]; ++e) {
+        const int d = atomicAdd(cursor + col[e], 1);
+        tcol[d] = (int)i;
+        tval[d] = val[e];
+    }
+}
+
+__global__ void k_col_sort(const int *toff, int64_t np, int *tcol, double *tval) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const int b = toff[j], e = toff[j + 1];
+    for (int a = b + 1; a < e; ++a) {  // insertion sort by row
+        const int c = tcol[a];
+        const double v = tval[a];
+        int k = a - 1;
+        while (k >= b && tcol[k] > c) {
+            tcol[k + 1] = tcol[k];
+            tval[k + 1] = tval[k];
+            --k;
         }
+        tcol[k + 1] = c;
+        tval[k + 1] = v;
+    }
+}
+
+void transpose_near_table(Mesh &m) {
+    if (m.ntT_ok) return;
+    cudaStream_t s = m.stream;
+    const int64_t np = m.np, nnz = m.nt_nnz;
+    DArray<int> cnt, cursor;
+    cnt.alloc(np + 1);
+    BEM_CUDA(cudaMemsetAsync(cnt.p, 0, (np + 1) * sizeof(int), s));
+    if (nnz > 0) {
+        k_col_count<<<cdiv(nnz, 256), 256, 0, s>>>(m.nt_col.p, nnz, cnt.p);
+        BEM_CHECK_LAUNCH();
+    }
     m.ntT_off.alloc(np + 1);
+    exclusive_scan_int(cnt.p, m.ntT_off.p, (int)np + 1, s);
     m.ntT_col.alloc(nnz);
     m.ntT_val.alloc(nnz);
-    BEM_CUDA(cudaMemcpyAsync(m.ntT_off.p, toff.data(), (np + 1) * sizeof(int), cudaMemcpyHostToDevice, m.stream));
     if (nnz > 0) {
-        BEM_CUDA(cudaMemcpyAsync(m.ntT_col.p, tcol.data(), nnz * sizeof(int), cudaMemcpyHostToDevice, m.stream));
-        BEM_CUDA(cudaMemcpyAsync(m.ntT_val.p, tval.data(), nnz * sizeof(double), cudaMemcpyHostToDevice, m.stream));
+        cursor.alloc(np + 1);
+        BEM_CUDA(cudaMemcpyAsync(cursor.p, m.ntT_off.p, (np + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+        k_col_fill<<<cdiv(np, 256), 256, 0, s>>>(m.nt_off.p, m.nt_col.p, m.nt_val.p, np, cursor.p, m.ntT_col.p,
+                                                 m.ntT_val.p);
+        BEM_CHECK_LAUNCH();
+        k_col_sort<<<cdiv(np, 256), 256, 0, s>>>(m.ntT_off.p, np, m.ntT_col.p, m.ntT_val.p);
+        BEM_CHECK_LAUNCH();
     }
-    BEM_CUDA(cudaStreamSynchronize(m.stream));
+    BEM_CUDA(cudaStreamSynchronize(s));  // the counters are released on return
+    m.ntT_ok = true;
 }
 
 // Per-quadrature-point normals (the normal of the point's panel) in the
@@ -2183,7 +2241,7 @@ void build_near_table(Mesh &m, const double *panels) {
     const double *exact_pan = m.opt.near_table == BEM_NEAR_EXACT ? panels : nullptr;
     if (m.opt.precision == BEM_MIXED) near_table_impl<float>(m, exact_pan);
     else near_table_impl<double>(m, exact_pan);
-    transpose_near_table(m);
+    m.ntT_ok = false;  // the transpose is built when the transposed product first needs it
 }
 
 

@@ -14,6 +14,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <stdint.h>
 #include <stdexcept>
 #include <string>
@@ -53,6 +56,26 @@ void set_last_error(const std::string &msg);
     } while (0)
 
 #define BEM_CHECK_LAUNCH() BEM_CUDA(cudaGetLastError())
+
+// Wall time of each build step (the stream synchronised at each mark),
+// printed to stderr when the environment sets BEM_TIMING=1.
+struct StepTimer {
+    cudaStream_t s;
+    bool on;
+    std::chrono::steady_clock::time_point t;
+    explicit StepTimer(cudaStream_t st) : s(st), on(false) {
+        const char *e = std::getenv("BEM_TIMING");
+        on = e && e[0] == '1';
+        t = std::chrono::steady_clock::now();
+    }
+    void mark(const char *what) {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        const auto n = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "[bem] %-52s %9.1f ms\n", what, std::chrono::duration<double, std::milli>(n - t).count());
+        t = n;
+    }
+};
 
 // Raise a kernel's dynamic shared-memory limit once per (kernel, device);
 // repeated requests are free (no runtime call), which keeps graph capture clean.
@@ -247,6 +270,7 @@ struct Mesh {
     // near-singular FP64 table (CSR over sorted targets) and its transpose
     DArray<int> nt_off, nt_col, ntT_off, ntT_col;
     DArray<double> nt_val, ntT_val;
+    bool ntT_ok = false;               // the transpose is built (on first use by K'^T)
     int64_t nt_nnz = 0;
     DArray<int> qp_of_panel;           // [np][nq] sorted quadrature points of each sorted panel
 
@@ -296,6 +320,8 @@ void rebuild_charge_tree(Mesh &m, const double *d_charges);
 void build_near_table(Mesh &m, const double *panels);
 // per panel, its quadrature points' positions in the sorted quadrature order
 void build_qp_of_panel(Mesh &m);
+// the near-singular table's transpose (for K'^T), built on first use
+void transpose_near_table(Mesh &m);
 // Galerkin form: per-quadrature-point normal records and the scratch it needs
 void build_galerkin_geometry(Mesh &m);
 void build_tables(Mesh &m);

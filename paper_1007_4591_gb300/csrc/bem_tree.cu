@@ -274,6 +274,13 @@ __global__ void k_inverse_perm(const int *perm, int *rank, int64_t n) {
     if (i < n) rank[perm[i]] = (int)i;
 }
 
+__global__ void k_qp_of_panel(const int *cen_perm, const int *invq, int nq, int64_t np, int *out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= np * nq) return;
+    const int64_t j = i / nq, q = i - j * nq;
+    out[i] = invq[(int64_t)cen_perm[j] * nq + q];
+}
+
 __global__ void k_qp_panel(const int *qperm, const int *rank, int nq, int *qpanel, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) qpanel[i] = rank[qperm[i] / nq];
@@ -891,6 +898,17 @@ void build_geometry_and_trees(Mesh &m, const double *d_panels, const double *d_c
     k_inverse_perm<<<cdiv(np, TB), TB, 0, s>>>(m.cen_perm.p, rank.p, np);
     m.qp_panel.alloc(nqp);
     k_qp_panel<<<cdiv(nqp, TB), TB, 0, s>>>(qperm.p, rank.p, (int)nq, m.qp_panel.p, nqp);
+    // each sorted panel's quadrature points in the rule's order, as sorted
+    // positions: qp_of_panel[j nq + q] = inverse(qperm)[cen_perm[j] nq + q]
+    {
+        DArray<int> invq;
+        invq.alloc(nqp);
+        k_inverse_perm<<<cdiv(nqp, TB), TB, 0, s>>>(qperm.p, invq.p, nqp);
+        m.qp_of_panel.alloc(nqp);
+        k_qp_of_panel<<<cdiv(nqp, TB), TB, 0, s>>>(m.cen_perm.p, invq.p, (int)nq, np, m.qp_of_panel.p);
+        BEM_CHECK_LAUNCH();
+        BEM_CUDA(cudaStreamSynchronize(s));  // invq is released on return
+    }
     m.qpg64.alloc(nqp * 3);
     m.qw64.alloc(nqp);
     k_gather_rows<double><<<cdiv(nqp, TB), TB, 0, s>>>(qp.p, qperm.p, m.qpg64.p, nqp, 3);
