@@ -329,6 +329,17 @@ const Tables &tables_for(const Mesh &m, const Tree &t);
 // stable sort of int keys in [0, 2^bits) with int values, on the device
 void sort_pairs_int(const int *k_in, const int *v_in, int *k_out, int *v_out, int64_t n, int bits,
                     cudaStream_t s);
+// hand-written sorting and scans (bem_sort.cu): stable LSD radix sorts of
+// the low `bits` bits of the keys (v_in / v_out may be null: keys only),
+// exclusive / inclusive int scans, and the unique values of a sorted array
+// (returns their count)
+void radix_sort_u64(const uint64_t *k_in, const int *v_in, uint64_t *k_out, int *v_out, int64_t n, int bits,
+                    cudaStream_t s);
+void radix_sort_u32(const uint32_t *k_in, const int *v_in, uint32_t *k_out, int *v_out, int64_t n, int bits,
+                    cudaStream_t s);
+void scan_exclusive_i32(const int *in, int *out, int64_t n, cudaStream_t s);
+void scan_inclusive_i32(const int *in, int *out, int64_t n, cudaStream_t s);
+int64_t unique_sorted_u64(const uint64_t *in, uint64_t *out, int64_t n, cudaStream_t s);
 void build_translation_groups(Mesh &m, Tree &t);
 // tensor-core M2L (bem_tc.cu)
 bool tc_m2l_available(const Mesh &m);

@@ -7,7 +7,6 @@
 // plus the cell itself) and the M2L interaction list ("cells whose parents
 // are neighbors of the given cell's parent, and yet not directly adjacent to
 // the given cell", Sec. 2.3).
-#include <cub/cub.cuh>
 
 #include <algorithm>
 #include <cmath>
@@ -478,47 +477,20 @@ __global__ void k_count_pairs(const int *tbeg, const int *sbeg, const int *nbr_o
 }
 
 // ----------------------------------------------------------- host helpers
-static void *cub_temp(size_t bytes, DArray<char> &buf) {
-    if (buf.n < bytes) buf.alloc(bytes);
-    return buf.p;
-}
-
-static void sort_pairs(uint64_t *k_in, int *v_in, uint64_t *k_out, int *v_out, int64_t n,
-                       cudaStream_t s) {
-    DArray<char> tmp;
-    size_t bytes = 0;
-    BEM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, k_in, k_out, v_in, v_out, (int)n, 0,
-                                             3 * MORTON_BITS, s));
-    void *t = cub_temp(bytes, tmp);
-    BEM_CUDA(cub::DeviceRadixSort::SortPairs(t, bytes, k_in, k_out, v_in, v_out, (int)n, 0,
-                                             3 * MORTON_BITS, s));
+// Morton sort of (key, index) pairs over the keys' 63 bits (stable).
+static void sort_pairs(uint64_t *k_in, int *v_in, uint64_t *k_out, int *v_out, int64_t n, cudaStream_t s) {
+    radix_sort_u64(k_in, v_in, k_out, v_out, n, 3 * MORTON_BITS, s);
 }
 
 void sort_pairs_int(const int *k_in, const int *v_in, int *k_out, int *v_out, int64_t n, int bits,
                     cudaStream_t s) {
-    DArray<char> tmp;
-    size_t bytes = 0;
-    BEM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, k_in, k_out, v_in, v_out, (int)n, 0, bits, s));
-    void *t = cub_temp(bytes, tmp);
-    BEM_CUDA(cub::DeviceRadixSort::SortPairs(t, bytes, k_in, k_out, v_in, v_out, (int)n, 0, bits, s));
-    BEM_CUDA(cudaStreamSynchronize(s));  // `tmp` is released on return
+    radix_sort_u32(reinterpret_cast<const uint32_t *>(k_in), v_in, reinterpret_cast<uint32_t *>(k_out), v_out, n,
+                   bits, s);
 }
 
-static void scan_exclusive(const int *in, int *out, int n, cudaStream_t s) {
-    DArray<char> tmp;
-    size_t bytes = 0;
-    BEM_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, n, s));
-    void *t = cub_temp(bytes, tmp);
-    BEM_CUDA(cub::DeviceScan::ExclusiveSum(t, bytes, in, out, n, s));
-}
+static void scan_exclusive(const int *in, int *out, int n, cudaStream_t s) { scan_exclusive_i32(in, out, n, s); }
 
-static void scan_inclusive(const int *in, int *out, int n, cudaStream_t s) {
-    DArray<char> tmp;
-    size_t bytes = 0;
-    BEM_CUDA(cub::DeviceScan::InclusiveSum(nullptr, bytes, in, out, n, s));
-    void *t = cub_temp(bytes, tmp);
-    BEM_CUDA(cub::DeviceScan::InclusiveSum(t, bytes, in, out, n, s));
-}
+static void scan_inclusive(const int *in, int *out, int n, cudaStream_t s) { scan_inclusive_i32(in, out, n, s); }
 
 template <class T>
 static T to_host(const T *d, cudaStream_t s) {
@@ -557,27 +529,8 @@ static void build_tree(Mesh &m, Tree &t, SetKeys cen, SetKeys qp, SetKeys chg, i
         BEM_CHECK_LAUNCH();
         o += sk.n;
     }
-    {
-        DArray<char> tmp;
-        size_t bytes = 0;
-        BEM_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, bytes, pref.p, pref_sorted.p, (int)total,
-                                                0, 3 * MORTON_BITS, s));
-        cub_temp(bytes, tmp);
-        BEM_CUDA(cub::DeviceRadixSort::SortKeys(tmp.p, bytes, pref.p, pref_sorted.p, (int)total,
-                                                0, 3 * MORTON_BITS, s));
-    }
-    DArray<int> nsel;
-    nsel.alloc(1);
-    {
-        DArray<char> tmp;
-        size_t bytes = 0;
-        BEM_CUDA(cub::DeviceSelect::Unique(nullptr, bytes, pref_sorted.p, pref.p, nsel.p,
-                                           (int)total, s));
-        cub_temp(bytes, tmp);
-        BEM_CUDA(cub::DeviceSelect::Unique(tmp.p, bytes, pref_sorted.p, pref.p, nsel.p,
-                                           (int)total, s));
-    }
-    const int nleaf = to_host(nsel.p, s);
+    radix_sort_u64(pref.p, nullptr, pref_sorted.p, nullptr, total, 3 * MORTON_BITS, s);
+    const int nleaf = (int)unique_sorted_u64(pref_sorted.p, pref.p, total, s);
 
     // 2. levels bottom-up
     std::vector<DArray<uint64_t>> lkeys(L + 1);
