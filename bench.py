@@ -468,6 +468,11 @@ def run_ours(args):
                              f"{f_mhz:.0f} MHz (sm_max_mhz from MEASURED_PEAKS.json, {src})",
               "algorithmic": f"20 flop x {info['p2p_pairs']} (collocation point, source point) pairs"}
     rl_p2p["frac"] = round(rl_p2p["achieved"] / fp32_peak, 4)
+    # the FP32 rate the FMA pipe delivers on this device (packed FMA chains on
+    # every SM), next to the derived peak
+    fp32_meas = pkg.bem_fp32_peak()
+    rl_p2p["peak_measured"] = round(fp32_meas, 2)
+    rl_p2p["frac_of_measured"] = round(rl_p2p["achieved"] / fp32_meas, 4) if fp32_meas > 0 else None
     # M2L: credited with the rotation-form count (8,866 flop per translation at
     # p = 10), not the dense 121 x 121 product the kernel executes; peak = the
     # dense TF32 tensor rate, the measured bf16 rate x the nominal 1.1 / 2.25

@@ -296,6 +296,12 @@ int bem_last_m2l_ms(const bem_mesh *mesh, double *times);
  * BEM_EINVAL if profiling is off. */
 int bem_last_near_ms(const bem_mesh *mesh, double *times);
 
+/* FP32 throughput of the current device in TFLOP/s, measured by chains of
+ * packed FP32 fused multiply-adds on every SM (a few milliseconds): the
+ * achievable peak of the near-field kernel's arithmetic, for rooflines (the
+ * paper has no counterpart).  BEM_EINVAL for a NULL pointer. */
+int bem_fp32_peak(double *tflops);
+
 /* Message for the calling thread's last error (static storage, never NULL). */
 const char *bem_last_error(void);
 

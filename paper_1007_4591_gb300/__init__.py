@@ -99,6 +99,7 @@ _SIGS = {
     "bem_last_phase_ms": [_vp, _vp],
     "bem_last_m2l_ms": [_vp, _vp],
     "bem_last_near_ms": [_vp, _vp],
+    "bem_fp32_peak": [_vp],
     "bem_last_error": [],
     "bem_batch_solve": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
     "bem_normal_field_noalloc": [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp, _vp],
@@ -266,6 +267,13 @@ def bem_last_m2l_ms(h):
     t = np.zeros(3)
     _check(load_library().bem_last_m2l_ms(h, _ptr(t)), "bem_last_m2l_ms")
     return dict(zip(["split", "tc"], t.tolist()[:2]))
+
+
+def bem_fp32_peak() -> float:
+    """Measured FP32 throughput of the current device, TFLOP/s."""
+    t = ctypes.c_double()
+    _check(load_library().bem_fp32_peak(ctypes.byref(t)), "bem_fp32_peak")
+    return float(t.value)
 
 
 def bem_last_near_ms(h):

@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
