@@ -41,6 +41,29 @@ def test_batch_solve_equals_one_at_a_time(pkg):
         g.close()
 
 
+def test_batch_solve_bitwise_in_the_deterministic_form(pkg):
+    """With the translations as per-target gathers (m2l_mode = 2: M2M, M2L
+    and L2L each summed by its output cell in a fixed order, no atomics) every
+    kernel of the solve adds in a fixed order, so the batched solve
+    reproduces one-at-a-time solves bit for bit (sigma, dG and both BIBEE
+    bounds), and a repeated product is bitwise identical."""
+    mols = _mols()
+    meshes = [pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=10, tol=1e-10, m2l_mode=2) for m in mols]
+    try:
+        sig_b = [torch.empty(m.n_p, dtype=torch.float64, device="cuda") for m in mols]
+        dg, dc, dp, stats = pkg.bem_batch_solve(meshes, threads=3, sigmas=sig_b)
+        for i, g in enumerate(meshes):
+            s, st = g.solve()
+            assert torch.equal(s, sig_b[i]), i
+            assert g.energy(s) == dg[i], i
+            assert g.bibee(pkg.BEM_BIBEE_CFA) == dc[i] and g.bibee(pkg.BEM_BIBEE_P) == dp[i], i
+            x = torch.from_numpy(np.random.default_rng(i).standard_normal(g.n_p)).cuda()
+            assert torch.equal(g.matvec(x), g.matvec(x)), i
+    finally:
+        for g in meshes:
+            g.close()
+
+
 def test_batch_energies_match_oracle(pkg):
     mols = _mols()[:3]
     meshes = [pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=10, tol=1e-10) for m in mols]
