@@ -170,7 +170,8 @@ static void alloc_work(Mesh &m) {
     if (tc_m2l_available(m)) {
         ensure(m.Mtc, tc_staging_floats(m));
     }
-    const size_t nsrc = (size_t)std::max<int64_t>(m.nqp, m.nc);
+    // near-field source pairs: each leaf padded to an even count
+    const size_t nsrc = (size_t)std::max<int64_t>(m.nqp, m.nc) + (size_t)std::max(m.tp.nleaf, m.tc.nleaf) + 4;
     if (m.opt.precision == BEM_MIXED) ensure(m.str32, nsrc);
     else ensure(m.str64, nsrc);
     ensure(m.near64, (size_t)m.np);

@@ -343,18 +343,49 @@ __device__ __forceinline__ void dn_pair(T dx, T dy, T dz, T nx, T ny, T nz, T &n
     ri3 = ri * ri * ri;
 }
 
-// Strength records of a pass's near field, s = A_j w_q dens[panel] for
-// quadrature points or s = q_k (or dens[k]) for charges, next to the
-// leaf-relative coordinates: the near-field kernel stages one record per
-// source (P2M forms the same products itself).
+// Strength records of a pass's near field, in pairs of sources: the sources
+// of leaf S occupy pairs [P_S, P_S + ceil(n_S / 2)), P_S = ceil((beg_S + S) / 2)
+// (every leaf starts on a whole pair, and P_S + ceil(n_S / 2) <= P_{S+1}),
+// pair p as out[2p] = (x0, x1, y0, y1), out[2p + 1] = (z0, z1, s0, s1) with the
+// leaf-relative coordinates and the strengths s = A_j w_q dens[panel] for
+// quadrature points or s = q_k (or dens[k]) for charges; an odd leaf's last
+// pair has a zero partner.  One CTA (an even number of threads) per leaf.
 template <class T, int SRC>
-__global__ void k_strength(const typename V4T<T>::t *rec, const int *qpanel, const double *dens,
-                           int64_t n, typename V4T<T>::t *out) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    typename V4T<T>::t r = rec[i];
-    r.w = src_strength<T, SRC>(r.w, i, qpanel, dens);
-    out[i] = r;
+__global__ void k_strength_pairs(TreeView tv, const typename V4T<T>::t *rec, const int *qpanel, const double *dens,
+                                 typename V4T<T>::t *out) {
+    using V4 = typename V4T<T>::t;
+    const int S = blockIdx.x;
+    const int *sb_ = SRC == SRC_QUAD ? tv.qp_beg : tv.chg_beg;
+    const int b = sb_[S], n = sb_[S + 1] - b;
+    const int64_t P = ((int64_t)b + S + 1) >> 1;
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        T x = 0, y = 0, z = 0, w = 0;
+        if (i < n) {
+            const V4 r = rec[b + i];
+            x = r.x;
+            y = r.y;
+            z = r.z;
+            w = src_strength<T, SRC>(r.w, (int64_t)b + i, qpanel, dens);
+        }
+        // the odd lane's values go to its even neighbour (zero past the end)
+        const T px = __shfl_down_sync(0xffffffffu, x, 1), py = __shfl_down_sync(0xffffffffu, y, 1);
+        const T pz = __shfl_down_sync(0xffffffffu, z, 1), pw = __shfl_down_sync(0xffffffffu, w, 1);
+        if (!(threadIdx.x & 1) && i < n) {
+            V4 a, c;
+            a.x = x;
+            a.y = px;
+            a.z = y;
+            a.w = py;
+            c.x = z;
+            c.y = pz;
+            c.z = w;
+            c.w = pw;
+            const int64_t pr = P + (i >> 1);
+            out[2 * pr] = a;
+            out[2 * pr + 1] = c;
+        }
+    }
 }
 
 // y = x + Ehat (far + near64) / (4 pi), near64 already holding the table's
@@ -367,6 +398,16 @@ __global__ void k_apply_far_near(const double *x, const T *far, const double *ne
     double v = near64 ? near64[i] : 0.0;
     if (far) v += (double)far[i];
     y[i] = x[i] + ehat * (v * (1.0 / FOUR_PI));
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// 16-byte copy global -> shared (ok = false writes zero, src-size 0)
+__device__ __forceinline__ void cp_async_16(void *dst, const void *src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
 }
 
 // Two lanes of T: packed FP32 instructions on sm_100+ (per component the
@@ -388,26 +429,50 @@ template <> struct Pk<double> {
 };
 
 // Near field of one target leaf: every source point of the adjacent leaves
-// (and the leaf itself), staged through shared memory in tiles of
-// P2P_TILE sources, coordinates moved into the target leaf's frame.  Sources
-// are stored in pairs, (x0,x1,y0,y1) and (z0,z1,w0,w1), so that one packed
-// instruction evaluates a target against two sources.
-// Thread mapping: targets are taken P2P_TPT at a time into groups; the
-// threads split into ngroups x G (G = threads / ngroups, any integer), each
-// thread owning P2P_TPT targets and a 1/G share of the source pairs of each
-// tile.  Tile sums go into a second accumulator; the G partial sums of a
-// target are added in a fixed order at the end.  A pair of coincident points
-// (a collocation point and its own panel's centroid node) gives d = 0,
-// n.d = 0 and r^2 = eps, a finite zero.
+// (and the leaf itself), streamed through shared memory in tiles of source
+// pairs, coordinates moved into the target leaf's frame.  The source pairs
+// come from the pair records of k_strength_pairs, (x0,x1,y0,y1) and
+// (z0,z1,s0,s1), so one packed instruction evaluates a target against two
+// sources; a neighbour leaf's pairs are a contiguous run (its odd partner has
+// weight zero).
+// Staging: each thread owns PPT pair slots of every tile.  After the tile's
+// barrier it copies the records of its slots of the next tile with cp.async
+// into the second of two buffers, computes the current tile, then rewrites its
+// own slots in place into the target leaf's frame, -(y + o) (the loop then
+// forms c - (y + o) as c + (-(y + o)), the same value, with plain packed
+// adds).  A thread finds the neighbour leaf of each of its pairs by a forward
+// walk over the leaves' running pair counts (its pairs increase monotonically).
+// Thread mapping of the arithmetic: targets are taken P2P_TPT at a time into
+// groups; the threads split into ngroups x G (G = threads / ngroups, any
+// integer), each thread owning P2P_TPT targets and a 1/G share of the source
+// pairs of each tile (a tile holds a whole number of pairs per thread).  Tile
+// sums go into a second accumulator; the G partial sums of a target are added
+// in a fixed order at the end.  A pair of coincident points (a collocation
+// point and its own panel's centroid node) gives d = 0, n.d = 0 and
+// r^2 = eps, a finite zero; so does a zero partner placed at a target.
 template <class T> struct P2PTpt;
 template <> struct P2PTpt<float> { static constexpr int v = 4; };
 template <> struct P2PTpt<double> { static constexpr int v = 2; };
-// Forward kernel: CTA size NT (128 for leaves of a few dozen targets, 256
-// above) and sources fetched per thread for each shared tile (8 in FP32: few
-// barriers per source; 2 in FP64 to stay within static shared memory).
-template <class T> struct P2PFpt;
-template <> struct P2PFpt<float> { static constexpr int v = 8; };
-template <> struct P2PFpt<double> { static constexpr int v = 2; };
+// Pair slots per thread and tile: FP32 tiles of 384 pairs for 128 threads
+// (24 KB for the two buffers: 8 CTAs per SM) and 512 for 256 threads.
+template <class T, int NT> struct P2PPpt { static constexpr int v = 1; };
+template <> struct P2PPpt<float, 128> { static constexpr int v = 3; };
+template <> struct P2PPpt<float, 256> { static constexpr int v = 2; };
+
+// Dynamic shared memory of k_p2p: two buffers of pair records.
+template <class T, int NT>
+constexpr size_t p2p_smem() {
+    return (size_t)2 * 2 * NT * P2PPpt<T, NT>::v * sizeof(typename V4T<T>::t);
+}
+
+// A neighbour leaf of the target leaf: its offset in the target leaf's frame
+// and the index of its first source pair less its start in the leaf's
+// concatenated pair list.
+template <class T>
+struct alignas(4 * sizeof(T)) NbSeg {
+    T ox, oy, oz;
+    int base;
+};
 
 // With tab.out64 set (the collocation K' product) each target's value goes
 // out in FP64 together with 4 pi times its row of the near-singular table
@@ -420,21 +485,24 @@ struct NearTab {
 
 // NB: the most neighbour leaves a leaf has (27 for one-cell separation, 125
 // for the charge tree's two cells).
-template <class T, int SRC, int TGT, int P2PF_THREADS, int NB = 27>
-__global__ void __launch_bounds__(P2PF_THREADS)
+template <class T, int SRC, int TGT, int NT, int NB = 27>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 1024 / NT : 1)
 k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
-      const typename V4T<T>::t *src, const int *qpanel, const double *dens, T h, T *out, NearTab tab) {
+      const typename V4T<T>::t *src, T h, T *out, NearTab tab) {
     using V4 = typename V4T<T>::t;
     using P = Pk<T>;
     using v2 = typename P::v;
-    static_assert(NB <= P2PF_THREADS, "one thread per neighbour leaf in the set-up");
+    static_assert(NB <= NT, "one thread per neighbour leaf in the set-up");
     constexpr int P2P_TPT = P2PTpt<T>::v;
-    constexpr int P2PF_TILE = P2PF_THREADS * P2PFpt<T>::v;  // sources per tile
-    constexpr int P2PF_PAIRS = P2PF_TILE / 2;
-    __shared__ V4 shA[P2PF_PAIRS], shB[P2PF_PAIRS];
-    __shared__ int s_beg[NB + 1], s_cum[NB + 1];
-    __shared__ T s_off[NB][3];
-    __shared__ T s_part[P2PF_THREADS * 4];
+    constexpr int PPT = P2PPpt<T, NT>::v;
+    constexpr int TP = NT * PPT;                 // pair slots per buffer
+    constexpr int NCP = (int)(sizeof(V4) / 16);  // 16-byte copies per record
+    extern __shared__ __align__(32) unsigned char p2p_sm[];
+    V4 *shA = reinterpret_cast<V4 *>(p2p_sm);  // [2][TP] (x0,x1,y0,y1)
+    V4 *shB = shA + 2 * TP;                    // [2][TP] (z0,z1,s0,s1)
+    __shared__ T s_part[NT * P2P_TPT];
+    __shared__ int s_pc[NB + 1];
+    __shared__ NbSeg<T> s_seg[NB];
     const int leaf = tv.p2p_order[blockIdx.x];  // heaviest leaves first
     constexpr bool DN = TGT == TGT_CEN_DN || TGT == TGT_QUAD_DN;  // normal field, else potential
     const int *tb_ = TGT == TGT_CEN_DN ? tv.cen_beg : (TGT == TGT_QUAD_DN ? tv.qp_beg : tv.chg_beg);
@@ -446,28 +514,83 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
     if (threadIdx.x < nn) {
         const int S = tv.nbr[nb0 + threadIdx.x];
         const int4 cs = tv.ijk[tv.leaf0 + S];
-        s_beg[threadIdx.x] = sb_[S];
-        s_cum[threadIdx.x + 1] = sb_[S + 1] - sb_[S];
-        s_off[threadIdx.x][0] = (T)((double)(cs.x - ct.x) * (double)h);
-        s_off[threadIdx.x][1] = (T)((double)(cs.y - ct.y) * (double)h);
-        s_off[threadIdx.x][2] = (T)((double)(cs.z - ct.z) * (double)h);
+        const int b = sb_[S];
+        s_pc[threadIdx.x + 1] = (sb_[S + 1] - b + 1) >> 1;
+        NbSeg<T> sg;
+        sg.ox = (T)((double)(cs.x - ct.x) * (double)h);
+        sg.oy = (T)((double)(cs.y - ct.y) * (double)h);
+        sg.oz = (T)((double)(cs.z - ct.z) * (double)h);
+        sg.base = (int)(((int64_t)b + S + 1) >> 1);  // the leaf's first pair
+        s_seg[threadIdx.x] = sg;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        s_cum[0] = 0;
-        for (int k = 0; k < nn; ++k) s_cum[k + 1] += s_cum[k];
+        s_pc[0] = 0;
+        for (int k = 0; k < nn; ++k) {
+            s_seg[k].base -= s_pc[k];
+            s_pc[k + 1] += s_pc[k];
+        }
     }
     __syncthreads();
-    const int total = s_cum[nn];
+    const int total = s_pc[nn];  // source pairs
+    int kslot[PPT];              // neighbour leaf of each of this thread's slots
+    // copies of this thread's slots of the tpr pairs from pair pb into buffer bf
+    auto issue = [&](int pb, int tpr, int bf, int &k) {
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+            const int u = threadIdx.x + NT * i;
+            const int j = pb + u;
+            if (u < tpr && j < total) {
+                while (s_pc[k + 1] <= j) ++k;
+                kslot[i] = k;
+                const char *g = reinterpret_cast<const char *>(src + 2 * (int64_t)(s_seg[k].base + j));
+                char *da = reinterpret_cast<char *>(shA + bf * TP + u);
+                char *db = reinterpret_cast<char *>(shB + bf * TP + u);
+#pragma unroll
+                for (int c = 0; c < NCP; ++c) {
+                    cp_async_16(da + 16 * c, g + 16 * c, true);
+                    cp_async_16(db + 16 * c, g + sizeof(V4) + 16 * c, true);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    // this thread's slots, in place: -(y + o) for both sources of a pair
+    auto convert = [&](int pb, int tpr, int bf) {
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+            const int u = threadIdx.x + NT * i;
+            const int j = pb + u;
+            if (u < tpr && j < total) {
+                const NbSeg<T> sg = s_seg[kslot[i]];
+                V4 a = shA[bf * TP + u], b = shB[bf * TP + u];
+                a.x = -(a.x + sg.ox);
+                a.y = -(a.y + sg.ox);
+                a.z = -(a.z + sg.oy);
+                a.w = -(a.w + sg.oy);
+                b.x = -(b.x + sg.oz);
+                b.y = -(b.y + sg.oz);
+                shA[bf * TP + u] = a;
+                shB[bf * TP + u] = b;
+            }
+        }
+    };
     const int ntgt = te - tb;
     const v2 EPS2 = P::mk(P2PEps<T>::v, P2PEps<T>::v);
-    constexpr int MAXT = (P2PF_THREADS / 4) * P2P_TPT;  // targets per pass (G >= 4)
+    constexpr int MAXT = (NT / 4) * P2P_TPT;  // targets per pass (G >= 4)
     for (int t0 = 0; t0 < ntgt; t0 += MAXT) {
+        if (t0 > 0) __syncthreads();  // the previous pass's buffers and partial sums are read
         const int nt = min(ntgt - t0, MAXT);
         const int ngroups = (nt + P2P_TPT - 1) / P2P_TPT;
-        const int G = P2PF_THREADS / ngroups;
+        const int G = NT / ngroups;
         const int grp = threadIdx.x / G, g = threadIdx.x - grp * G;
         const bool active = grp < ngroups;
+        // tiles of a whole number of pairs per thread of a group: every
+        // thread makes the same number of steps between two barriers
+        const int tpr = (TP / G) * G;
+        const int ntile = (total + tpr - 1) / tpr;
+        int kw = 0;
+        if (ntile > 0) issue(0, tpr, 0, kw);
         v2 cx[P2P_TPT], cy[P2P_TPT], cz[P2P_TPT], nx[P2P_TPT], ny[P2P_TPT], nz[P2P_TPT];
         T outer[P2P_TPT];
 #pragma unroll
@@ -494,46 +617,27 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
             nz[q] = P::mk(f, f);
             outer[q] = 0;
         }
-        for (int vb = 0; vb < total; vb += P2PF_TILE) {
+        if (ntile > 0) {
+            cp_async_wait<0>();
+            convert(0, tpr, 0);
+        }
+        for (int it = 0; it < ntile; ++it) {
+            const int pb = it * tpr;
+            const int bf = it & 1;
+            const bool more = it + 1 < ntile;
+            // tile it is in place everywhere, and every thread is done with
+            // tile it - 1, whose buffer the next copies overwrite
             __syncthreads();
-            // the tile [vb, ve) walks the neighbour segments it overlaps; the
-            // threads copy each overlap as one contiguous run (source v to
-            // slot v - vb: pair (v - vb) / 2, lane (v - vb) % 2)
-            const int ve = min(vb + P2PF_TILE, total);
-            int k = 0;
-            while (s_cum[k + 1] <= vb) ++k;
-            for (; k < nn && s_cum[k] < ve; ++k) {
-                const int lo = max(s_cum[k], vb), hi = min(s_cum[k + 1], ve);
-                const int sb = s_beg[k] - s_cum[k];
-                const T ox = s_off[k][0], oy = s_off[k][1], oz = s_off[k][2];
-                for (int v = lo + threadIdx.x; v < hi; v += P2PF_THREADS) {
-                    const V4 r = src[sb + v];
-                    const int u = v - vb;
-                    T *a = reinterpret_cast<T *>(shA + (u >> 1)) + (u & 1);
-                    T *b = reinterpret_cast<T *>(shB + (u >> 1)) + (u & 1);
-                    // staged negated, -(y + o): the loop then forms c - (y + o)
-                    // as c + (-(y + o)), the same value, with plain packed adds
-                    a[0] = -(r.x + ox);
-                    a[2] = -(r.y + oy);
-                    b[0] = -(r.z + oz);
-                    b[2] = src_strength<T, SRC>(r.w, sb + v, qpanel, dens);
-                }
-            }
-            if (((ve - vb) & 1) && threadIdx.x == 0) {  // odd tail: a zero-weight partner
-                const int u = ve - vb;
-                T *a = reinterpret_cast<T *>(shA + (u >> 1)) + 1;
-                T *b = reinterpret_cast<T *>(shB + (u >> 1)) + 1;
-                a[0] = a[2] = b[0] = b[2] = 0;
-            }
-            __syncthreads();
-            const int npair = min(P2PF_PAIRS, (total - vb + 1) >> 1);
+            if (more) issue(pb + tpr, tpr, bf ^ 1, kw);
+            const V4 *cA = shA + bf * TP, *cB = shB + bf * TP;
+            const int npair = min(tpr, total - pb);
             if (active) {
                 v2 acc[P2P_TPT];
 #pragma unroll
                 for (int q = 0; q < P2P_TPT; ++q) acc[q] = P::mk(0, 0);
 #pragma unroll 2
                 for (int j = g; j < npair; j += G) {
-                    const V4 a = shA[j], b = shB[j];  // -(y + o) and the strengths
+                    const V4 a = cA[j], b = cB[j];  // -(y + o) and the strengths
                     const v2 yx = P::mk(a.x, a.y), yy = P::mk(a.z, a.w);
                     const v2 yz = P::mk(b.x, b.y), yw = P::mk(b.z, b.w);
 #pragma unroll
@@ -552,6 +656,10 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
                 }
 #pragma unroll
                 for (int q = 0; q < P2P_TPT; ++q) outer[q] += acc[q].x + acc[q].y;
+            }
+            if (more) {
+                cp_async_wait<0>();
+                convert(pb + tpr, tpr, bf ^ 1);
             }
         }
         __syncthreads();
@@ -1272,15 +1380,6 @@ __device__ __forceinline__ void cp_async_elt(T *dst, const T *src, bool ok) {
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// 16-byte copy global -> shared (ok = false writes zero, src-size 0)
-__device__ __forceinline__ void cp_async_16(void *dst, const void *src, bool ok) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
-}
 
 // out[p_out[j]] += Op[class] x in[p_in[j]] for the pairs of one chunk (one
 // operator class): a [BM x nc] x [nc x BN] product whose K loop is staged
@@ -1840,16 +1939,25 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
         const bool tn = timed && m.tm.on && m.tm.nev[0];
         if (tn) BEM_CUDA(cudaEventRecord(m.tm.nev[0], ss));
         if (ns > 0) {
-            if (sk == SRC_QUAD) k_strength<T, SRC_QUAD><<<cdiv(ns, 256), 256, 0, ss>>>(srec, qpanel, dens, ns, strec);
-            else k_strength<T, SRC_CHARGE><<<cdiv(ns, 256), 256, 0, ss>>>(srec, nullptr, dens, ns, strec);
+            if (sk == SRC_QUAD) k_strength_pairs<T, SRC_QUAD><<<t.nleaf, 128, 0, ss>>>(tv, srec, qpanel, dens, strec);
+            else k_strength_pairs<T, SRC_CHARGE><<<t.nleaf, 128, 0, ss>>>(tv, srec, nullptr, dens, strec);
             BEM_CHECK_LAUNCH();
         }
         if (tn) BEM_CUDA(cudaEventRecord(m.tm.nev[1], ss));
         // 128-thread CTAs when the average leaf holds at most 32 targets
         const bool small = ntgt <= (int64_t)32 * t.nleaf;
+        // (the dynamic tile buffers plus at most 9 KB of static arrays; above
+        // 48 KB in all the kernel needs the opt-in)
         auto go = [&](auto k128, auto k256) {
-            if (small) k128<<<t.nleaf, 128, 0, ss>>>(tv, trec, nrec, strec, nullptr, nullptr, hh, near_b, ntab);
-            else k256<<<t.nleaf, 256, 0, ss>>>(tv, trec, nrec, strec, nullptr, nullptr, hh, near_b, ntab);
+            if (small) {
+                constexpr size_t sm = p2p_smem<T, 128>();
+                if (sm + 9216 > 48 * 1024) ensure_smem_attr(reinterpret_cast<const void *>(k128), sm);
+                k128<<<t.nleaf, 128, sm, ss>>>(tv, trec, nrec, strec, hh, near_b, ntab);
+            } else {
+                constexpr size_t sm = p2p_smem<T, 256>();
+                if (sm + 9216 > 48 * 1024) ensure_smem_attr(reinterpret_cast<const void *>(k256), sm);
+                k256<<<t.nleaf, 256, sm, ss>>>(tv, trec, nrec, strec, hh, near_b, ntab);
+            }
         };
         const bool wide = t.ws == 2;
         if (t.ws != 1 && t.ws != 2) throw Error(BEM_EUNSUPPORTED, "near field: separation not built");
@@ -2365,10 +2473,10 @@ bool is_near_field_kernel(const void *func) {
         reinterpret_cast<const void *>(k_p2p<double, SRC_QUAD, TGT_CHG_PHI, 256, 125>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_QUAD_DN, 128, 125>),
         reinterpret_cast<const void *>(k_p2p<double, SRC_CHARGE, TGT_QUAD_DN, 256, 125>),
-        reinterpret_cast<const void *>(k_strength<float, SRC_QUAD>),
-        reinterpret_cast<const void *>(k_strength<float, SRC_CHARGE>),
-        reinterpret_cast<const void *>(k_strength<double, SRC_QUAD>),
-        reinterpret_cast<const void *>(k_strength<double, SRC_CHARGE>),
+        reinterpret_cast<const void *>(k_strength_pairs<float, SRC_QUAD>),
+        reinterpret_cast<const void *>(k_strength_pairs<float, SRC_CHARGE>),
+        reinterpret_cast<const void *>(k_strength_pairs<double, SRC_QUAD>),
+        reinterpret_cast<const void *>(k_strength_pairs<double, SRC_CHARGE>),
         reinterpret_cast<const void *>(k_p2p_t<float>),
         reinterpret_cast<const void *>(k_p2p_t<double>),
     };
