@@ -474,6 +474,53 @@ struct alignas(4 * sizeof(T)) NbSeg {
     int base;
 };
 
+// Work list of the near-field kernel (k_p2p_list): per CTA, in launch order,
+// hdr[3b] = (neighbour leaves nn, source pairs, first record, 0),
+// hdr[3b + 1] = (first and end centroid, first and end quadrature point),
+// hdr[3b + 2] = (first and end charge, 0, 0), and the records
+// rec[first + k] = (P_S - pc_k, pc_k << 9 | cell offset of neighbour k) with
+// P_S the first pair of leaf S (k_strength_pairs), pc_k the pairs of
+// neighbours 0..k-1 and the offset's components + 2 in 3-bit fields.  Lists
+// of one-cell separation keep 27 record slots per CTA (first = 27 b, so a CTA
+// loads header and records in one round), wider ones are packed.
+struct P2PList {
+    const int4 *hdr;
+    const int2 *rec;
+};
+
+// One CTA (128 threads) per launch slot b: the records of leaf p2p_order[b];
+// first[b] is the slot's first record.
+template <int SRC>
+__global__ void k_p2p_list(TreeView tv, const int64_t *first, int4 *hdr, int2 *rec) {
+    __shared__ int s_pc[129];
+    const int b = blockIdx.x, leaf = tv.p2p_order[b];
+    const int nb0 = tv.nbr_off[leaf], nn = tv.nbr_off[leaf + 1] - nb0;
+    const int *sb_ = SRC == SRC_QUAD ? tv.qp_beg : tv.chg_beg;
+    const int k = threadIdx.x;
+    int S = 0;
+    if (k < nn) {
+        S = tv.nbr[nb0 + k];
+        s_pc[k + 1] = (sb_[S + 1] - sb_[S] + 1) >> 1;
+    }
+    __syncthreads();
+    if (k == 0) {
+        s_pc[0] = 0;
+        for (int j = 0; j < nn; ++j) s_pc[j + 1] += s_pc[j];
+    }
+    __syncthreads();
+    const int64_t f = first[b];
+    if (k < nn) {
+        const int4 ct = tv.ijk[tv.leaf0 + leaf], cs = tv.ijk[tv.leaf0 + S];
+        const int d = (cs.x - ct.x + 2) | ((cs.y - ct.y + 2) << 3) | ((cs.z - ct.z + 2) << 6);
+        rec[f + k] = make_int2((int)(((int64_t)sb_[S] + S + 1) >> 1) - s_pc[k], (s_pc[k] << 9) | d);
+    }
+    if (k == 0) {
+        hdr[3 * b] = make_int4(nn, s_pc[nn], (int)f, 0);
+        hdr[3 * b + 1] = make_int4(tv.cen_beg[leaf], tv.cen_beg[leaf + 1], tv.qp_beg[leaf], tv.qp_beg[leaf + 1]);
+        hdr[3 * b + 2] = make_int4(tv.chg_beg[leaf], tv.chg_beg[leaf + 1], 0, 0);
+    }
+}
+
 // With tab.out64 set (the collocation K' product) each target's value goes
 // out in FP64 together with 4 pi times its row of the near-singular table
 // applied to tab.x: out64_i = near_i + 4 pi sum_e val_e x[col_e].
@@ -487,7 +534,7 @@ struct NearTab {
 // for the charge tree's two cells).
 template <class T, int SRC, int TGT, int NT, int NB = 27>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 1024 / NT : 1)
-k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
+k_p2p(P2PList wl, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
       const typename V4T<T>::t *src, T h, T *out, NearTab tab) {
     using V4 = typename V4T<T>::t;
     using P = Pk<T>;
@@ -497,40 +544,35 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
     constexpr int PPT = P2PPpt<T, NT>::v;
     constexpr int TP = NT * PPT;                 // pair slots per buffer
     constexpr int NCP = (int)(sizeof(V4) / 16);  // 16-byte copies per record
+    constexpr int MAXT = (NT / 4) * P2P_TPT;     // targets per pass (G >= 4)
     extern __shared__ __align__(32) unsigned char p2p_sm[];
     V4 *shA = reinterpret_cast<V4 *>(p2p_sm);  // [2][TP] (x0,x1,y0,y1)
     V4 *shB = shA + 2 * TP;                    // [2][TP] (z0,z1,s0,s1)
     __shared__ T s_part[NT * P2P_TPT];
     __shared__ int s_pc[NB + 1];
     __shared__ NbSeg<T> s_seg[NB];
-    const int leaf = tv.p2p_order[blockIdx.x];  // heaviest leaves first
+    __shared__ int s_row[MAXT + 1];  // the pass's table row offsets
     constexpr bool DN = TGT == TGT_CEN_DN || TGT == TGT_QUAD_DN;  // normal field, else potential
-    const int *tb_ = TGT == TGT_CEN_DN ? tv.cen_beg : (TGT == TGT_QUAD_DN ? tv.qp_beg : tv.chg_beg);
-    const int *sb_ = SRC == SRC_QUAD ? tv.qp_beg : tv.chg_beg;
-    const int tb = tb_[leaf], te = tb_[leaf + 1];
+    // the CTA's header and neighbour records: one round of independent loads
+    const int4 h0 = wl.hdr[3 * blockIdx.x];
+    const int4 h1 = wl.hdr[3 * blockIdx.x + 1 + (TGT != TGT_CEN_DN && TGT != TGT_QUAD_DN)];
+    int2 r = make_int2(0, 0);
+    if (NB == 27 && threadIdx.x < NB) r = wl.rec[27 * (int64_t)blockIdx.x + threadIdx.x];
+    const int nn = h0.x;
+    const int tb = TGT == TGT_QUAD_DN ? h1.z : h1.x, te = TGT == TGT_QUAD_DN ? h1.w : h1.y;
     if (tb == te) return;
-    const int nb0 = tv.nbr_off[leaf], nn = tv.nbr_off[leaf + 1] - nb0;
-    const int4 ct = tv.ijk[tv.leaf0 + leaf];
+    if (NB != 27 && threadIdx.x < nn) r = wl.rec[h0.z + threadIdx.x];
     if (threadIdx.x < nn) {
-        const int S = tv.nbr[nb0 + threadIdx.x];
-        const int4 cs = tv.ijk[tv.leaf0 + S];
-        const int b = sb_[S];
-        s_pc[threadIdx.x + 1] = (sb_[S + 1] - b + 1) >> 1;
+        s_pc[threadIdx.x] = r.y >> 9;
+        // offsets of at most two cells: d h with |d| <= 2 is exact in T
         NbSeg<T> sg;
-        sg.ox = (T)((double)(cs.x - ct.x) * (double)h);
-        sg.oy = (T)((double)(cs.y - ct.y) * (double)h);
-        sg.oz = (T)((double)(cs.z - ct.z) * (double)h);
-        sg.base = (int)(((int64_t)b + S + 1) >> 1);  // the leaf's first pair
+        sg.ox = (T)((r.y & 7) - 2) * h;
+        sg.oy = (T)(((r.y >> 3) & 7) - 2) * h;
+        sg.oz = (T)(((r.y >> 6) & 7) - 2) * h;
+        sg.base = r.x;
         s_seg[threadIdx.x] = sg;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_pc[0] = 0;
-        for (int k = 0; k < nn; ++k) {
-            s_seg[k].base -= s_pc[k];
-            s_pc[k + 1] += s_pc[k];
-        }
-    }
+    if (threadIdx.x == 0) s_pc[nn] = h0.y;
     __syncthreads();
     const int total = s_pc[nn];  // source pairs
     int kslot[PPT];              // neighbour leaf of each of this thread's slots
@@ -577,7 +619,6 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
     };
     const int ntgt = te - tb;
     const v2 EPS2 = P::mk(P2PEps<T>::v, P2PEps<T>::v);
-    constexpr int MAXT = (NT / 4) * P2P_TPT;  // targets per pass (G >= 4)
     for (int t0 = 0; t0 < ntgt; t0 += MAXT) {
         if (t0 > 0) __syncthreads();  // the previous pass's buffers and partial sums are read
         const int nt = min(ntgt - t0, MAXT);
@@ -590,7 +631,15 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
         const int tpr = (TP / G) * G;
         const int ntile = (total + tpr - 1) / tpr;
         int kw = 0;
+        if (tab.off) {  // the pass's table row offsets, copied ahead: nt + 1 of them
+            for (int j = threadIdx.x; j <= nt; j += NT) {
+                const unsigned d = (unsigned)__cvta_generic_to_shared(s_row + j);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(tab.off + tb + t0 + j)
+                             : "memory");
+            }
+        }
         if (ntile > 0) issue(0, tpr, 0, kw);
+        else cp_async_commit();
         v2 cx[P2P_TPT], cy[P2P_TPT], cz[P2P_TPT], nx[P2P_TPT], ny[P2P_TPT], nz[P2P_TPT];
         T outer[P2P_TPT];
 #pragma unroll
@@ -617,10 +666,8 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
             nz[q] = P::mk(f, f);
             outer[q] = 0;
         }
-        if (ntile > 0) {
-            cp_async_wait<0>();
-            convert(0, tpr, 0);
-        }
+        cp_async_wait<0>();
+        if (ntile > 0) convert(0, tpr, 0);
         for (int it = 0; it < ntile; ++it) {
             const int pb = it * tpr;
             const int bf = it & 1;
@@ -663,6 +710,17 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
             }
         }
         __syncthreads();
+        // the near-singular table rows of the pass's targets (collocation
+        // product): all threads gather the rows' entries and the inputs they
+        // take into the freed pair buffers, then each target runs its row
+        constexpr int ECAP = (int)(p2p_smem<T, NT>() / (2 * sizeof(double)));
+        double *ev = reinterpret_cast<double *>(p2p_sm), *ex = ev + ECAP;
+        const int e0 = tab.off ? s_row[0] : 0, ne = tab.off ? s_row[nt] - e0 : 0;
+        if (ne <= ECAP)
+            for (int e = threadIdx.x; e < ne; e += NT) {
+                ev[e] = tab.val[e0 + e];
+                ex[e] = tab.x[tab.col[e0 + e]];
+            }
 #pragma unroll
         for (int q = 0; q < P2P_TPT; ++q) s_part[threadIdx.x * P2P_TPT + q] = outer[q];
         __syncthreads();
@@ -673,8 +731,13 @@ k_p2p(TreeView tv, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
             const int i = tb + t0 + threadIdx.x;
             if (tab.out64) {
                 double c = 0.0;
-                if (tab.off)
-                    for (int e = tab.off[i]; e < tab.off[i + 1]; ++e) c = fma(tab.val[e], tab.x[tab.col[e]], c);
+                if (tab.off) {
+                    const int ea = s_row[threadIdx.x], eb = s_row[threadIdx.x + 1];
+                    if (ne <= ECAP)
+                        for (int e = ea - e0; e < eb - e0; ++e) c = fma(ev[e], ex[e], c);
+                    else
+                        for (int e = ea; e < eb; ++e) c = fma(tab.val[e], tab.x[tab.col[e]], c);
+                }
                 tab.out64[i] = (double)(DN ? -a : a) + FOUR_PI * c;
             } else {
                 out[i] = DN ? -a : a;
@@ -1670,6 +1733,37 @@ static void build_p2p_order(Mesh &m, Tree &t) {
     for (int l = 0; l < n; ++l) ord[l] = w[l].second;
     t.p2p_order.alloc(n);
     BEM_CUDA(cudaMemcpyAsync(t.p2p_order.p, ord.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+    // the near field's work lists (pair counts below 2^22 per leaf: the
+    // records keep them in 23 bits)
+    int maxn = 0;
+    for (int l = 0; l < n; ++l) maxn = std::max(maxn, no[l + 1] - no[l]);
+    for (int l = 0; l < n; ++l) {
+        int64_t src = 0;
+        for (int e = no[l]; e < no[l + 1]; ++e) src += std::max(qb[nb[e] + 1] - qb[nb[e]], cb[nb[e] + 1] - cb[nb[e]]);
+        if (src / 2 + maxn >= (1 << 22)) throw Error(BEM_EUNSUPPORTED, "near field: too many sources next to one leaf");
+    }
+    if (t.ws != 1 && t.ws != 2) throw Error(BEM_EUNSUPPORTED, "near field: separation not built");
+    t.p2p_nb = t.ws == 1 ? 27 : 125;
+    if (maxn > t.p2p_nb) throw Error(BEM_ECUDA, "near field: neighbour list longer than the separation allows");
+    std::vector<int64_t> first(n + 1, 0);
+    for (int b = 0; b < n; ++b) first[b + 1] = first[b] + (t.ws == 1 ? 27 : no[ord[b] + 1] - no[ord[b]]);
+    if (first[n] >= ((int64_t)1 << 31)) throw Error(BEM_EUNSUPPORTED, "near field: work list too long");
+    DArray<int64_t> d_first;
+    d_first.alloc(n + 1);
+    BEM_CUDA(cudaMemcpyAsync(d_first.p, first.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    const TreeView tv = view(t);
+    const bool has[2] = {t.has_qp, t.has_chg};
+    for (int k = 0; k < 2; ++k) {
+        t.p2p_hdr[k] = DArray<int4>();
+        t.p2p_rec[k] = DArray<int2>();
+        if (!has[k] || n == 0) continue;
+        t.p2p_hdr[k].alloc((size_t)3 * n);
+        t.p2p_rec[k].alloc((size_t)first[n]);
+        BEM_CUDA(cudaMemsetAsync(t.p2p_rec[k].p, 0, (size_t)first[n] * sizeof(int2), s));
+        if (k == 0) k_p2p_list<SRC_QUAD><<<n, 128, 0, s>>>(tv, d_first.p, t.p2p_hdr[k].p, t.p2p_rec[k].p);
+        else k_p2p_list<SRC_CHARGE><<<n, 128, 0, s>>>(tv, d_first.p, t.p2p_hdr[k].p, t.p2p_rec[k].p);
+        BEM_CHECK_LAUNCH();
+    }
     BEM_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -1948,15 +2042,18 @@ static void run_pass(Mesh &m, const Tree &t, SrcKind sk, TgtKind tk, const doubl
         const bool small = ntgt <= (int64_t)32 * t.nleaf;
         // (the dynamic tile buffers plus at most 9 KB of static arrays; above
         // 48 KB in all the kernel needs the opt-in)
+        const int wk = sk == SRC_QUAD ? 0 : 1;
+        if (!t.p2p_hdr[wk].p) throw Error(BEM_ECUDA, "near field: work list missing");
+        const P2PList wl{t.p2p_hdr[wk].p, t.p2p_rec[wk].p};
         auto go = [&](auto k128, auto k256) {
             if (small) {
                 constexpr size_t sm = p2p_smem<T, 128>();
                 if (sm + 9216 > 48 * 1024) ensure_smem_attr(reinterpret_cast<const void *>(k128), sm);
-                k128<<<t.nleaf, 128, sm, ss>>>(tv, trec, nrec, strec, hh, near_b, ntab);
+                k128<<<t.nleaf, 128, sm, ss>>>(wl, trec, nrec, strec, hh, near_b, ntab);
             } else {
                 constexpr size_t sm = p2p_smem<T, 256>();
                 if (sm + 9216 > 48 * 1024) ensure_smem_attr(reinterpret_cast<const void *>(k256), sm);
-                k256<<<t.nleaf, 256, sm, ss>>>(tv, trec, nrec, strec, hh, near_b, ntab);
+                k256<<<t.nleaf, 256, sm, ss>>>(wl, trec, nrec, strec, hh, near_b, ntab);
             }
         };
         const bool wide = t.ws == 2;

@@ -155,6 +155,11 @@ struct Tree {
     DArray<int> g_out, g_in;      // all grouped pairs: M2L, then M2M and L2L per level
     DArray<int4> g_chunk;
     DArray<int> p2p_order;        // leaves by decreasing near-field work (launch order)
+    // near-field work lists in launch order, per source kind (quadrature
+    // points, charges): two int4 of leaf data and nb records per CTA
+    DArray<int4> p2p_hdr[2];
+    DArray<int2> p2p_rec[2];
+    int p2p_nb = 27;              // records per CTA (the most neighbour leaves)
     DArray<int4> tc_super;        // tensor-core M2L work items (offset, first chunk, chunks)
     int tc_nsuper = 0;
     int m2l_chunk0 = 0, m2l_nchunk = 0;

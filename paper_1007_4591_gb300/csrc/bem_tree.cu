@@ -649,6 +649,7 @@ static void build_tree(Mesh &m, Tree &t, SetKeys cen, SetKeys qp, SetKeys chg, i
 
 size_t Tree::bytes() const {
     return g_out.bytes() + g_in.bytes() + g_chunk.bytes() + p2p_order.bytes() + tc_super.bytes() +
+           p2p_hdr[0].bytes() + p2p_hdr[1].bytes() + p2p_rec[0].bytes() + p2p_rec[1].bytes() +
            key.bytes() + ijk.bytes() + parent.bytes() + child_beg.bytes() + child_end.bytes() +
            cen_beg.bytes() + qp_beg.bytes() + chg_beg.bytes() + nbr_off.bytes() + nbr.bytes() +
            m2l_off.bytes() + m2l_src.bytes() + m2l_ofs.bytes();
