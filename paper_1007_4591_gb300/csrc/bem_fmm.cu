@@ -57,6 +57,26 @@ template <> struct K<double> {
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
+// r^-3 from r^2.  FP32: 2^(-1.5 log2 r^2) with the approximate base-2
+// logarithm and exponential of the special-function unit (two of its
+// operations and one multiply, against a reciprocal square root and two
+// multiplies); both carry ~2^-22 error, about that of the cubed rsqrt.
+__device__ __forceinline__ float lg2a(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2a(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rinv3(float r2) { return ex2a(-1.5f * lg2a(r2)); }
+__device__ __forceinline__ double rinv3(double r2) {
+    const double ri = rsqrt(r2);
+    return ri * ri * ri;
+}
+
 // Regular solid harmonics R_n^m(x,y,z), 0 <= m <= n <= p, handed to emit(n, m, re, im).
 template <class T, class F>
 __device__ __forceinline__ void regular_solid(T x, T y, T z, int p, F &&emit) {
@@ -338,9 +358,8 @@ template <> struct P2PEps<double> { static constexpr double v = 1e-40; };
 template <class T>
 __device__ __forceinline__ void dn_pair(T dx, T dy, T dz, T nx, T ny, T nz, T &nd, T &ri3) {
     const T r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, P2PEps<T>::v)));
-    const T ri = rsq(r2);
     nd = fma(nx, dx, fma(ny, dy, nz * dz));
-    ri3 = ri * ri * ri;
+    ri3 = rinv3(r2);
 }
 
 // Strength records of a pass's near field, in pairs of sources: the sources
@@ -419,6 +438,11 @@ template <> struct Pk<float> {
     __device__ static v add(v a, v b) { return __fadd2_rn(a, b); }
     __device__ static v mul(v a, v b) { return __fmul2_rn(a, b); }
     __device__ static v fma(v a, v b, v c) { return __ffma2_rn(a, b, c); }
+    // r^-3 per lane, the arithmetic of rinv3 (the multiply packed)
+    __device__ static v rinv3(v r2) {
+        const v e = __fmul2_rn(make_float2(lg2a(r2.x), lg2a(r2.y)), make_float2(-1.5f, -1.5f));
+        return make_float2(ex2a(e.x), ex2a(e.y));
+    }
 };
 template <> struct Pk<double> {
     using v = double2;
@@ -426,6 +450,7 @@ template <> struct Pk<double> {
     __device__ static v add(v a, v b) { return make_double2(a.x + b.x, a.y + b.y); }
     __device__ static v mul(v a, v b) { return make_double2(a.x * b.x, a.y * b.y); }
     __device__ static v fma(v a, v b, v c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
+    __device__ static v rinv3(v r2) { return make_double2(::bem::rinv3(r2.x), ::bem::rinv3(r2.y)); }
 };
 
 // Near field of one target leaf: every source point of the adjacent leaves
@@ -691,13 +716,11 @@ k_p2p(P2PList wl, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
                     for (int q = 0; q < P2P_TPT; ++q) {
                         const v2 dx = P::add(cx[q], yx), dy = P::add(cy[q], yy), dz = P::add(cz[q], yz);
                         const v2 r2 = P::fma(dx, dx, P::fma(dy, dy, P::fma(dz, dz, EPS2)));
-                        const v2 ri = P::mk(rsq(r2.x), rsq(r2.y));
                         if (DN) {
                             const v2 nd = P::fma(nx[q], dx, P::fma(ny[q], dy, P::mul(nz[q], dz)));
-                            const v2 ri3 = P::mul(P::mul(ri, ri), ri);
-                            acc[q] = P::fma(P::mul(yw, nd), ri3, acc[q]);
+                            acc[q] = P::fma(P::mul(yw, nd), P::rinv3(r2), acc[q]);
                         } else {
-                            acc[q] = P::fma(yw, ri, acc[q]);
+                            acc[q] = P::fma(yw, P::mk(rsq(r2.x), rsq(r2.y)), acc[q]);
                         }
                     }
                 }
