@@ -20,6 +20,10 @@ What it computes (Sec. 2.1-2.2 of the paper, in the reading fixed below):
   d dG / d q_k and d dG / d x_k (solve A^T lam = C^T q).
 * Restarted GMRES (Saad & Schultz 1986) with modified Gram-Schmidt Arnoldi
   and Givens rotations, x0 = 0, relative residual |b - A x| / |b|.
+* The higher-accuracy panel integration (Sec. 2.1 names exact integrals over
+  flat panels as the alternative to quadrature): with exact_charge_near, the
+  charge-panel pairs of C, C^T and grad C closer than 2.5 sqrt(A_j) take the
+  exact single-layer integral over the flat panel.
 
 The dense sums live in ``bem_oracle.c`` (compiled with gcc, OpenMP over
 targets); this module does the linear algebra around them in numpy.
@@ -75,6 +79,11 @@ def _load():
             "oracle_grad_bt": (None, [i64, d, d, i64, d, d, d]),
             "oracle_solid_angle": (ctypes.c_double, [d, d]),
             "oracle_panel_dn": (ctypes.c_double, [d, d, d]),
+            "oracle_panel_phi": (ctypes.c_double, [d, d]),
+            "oracle_panel_grad_phi": (None, [d, d, d]),
+            "oracle_c_exact": (None, [i64, ci, d, d, d, d, d, i64, d, d, d]),
+            "oracle_ct_exact": (None, [i64, ci, d, d, d, d, d, i64, d, d, d]),
+            "oracle_grad_c_exact": (None, [i64, ci, d, d, d, d, d, i64, d, d, d]),
             "oracle_kprime_rows_near_exact": (None, [i64, ci, d, d, d, d, d, d, d, i64,
                                                      ctypes.POINTER(ctypes.c_int64), d]),
             "oracle_kprime_rows_galerkin": (None, [i64, ci, d, d, d, d, d, d, d, i64,
@@ -140,6 +149,20 @@ def panel_dn(t, n, tri) -> float:
     return float(lib.oracle_panel_dn(_p(_c(t)), _p(_c(n)), _p(_c(tri))))
 
 
+def panel_phi(t, tri) -> float:
+    """int_T dA_y / (4 pi |t - y|), exactly, for a flat triangle (the
+    single-layer potential of a unit density on one panel)."""
+    lib = _load()
+    return float(lib.oracle_panel_phi(_p(_c(t)), _p(_c(tri))))
+
+
+def panel_grad_phi(t, tri):
+    """grad_t of panel_phi: -int_T (t - y) / (4 pi |t - y|^3) dA_y."""
+    g = np.empty(3)
+    _load().oracle_panel_grad_phi(_p(_c(t)), _p(_c(tri)), _p(g))
+    return g
+
+
 def normal_field(targets, normals, charges):
     """Normal derivative of the charges' Coulomb potential at arbitrary points
     (the B q of Sec. 2.1 with the collocation points and normals replaced by
@@ -158,8 +181,13 @@ def normal_field(targets, normals, charges):
 class Problem:
     """Dense discrete operators of one molecule (panels + point charges)."""
 
-    def __init__(self, panels, charges, eps_in: float, eps_out: float, nq: int = 7):
+    def __init__(self, panels, charges, eps_in: float, eps_out: float, nq: int = 7,
+                 exact_charge_near: bool = False):
+        """exact_charge_near: C, C^T and grad C integrate the charge-panel
+        pairs closer than 2.5 sqrt(A_j) exactly over the flat panel (the
+        higher-accuracy panel integration of Sec. 2.1), the rest by the rule."""
         lib = _load()
+        self.exact_charge_near = bool(exact_charge_near)
         self.panels = _c(panels).reshape(-1, 3, 3)
         ch = _c(charges).reshape(-1, 4)
         self.xq = _c(ch[:, :3])
@@ -280,7 +308,11 @@ class Problem:
         ks = np.asarray(ks, dtype=np.int64)
         xk = _c(self.xq[ks])
         phi = np.empty(ks.shape[0])
-        _load().oracle_c(self.n, self.nq, _p(self.qp), _p(self.qw), ks.shape[0], _p(xk), _p(s), _p(phi))
+        if self.exact_charge_near:
+            _load().oracle_c_exact(self.n, self.nq, _p(self.qp), _p(self.qw), _p(self.cen), _p(self.area),
+                                   _p(self.panels), ks.shape[0], _p(xk), _p(s), _p(phi))
+        else:
+            _load().oracle_c(self.n, self.nq, _p(self.qp), _p(self.qw), ks.shape[0], _p(xk), _p(s), _p(phi))
         return phi
 
     def bt(self, v):
@@ -293,22 +325,34 @@ class Problem:
         """phi = C s (Eq. reac with G = 1/(4 pi r))."""
         s = _c(s)
         phi = np.empty(self.nc)
-        _load().oracle_c(self.n, self.nq, _p(self.qp), _p(self.qw), self.nc, _p(self.xq),
-                         _p(s), _p(phi))
+        if self.exact_charge_near:
+            _load().oracle_c_exact(self.n, self.nq, _p(self.qp), _p(self.qw), _p(self.cen), _p(self.area),
+                                   _p(self.panels), self.nc, _p(self.xq), _p(s), _p(phi))
+        else:
+            _load().oracle_c(self.n, self.nq, _p(self.qp), _p(self.qw), self.nc, _p(self.xq),
+                             _p(s), _p(phi))
         return phi
 
     def ct(self, u):
         u = _c(u)
         v = np.empty(self.n)
-        _load().oracle_ct(self.n, self.nq, _p(self.qp), _p(self.qw), self.nc, _p(self.xq),
-                          _p(u), _p(v))
+        if self.exact_charge_near:
+            _load().oracle_ct_exact(self.n, self.nq, _p(self.qp), _p(self.qw), _p(self.cen), _p(self.area),
+                                    _p(self.panels), self.nc, _p(self.xq), _p(u), _p(v))
+        else:
+            _load().oracle_ct(self.n, self.nq, _p(self.qp), _p(self.qw), self.nc, _p(self.xq),
+                              _p(u), _p(v))
         return v
 
     def grad_c(self, s):
         s = _c(s)
         g = np.empty((self.nc, 3))
-        _load().oracle_grad_c(self.n, self.nq, _p(self.qp), _p(self.qw), self.nc, _p(self.xq),
-                              _p(s), _p(g))
+        if self.exact_charge_near:
+            _load().oracle_grad_c_exact(self.n, self.nq, _p(self.qp), _p(self.qw), _p(self.cen),
+                                        _p(self.area), _p(self.panels), self.nc, _p(self.xq), _p(s), _p(g))
+        else:
+            _load().oracle_grad_c(self.n, self.nq, _p(self.qp), _p(self.qw), self.nc, _p(self.xq),
+                                  _p(s), _p(g))
         return g
 
     def grad_bt(self, v):

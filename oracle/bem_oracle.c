@@ -283,6 +283,149 @@ double oracle_panel_dn(const double *t, const double *n, const double *tri)
     return -dot3(n, v) / FOUR_PI;
 }
 
+/* int_T dA_y / (4 pi |t - y|) for a flat triangle tri[3][3] (the single-layer
+ * potential of a unit density, Sec. 2.1's G integrated over one panel).  In
+ * the plane of T let rho0 be the foot of t, h = (t - a0).nu its height and,
+ * for each edge e from p to q with outward in-plane normal m_e,
+ * d_e = m_e.(p - t) the distance of rho0 from the edge's line (positive on
+ * the inner side).  The 2D field F(rho) = (rho - rho0)(R - |h|)/|rho - rho0|^2
+ * has divergence 1/R in the plane, so the divergence theorem gives
+ *   int_T dA / R = sum_e d_e int_e (R - |h|)/s^2 dl
+ *                = sum_e d_e L_e - |h| int_T |h| / R^3 dA
+ * (s = |rho - rho0|, L_e = int_e dl / R), and the last integral is the
+ * magnitude of the solid angle W, so |h| |W| = h W. */
+double oracle_panel_phi(const double *t, const double *tri)
+{
+    double e1[3], e2[3], nu[3], a0t[3];
+    sub3(tri + 3, tri, e1);
+    sub3(tri + 6, tri, e2);
+    cross3(e1, e2, nu);
+    const double ln = norm3(nu);
+    for (int k = 0; k < 3; ++k) nu[k] /= ln;
+    sub3(t, tri, a0t);
+    const double h = dot3(a0t, nu);
+    double acc = -h * oracle_solid_angle(t, tri);
+    for (int e = 0; e < 3; ++e) {
+        const double *p = tri + 3 * e, *q = tri + 3 * ((e + 1) % 3);
+        double te[3], m[3], pt[3];
+        sub3(q, p, te);
+        const double lt = norm3(te);
+        for (int k = 0; k < 3; ++k) te[k] /= lt;
+        cross3(te, nu, m);
+        sub3(p, t, pt);
+        const double d = dot3(m, pt);
+        if (d != 0.0) acc += d * edge_log(t, p, q);
+    }
+    return acc / FOUR_PI;
+}
+
+/* grad_t of oracle_panel_phi: -int_T (t - y) / (4 pi |t - y|^3) dA, the
+ * field whose projection on n is oracle_panel_dn (solid angle along the
+ * normal, one edge logarithm per edge in the plane). */
+void oracle_panel_grad_phi(const double *t, const double *tri, double *g)
+{
+    double e1[3], e2[3], nu[3];
+    sub3(tri + 3, tri, e1);
+    sub3(tri + 6, tri, e2);
+    cross3(e1, e2, nu);
+    const double ln = norm3(nu);
+    for (int k = 0; k < 3; ++k) nu[k] /= ln;
+    const double W = oracle_solid_angle(t, tri);
+    double v[3];
+    for (int k = 0; k < 3; ++k) v[k] = nu[k] * W;
+    for (int e = 0; e < 3; ++e) {
+        const double *p = tri + 3 * e, *q = tri + 3 * ((e + 1) % 3);
+        double te[3], m[3];
+        sub3(q, p, te);
+        const double lt = norm3(te);
+        for (int k = 0; k < 3; ++k) te[k] /= lt;
+        cross3(te, nu, m);
+        const double L = edge_log(t, p, q);
+        for (int k = 0; k < 3; ++k) v[k] += m[k] * L;
+    }
+    for (int k = 0; k < 3; ++k) g[k] = -v[k] / FOUR_PI;
+}
+
+/* Charge-panel entries with the higher-accuracy panel integration of the
+ * near-singular pairs: a charge x_k closer than 2.5 sqrt(A_j) to the centroid
+ * of panel j takes the exact single-layer integral over the flat panel (and
+ * its gradient), every other pair the quadrature rule.  phi = C s, v = C^T u,
+ * g = grad_x (C s); panels[n][3][3], cen[n][3], area[n]. */
+static int charge_near(const double *x, const double *cen, const double *area, int64_t j)
+{
+    double d[3];
+    sub3(x, cen + 3 * j, d);
+    return dot3(d, d) <= 6.25 * area[j];
+}
+
+void oracle_c_exact(int64_t n, int nq, const double *qp, const double *qw, const double *cen,
+                    const double *area, const double *panels, int64_t nc, const double *xq,
+                    const double *s, double *phi)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nc; ++k) {
+        const double *x = xq + 3 * k;
+        double acc = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double pj = 0.0;
+            if (charge_near(x, cen, area, j))
+                pj = oracle_panel_phi(x, panels + 9 * j);
+            else
+                for (int q = 0; q < nq; ++q) pj += qw[j * nq + q] * green(x, qp + 3 * (j * nq + q));
+            acc += s[j] * pj;
+        }
+        phi[k] = acc;
+    }
+}
+
+void oracle_ct_exact(int64_t n, int nq, const double *qp, const double *qw, const double *cen,
+                     const double *area, const double *panels, int64_t nc, const double *xq,
+                     const double *u, double *v)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int64_t k = 0; k < nc; ++k) {
+            const double *x = xq + 3 * k;
+            double pj = 0.0;
+            if (charge_near(x, cen, area, j))
+                pj = oracle_panel_phi(x, panels + 9 * j);
+            else
+                for (int q = 0; q < nq; ++q) pj += qw[j * nq + q] * green(x, qp + 3 * (j * nq + q));
+            acc += u[k] * pj;
+        }
+        v[j] = acc;
+    }
+}
+
+void oracle_grad_c_exact(int64_t n, int nq, const double *qp, const double *qw, const double *cen,
+                         const double *area, const double *panels, int64_t nc, const double *xq,
+                         const double *s, double *g /*[nc][3]*/)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nc; ++k) {
+        const double *x = xq + 3 * k;
+        double a[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (charge_near(x, cen, area, j)) {
+                double gj[3];
+                oracle_panel_grad_phi(x, panels + 9 * j, gj);
+                for (int c = 0; c < 3; ++c) a[c] += s[j] * gj[c];
+            } else {
+                for (int q = 0; q < nq; ++q) {
+                    const double *y = qp + 3 * (j * nq + q);
+                    double d[3];
+                    sub3(x, y, d);
+                    const double r2 = dot3(d, d), r = sqrt(r2);
+                    const double f = -s[j] * qw[j * nq + q] / (FOUR_PI * r2 * r);
+                    for (int c = 0; c < 3; ++c) a[c] += f * d[c];
+                }
+            }
+        }
+        for (int c = 0; c < 3; ++c) g[3 * k + c] = a[c];
+    }
+}
+
 /* Rows of K' x where every pair (i, j != i) with |c_i - c_j| <= 2.5 sqrt(A_i)
  * uses the exact panel integral above and every other pair the quadrature
  * rule (the near-singular set of the accelerated product). */

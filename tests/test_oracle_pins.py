@@ -16,7 +16,13 @@ index, a transposed operand, a wrong quadrature weight) fails at least one:
 * GMRES against dense LU (numpy.linalg.solve) on the assembled matrix;
 * adjoint: dot-product identities for K'^T, B^T, C^T and central finite
   differences of the energy in the charge values and positions;
-* rigid-motion invariance of the energy.
+* rigid-motion invariance of the energy;
+* exact flat-panel integrals: the normal field by closed-surface solid
+  angles, refined quadrature and its unit jump; the single-layer potential by
+  the equilateral centroid closed form, a polar integral on the panel's axis,
+  refined quadrature, finite differences of its gradient, the jump of its
+  normal derivative, and the uniform-shell potential R inside a sphere for
+  charges just under the surface.
 """
 import os
 
@@ -451,3 +457,140 @@ def test_sampled_rows_match_the_full_products(small3):
     ks = np.random.default_rng(15).choice(m.n_c, 9, replace=False)
     np.testing.assert_array_equal(P.c_rows(s, ks), P.c(s)[ks])
     np.testing.assert_array_equal(oracle.normal_field(P.cen, P.nrm, m.charges), P.bq())
+
+
+# ------------------------------- exact single-layer integrals over a panel
+# int_T dA / (4 pi |t - y|) over a flat triangle and its gradient, used for
+# the charge-panel pairs closer than 2.5 sqrt(A_j) in the higher-accuracy
+# charge products (C, C^T, grad C).
+def _refined_7pt_phi(t, tri, levels):
+    import ctypes
+    bary = np.zeros(21)
+    w = np.zeros(7)
+    oracle._load().oracle_quad_rule(7, bary.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    bary = bary.reshape(7, 3)
+    tris = [np.asarray(tri, dtype=np.float64)]
+    for _ in range(levels):
+        nxt = []
+        for a, b, c in tris:
+            ab, bc, ca = (a + b) / 2, (b + c) / 2, (c + a) / 2
+            nxt += [np.array([a, ab, ca]), np.array([ab, b, bc]), np.array([ca, bc, c]),
+                    np.array([ab, bc, ca])]
+        tris = nxt
+    acc = 0.0
+    for tt in tris:
+        A = 0.5 * np.linalg.norm(np.cross(tt[1] - tt[0], tt[2] - tt[0]))
+        r = np.linalg.norm(np.asarray(t) - bary @ tt, axis=1)
+        acc += float(np.sum(A * w / (4 * np.pi * r)))
+    return acc
+
+
+def _equilateral(a=1.0):
+    return np.array([[0.0, 0.0, 0.0], [a, 0.0, 0.0], [a / 2, a * np.sqrt(3) / 2, 0.0]])
+
+
+def test_single_layer_at_the_centroid_of_an_equilateral_triangle():
+    # in polar coordinates about the centroid each edge (inradius r) gives
+    # r * 2 asinh(sqrt 3): int_T dA / R = sqrt(3) a ln(2 + sqrt 3)
+    for a in (1.0, 0.37, 2.5):
+        tri = _equilateral(a)
+        ex = np.sqrt(3) * a * np.log(2 + np.sqrt(3)) / (4 * np.pi)
+        assert abs(oracle.panel_phi(tri.mean(axis=0), tri) - ex) < 1e-14 * max(1.0, ex)
+
+
+def test_single_layer_on_the_axis_of_an_equilateral_triangle():
+    # t at height h above the centroid: int_T dA / R =
+    # 3 int_{-pi/3}^{pi/3} (sqrt(r^2 sec^2 th + h^2) - |h|) dth, r the inradius
+    from scipy.integrate import quad
+    a = 1.3
+    tri = _equilateral(a)
+    r = a / (2 * np.sqrt(3))
+    for h in (1e-4, 0.03, 0.5, 3.0, -0.2):
+        f = lambda th: np.sqrt((r / np.cos(th)) ** 2 + h * h) - abs(h)
+        ref = 3 * quad(f, -np.pi / 3, np.pi / 3, epsabs=1e-14, epsrel=1e-13, limit=200)[0] / (4 * np.pi)
+        got = oracle.panel_phi(tri.mean(axis=0) + np.array([0.0, 0.0, h]), tri)
+        assert abs(got - ref) < 1e-13, (h, got, ref)
+
+
+def test_single_layer_matches_refined_quadrature():
+    tri = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.2, 0.9, 0.1]])
+    # above the panel, behind it, in its plane beyond an edge and beyond a vertex
+    for t in ([0.3, 0.4, 0.35], [0.5, 0.2, -0.4], [-0.7, 0.0, 0.0], [1.6, -0.5, 0.05]):
+        ex = oracle.panel_phi(t, tri)
+        assert abs(_refined_7pt_phi(t, tri, 5) - ex) < 1e-10 * abs(ex), (t, ex)
+        assert abs(_refined_7pt_phi(t, tri, 0) - ex) > 1e-12   # the unrefined rule is not exact
+
+
+def test_single_layer_gradient_is_the_derivative_of_the_potential():
+    tri = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.2, 0.9, 0.1]])
+    eps = 1e-5
+    for t in ([0.3, 0.4, 0.35], [0.4, 0.3, -0.02], [-0.7, 0.1, 0.05]):
+        t = np.array(t)
+        g = oracle.panel_grad_phi(t, tri)
+        fd = np.array([(oracle.panel_phi(t + eps * e, tri) - oracle.panel_phi(t - eps * e, tri)) / (2 * eps)
+                       for e in np.eye(3)])
+        assert np.max(np.abs(g - fd)) < 1e-8 * max(1.0, np.max(np.abs(g))), (t, g, fd)
+
+
+def test_single_layer_is_continuous_and_its_normal_derivative_jumps_by_one():
+    # a unit sheet density: the potential is continuous through the panel and
+    # its normal derivative drops by 1 from behind to the side the normal
+    # points to; the tangential derivatives are continuous
+    tri = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    nu = np.array([0.0, 0.0, 1.0])
+    c = np.array([0.3, 0.25, 0.0])
+    p_up, p_dn = oracle.panel_phi(c + 1e-9 * nu, tri), oracle.panel_phi(c - 1e-9 * nu, tri)
+    assert abs(p_up - p_dn) < 1e-12
+    g_up, g_dn = oracle.panel_grad_phi(c + 1e-9 * nu, tri), oracle.panel_grad_phi(c - 1e-9 * nu, tri)
+    assert abs((g_up - g_dn) @ nu + 1.0) < 1e-7
+    assert np.max(np.abs((g_up - g_dn)[:2])) < 1e-7
+
+
+def _shell_problem(depth):
+    # a uniform unit density on a sphere of radius R has potential R at every
+    # interior point; charges just under three panel centroids and one deep
+    m = synth.born(4, radius=2.0)
+    P0 = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+    ks = [0, 300, 2000]
+    pts = [P0.cen[k] - depth * P0.nrm[k] for k in ks] + [[0.1, -0.2, 0.3]]
+    ch = np.array([[*p, 1.0] for p in pts])
+    return (oracle.Problem(m.panels, ch, m.eps_in, m.eps_out),
+            oracle.Problem(m.panels, ch, m.eps_in, m.eps_out, exact_charge_near=True))
+
+
+def test_exact_charge_near_pairs_recover_the_shell_potential():
+    R = 2.0
+    Pq, Pe = _shell_problem(0.01)
+    one = np.ones(Pq.n)
+    phi_q, phi_e = Pq.c(one), Pe.c(one)
+    # the flat inscribed mesh (panel edge ~0.1 A) gives R to ~5e-4 everywhere
+    # inside; the 7-point rule 0.01 A under a panel errs several times more
+    assert np.max(np.abs(phi_e / R - 1)) < 1e-3, phi_e
+    assert np.min(np.abs(phi_q[:3] / R - 1)) > 5 * np.max(np.abs(phi_e[:3] / R - 1)), (phi_q, phi_e)
+    # far from the surface both variants coincide
+    assert abs(phi_q[3] - phi_e[3]) < 1e-14
+
+
+def test_exact_charge_near_transpose_and_gradient():
+    Pq, Pe = _shell_problem(0.02)
+    rng = np.random.default_rng(3)
+    s, u = rng.standard_normal(Pe.n), rng.standard_normal(Pe.nc)
+    # C^T is the transpose of C (dot-product identity), in both variants
+    for P in (Pq, Pe):
+        assert abs(u @ P.c(s) - P.ct(u) @ s) < 1e-12 * np.linalg.norm(u) * np.linalg.norm(P.ct(u)) * 10
+    # the gradient at the charges is the derivative of C s (small steps keep
+    # every pair on its side of the near/far threshold)
+    g = Pe.grad_c(s)
+    eps = 1e-6
+    for k in range(Pe.nc):
+        for c in range(3):
+            xp, xm = Pe.xq.copy(), Pe.xq.copy()
+            xp[k, c] += eps
+            xm[k, c] -= eps
+            chp = np.column_stack([xp, Pe.q])
+            chm = np.column_stack([xm, Pe.q])
+            fp = oracle.Problem(Pe.panels, chp, Pe.eps_in, Pe.eps_out, exact_charge_near=True).c(s)[k]
+            fm = oracle.Problem(Pe.panels, chm, Pe.eps_in, Pe.eps_out, exact_charge_near=True).c(s)[k]
+            fd = (fp - fm) / (2 * eps)
+            assert abs(g[k, c] - fd) < 1e-6 * max(1.0, abs(fd)), (k, c, g[k, c], fd)
