@@ -76,6 +76,14 @@ extern "C" {
 #define BEM_FLAG_M2L_REDUCE 16u   /* accepted for compatibility, no effect: the tensor-core M2L
                                      always adds each pair's row into its target cell with
                                      vector reductions (no per-pair buffer) */
+#define BEM_FLAG_CHARGE_NEAR_EXACT 32u /* higher-accuracy panel integration of the charges
+                                     (Sec. 2.1): in C s, C^T q and grad_x C s every pair of a
+                                     charge and a panel whose centroid lies within 2.5 sqrt(A_j)
+                                     takes the exact single-layer integral over the flat panel
+                                     (FP64) instead of the quadrature rule; the panel vertices
+                                     are kept on the device (72 bytes per panel).  Returns
+                                     BEM_EUNSUPPORTED if a panel is wider than the charge tree's
+                                     neighbour reach. */
 
 /* bem_options.near_table */
 #define BEM_NEAR_QUADRATURE 1

@@ -40,6 +40,7 @@ BEM_FLAG_NO_NEAR = 2
 BEM_FLAG_NO_NEARTAB = 4
 BEM_FLAG_CHECK_CHARGES = 8
 BEM_FLAG_M2L_REDUCE = 16
+BEM_FLAG_CHARGE_NEAR_EXACT = 32
 BEM_CHARGE_AUTO = 0
 BEM_CHARGE_FMM = 1
 BEM_CHARGE_DIRECT = 2

@@ -228,10 +228,12 @@ void adjoint_gradients(Mesh &m, double grad_out, double *dq_s, double *dx_s) {
     lam.alloc(np);
     // C sigma and its gradient at the charges
     direct_adjoint(m, AS_QUAD, AT_CHG_GRAD, m.sigma_s.p, cs4.p);
+    charge_near_phi(m, m.sigma_s.p, cs4.p, 4, 4);
     // C^T q: potential of the charges at the quadrature points, summed per panel
     direct_adjoint(m, AS_CHARGE, AT_QUAD_PHI, nullptr, ct4.p);
     k_panel_sum4<<<cdiv(np, 256), 256, 0, s>>>(ct4.p, m.qp_of_panel.p, m.qw64.p, (int)m.nq, np, rhs.p);
     BEM_CHECK_LAUNCH();
+    charge_near_ct(m, m.q64.p, rhs.p);
     // A^T lam = C^T q
     BEM_CUDA(cudaMemsetAsync(lam.p, 0, np * sizeof(double), s));
     bem_solve_stats st{};

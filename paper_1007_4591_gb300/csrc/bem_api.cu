@@ -136,6 +136,8 @@ size_t Mesh::bytes() const {
     if (tab) b += tab->bytes();
     if (tab2) b += tab2->bytes();
     b += Mf.bytes() + Lf.bytes() + Md.bytes() + Ld.bytes();
+    b += pan64.bytes() + cn_off.bytes() + cn_col.bytes() + cn_val.bytes() + cnT_off.bytes() + cnT_row.bytes() +
+         cnT_val.bytes();
     b += Mtc.bytes() + ctq.bytes() + str32.bytes() + str64.bytes() + near64.bytes() + dpart_f.bytes() +
          dpart_d.bytes();
     b += xs.bytes() + ys.bytes() + zs.bytes() + far_f.bytes() + near_f.bytes() + far_d.bytes() +
@@ -283,6 +285,7 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
         const double *dc = n_c > 0 ? dev_in(*m, charges, (size_t)n_c * 4, sc) : nullptr;
         st.mark("inputs to the device");
         build_geometry_and_trees(*m, dp, dc);
+        keep_panel_vertices(*m, dp);
         st.mark("geometry, Morton sort, trees, lists");
         if (m->opt.galerkin) build_galerkin_geometry(*m);
         build_tables(*m);
@@ -295,6 +298,7 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
         st.mark("work buffers");
         if (m->opt.near_table) build_near_table(*m, dp);
         st.mark("near-singular table");
+        build_charge_near(*m);
         build_ctq(*m);
         sync(*m);
         st.mark("C^T q");
@@ -360,6 +364,7 @@ int bem_set_charges(bem_mesh *m, const double *charges, int64_t n_c) {
         build_tables(*m);  // the charge tree's separation may have changed
         build_translation_groups(*m, m->tc);
         alloc_work(*m);
+        build_charge_near(*m);
         build_ctq(*m);
         m->have_sigma = false;
         sync(*m);
@@ -468,6 +473,7 @@ static double energy_sorted(Mesh &m, const double *sig_s, double *phi_user) {
     if (!phi_user && m.ctq_ok) return energy_from_ctq(m, sig_s);
     double *phi_s = m.zs.p;  // n_c <= 3 * max(n_p, n_c)
     charge_pass(m, SRC_QUAD, TGT_CHG_PHI, sig_s, phi_s);
+    charge_near_phi(m, sig_s, phi_s, 1, 1);
     const double dG = energy_from_phi(m, phi_s);
     if (phi_user) {
         // phi_reac = (C sigma) / eps_in in the caller's charge order

@@ -196,6 +196,7 @@ void build_ctq(Mesh &m) {
     direct_pass(m, SRC_CHARGE, TGT_QUAD_PHI, nullptr, psi.p);
     k_panel_wsum<<<cdiv(m.np, 256), 256, 0, m.stream>>>(psi.p, m.qp_of_panel.p, m.qw64.p, (int)m.nq, m.np, m.ctq.p);
     BEM_CHECK_LAUNCH();
+    charge_near_ct(m, m.q64.p, m.ctq.p);
     BEM_CUDA(cudaStreamSynchronize(m.stream));
     m.ctq_ok = true;
 }

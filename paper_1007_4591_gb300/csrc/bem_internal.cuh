@@ -290,6 +290,13 @@ struct Mesh {
     // work vectors
     DArray<double> xs, ys, zs;         // sorted-order f64 vectors
     DArray<double> near64;             // near field + 4 pi x near-singular table x (collocation product)
+    // charge-panel pairs integrated exactly (BEM_FLAG_CHARGE_NEAR_EXACT):
+    // panel vertices in sorted order, the (exact - rule) / (4 pi) of each pair's
+    // potential and gradient by charge (CSR), and the potential part by panel
+    DArray<double> pan64;              // [np][9]
+    DArray<int> cn_off, cn_col, cnT_off, cnT_row;
+    DArray<double> cn_val, cnT_val;    // [nnz][4], [nnz]
+    int cn_nnz = 0;
     DArray<float4> str32;              // per-pass near-field source strength records (mixed)
     DArray<double4> str64;             // (fp64 mode)
     DArray<float> far_f, near_f;       // per-target partial results (mixed)
@@ -324,6 +331,15 @@ void rebuild_charge_tree(Mesh &m, const double *d_charges);
 // panels: [np][3][3] f64 device array in the caller's order (read when
 // opt.near_table == BEM_NEAR_EXACT)
 void build_near_table(Mesh &m, const double *panels);
+// exact charge-panel pairs (bem_charge_near.cu): the panel vertices kept at
+// creation, the table built per charge set, and its application to the
+// potential (and gradient) at the charges (C s; stride / ncomp 1 / 1 or 4 / 4
+// for (phi, grad)) and to C^T u (per panel); no-ops unless the flag is set
+bool charge_near_on(const Mesh &m);
+void keep_panel_vertices(Mesh &m, const double *d_panels);
+void build_charge_near(Mesh &m);
+void charge_near_phi(Mesh &m, const double *s_sorted, double *out, int stride, int ncomp);
+void charge_near_ct(Mesh &m, const double *u_sorted, double *v);
 // per panel, its quadrature points' positions in the sorted quadrature order
 void build_qp_of_panel(Mesh &m);
 // the near-singular table's transpose (for K'^T), built on first use
