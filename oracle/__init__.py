@@ -89,6 +89,8 @@ def _load():
             "oracle_kprime_rows_galerkin": (None, [i64, ci, d, d, d, d, d, d, d, i64,
                                                    ctypes.POINTER(ctypes.c_int64), d]),
             "oracle_bq_galerkin": (None, [i64, ci, d, d, d, d, i64, d, d, d]),
+            "oracle_kprime_t_galerkin": (None, [i64, ci, d, d, d, d, d, d, d, d]),
+            "oracle_bt_galerkin": (None, [i64, ci, d, d, d, d, i64, d, d, d, d]),
             "oracle_num_threads": (ci, []),
             "oracle_set_threads": (None, [ci]),
         }
@@ -259,11 +261,48 @@ class Problem:
                                    self.nc, _p(self.xq), _p(q), _p(E))
         return E
 
-    def solve_galerkin(self, tol: float = 1e-10, restart: int = 30, maxiter: int = 500):
-        """sigma from (I + Ehat K'_G) sigma = -Ehat B_G q (Galerkin form)."""
-        b = -self.ehat * self.bq_galerkin()
-        op = lambda v: _c(v) + self.ehat * self.kprime_galerkin(v)
+    def solve_galerkin(self, tol: float = 1e-10, restart: int = 30, maxiter: int = 500,
+                       transpose: bool = False, b=None):
+        """sigma from (I + Ehat K'_G) sigma = -Ehat B_G q (Galerkin form), or
+        with transpose the system (I + Ehat K'_G^T) x = b."""
+        if transpose:
+            op = lambda v: _c(v) + self.ehat * self.kprime_t_galerkin(v)
+        else:
+            op = lambda v: _c(v) + self.ehat * self.kprime_galerkin(v)
+        b = -self.ehat * self.bq_galerkin() if b is None else _c(b)
         return gmres(op, b, tol=tol, restart=restart, maxiter=maxiter)
+
+    def kprime_t_galerkin(self, x):
+        """K'_G^T x, entry for entry the transpose of kprime_galerkin."""
+        x = _c(x)
+        y = np.empty(self.n)
+        _load().oracle_kprime_t_galerkin(self.n, self.nq, _p(self.cen), _p(self.nrm), _p(self.area),
+                                         _p(self.panels), _p(self.qp), _p(self.qw), _p(x), _p(y))
+        return y
+
+    def bt_galerkin(self, v, grad=False):
+        """B_G^T v (and its gradient in the charge positions, [nc, 3])."""
+        v = _c(v)
+        u = np.empty(self.nc)
+        h = np.empty((self.nc, 3)) if grad else None
+        _load().oracle_bt_galerkin(self.n, self.nq, _p(self.nrm), _p(self.area), _p(self.qp), _p(self.qw),
+                                   self.nc, _p(self.xq), _p(v), _p(u),
+                                   _p(h) if grad else ctypes.POINTER(ctypes.c_double)())
+        return (u, h) if grad else u
+
+    def gradients_galerkin(self, tol: float = 1e-12, restart: int = 30, maxiter: int = 1000):
+        """The adjoint gradients of the Galerkin form's energy: as gradients()
+        with K' and B replaced by K'_G and B_G (C is the same)."""
+        sigma, _ = self.solve_galerkin(tol=tol, restart=restart, maxiter=maxiter)
+        lam, _ = self.solve_galerkin(tol=tol, restart=restart, maxiter=maxiter, transpose=True,
+                                     b=self.ct(self.q))
+        pref = 4.0 * np.pi * KCAL_PER_MOL / (2.0 * self.eps_in)
+        phi = self.c(sigma)
+        bt, gbt = self.bt_galerkin(lam, grad=True)
+        dq = pref * (phi - self.ehat * bt)
+        dx = pref * self.q[:, None] * (self.grad_c(sigma) - self.ehat * gbt)
+        dg = pref * float(self.q @ phi)
+        return dg, dq, dx, sigma, lam
 
     def kprime_t(self, x):
         x = _c(x)

@@ -493,6 +493,72 @@ void oracle_kprime_rows_galerkin(int64_t n, int nq, const double *cen, const dou
     }
 }
 
+/* The transpose of the Galerkin K': y_j = sum_{i != j} x_i (K'_G)_ij with
+ * (K'_G)_ij = sum_q (qw_iq / A_i) k_ij(y_iq), the inner integral k_ij over
+ * panel j exact when |c_i - c_j| <= 2.5 sqrt(A_i) and by the rule otherwise
+ * (entry for entry the matrix of oracle_kprime_rows_galerkin). */
+void oracle_kprime_t_galerkin(int64_t n, int nq, const double *cen, const double *nrm,
+                              const double *area, const double *panels, const double *qp,
+                              const double *qw, const double *x, double *y)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (i == j) continue;
+            const double tau = 2.5 * sqrt(area[i]);
+            double d[3];
+            sub3(cen + 3 * i, cen + 3 * j, d);
+            const int near = dot3(d, d) <= tau * tau;
+            double kij = 0.0;
+            for (int q = 0; q < nq; ++q) {
+                const double *t = qp + 3 * (i * nq + q);
+                double k = 0.0;
+                if (near)
+                    k = oracle_panel_dn(t, nrm + 3 * i, panels + 9 * j);
+                else
+                    for (int s2 = 0; s2 < nq; ++s2)
+                        k += qw[j * nq + s2] * dn_green(t, nrm + 3 * i, qp + 3 * (j * nq + s2));
+                kij += qw[i * nq + q] / area[i] * k;
+            }
+            acc += kij * x[i];
+        }
+        y[j] = acc;
+    }
+}
+
+/* The Galerkin B^T v and its gradient in the charge positions:
+ * (B_G)_ik = sum_q (qw_iq / A_i) [-(y_iq - x_k).n_i] / (4 pi |y_iq - x_k|^3),
+ * u_k = sum_i v_i (B_G)_ik, h_k = sum_i v_i grad_{x_k} (B_G)_ik with
+ * grad_{x_k} of one term [n_i / |d|^3 - 3 (d.n_i) d / |d|^5] / (4 pi),
+ * d = y_iq - x_k. */
+void oracle_bt_galerkin(int64_t n, int nq, const double *nrm, const double *area, const double *qp,
+                        const double *qw, int64_t nc, const double *xq, const double *v, double *u,
+                        double *h /* [nc][3] or NULL */)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nc; ++k) {
+        double a = 0.0, g[3] = {0.0, 0.0, 0.0};
+        for (int64_t i = 0; i < n; ++i) {
+            for (int q = 0; q < nq; ++q) {
+                const double *t = qp + 3 * (i * nq + q), *ni = nrm + 3 * i;
+                const double f = v[i] * qw[i * nq + q] / area[i];
+                a += f * dn_green(t, ni, xq + 3 * k);
+                if (h) {
+                    double d[3];
+                    sub3(t, xq + 3 * k, d);
+                    const double r2 = dot3(d, d), r = sqrt(r2), dn = dot3(d, ni);
+                    for (int c = 0; c < 3; ++c)
+                        g[c] += f * (ni[c] / (r2 * r) - 3.0 * dn * d[c] / (r2 * r2 * r)) / FOUR_PI;
+                }
+            }
+        }
+        u[k] = a;
+        if (h)
+            for (int c = 0; c < 3; ++c) h[3 * k + c] = g[c];
+    }
+}
+
 /* Galerkin right-hand side field: the normal field of the charges averaged
  * over each panel by the rule, E_i = sum_q (qw_iq / A_i) E_n(y_iq). */
 void oracle_bq_galerkin(int64_t n, int nq, const double *nrm, const double *area, const double *qp,

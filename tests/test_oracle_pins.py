@@ -22,7 +22,9 @@ index, a transposed operand, a wrong quadrature weight) fails at least one:
   the equilateral centroid closed form, a polar integral on the panel's axis,
   refined quadrature, finite differences of its gradient, the jump of its
   normal derivative, and the uniform-shell potential R inside a sphere for
-  charges just under the surface.
+  charges just under the surface;
+* the Galerkin form's transposes by dot-product identities and entry by
+  entry, its adjoint gradients by central differences and q.(d dG/dq) = 2 dG.
 """
 import os
 
@@ -594,3 +596,47 @@ def test_exact_charge_near_transpose_and_gradient():
             fm = oracle.Problem(Pe.panels, chm, Pe.eps_in, Pe.eps_out, exact_charge_near=True).c(s)[k]
             fd = (fp - fm) / (2 * eps)
             assert abs(g[k, c] - fd) < 1e-6 * max(1.0, abs(fd)), (k, c, g[k, c], fd)
+
+
+# ------------------------------------- Galerkin transposes and gradients
+def test_galerkin_transposes_by_dot_products():
+    m = synth.small_molecule(2, n_charges=12)
+    P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+    rng = np.random.default_rng(8)
+    x, y = rng.normal(size=P.n), rng.normal(size=P.n)
+    kx = P.kprime_galerkin(x)
+    assert abs(kx @ y - x @ P.kprime_t_galerkin(y)) < 1e-12 * np.abs(kx).sum() * np.abs(y).max()
+    # entry for entry: K'_G^T e_j is row j of K'_G, (K'_G e_i)_j for every i
+    eye = np.eye(P.n)
+    for j in (0, 7, P.n - 1):
+        row_j = np.array([P.kprime_rows_galerkin(eye[i], [j])[0] for i in range(P.n)])
+        np.testing.assert_allclose(P.kprime_t_galerkin(eye[j]), row_j, rtol=1e-12, atol=1e-14)
+    q, v = rng.normal(size=P.nc), rng.normal(size=P.n)
+    bq = P.bq_galerkin(q)
+    assert abs(bq @ v - q @ P.bt_galerkin(v)) < 1e-12 * np.linalg.norm(bq) * np.linalg.norm(v)
+
+
+def _energy_galerkin_at(m, charges, tol=1e-13):
+    P = oracle.Problem(m.panels, charges, m.eps_in, m.eps_out)
+    sig, _ = P.solve_galerkin(tol=tol, maxiter=2000)
+    return P.energy(sig)[0]
+
+
+def test_galerkin_gradients_match_central_differences():
+    m = synth.small_molecule(2, n_charges=9)
+    P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+    dg, dq, dx, _, _ = P.gradients_galerkin(tol=1e-13)
+    assert abs(P.q @ dq - 2 * dg) < 1e-8 * abs(dg)     # dG is quadratic in q
+    hq, hx = 1e-4, 1e-4
+    for k in range(0, P.nc, 4):
+        cp, cm = m.charges.copy(), m.charges.copy()
+        cp[k, 3] += hq
+        cm[k, 3] -= hq
+        fd = (_energy_galerkin_at(m, cp) - _energy_galerkin_at(m, cm)) / (2 * hq)
+        assert abs(fd - dq[k]) < 1e-7 * max(1.0, abs(dq[k])), (k, fd, dq[k])
+        for d in range(3):
+            cp, cm = m.charges.copy(), m.charges.copy()
+            cp[k, d] += hx
+            cm[k, d] -= hx
+            fd = (_energy_galerkin_at(m, cp) - _energy_galerkin_at(m, cm)) / (2 * hx)
+            assert abs(fd - dx[k, d]) < 1e-6 * max(1.0, np.abs(dx).max()), (k, d, fd, dx[k, d])
