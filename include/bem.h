@@ -117,9 +117,9 @@ typedef struct bem_options {
     int galerkin;      /* 0 (default) = collocation at the centroids; 1 = Galerkin form with
                           piecewise-constant functions (Sec. 2.1): every row of K' and of the
                           right-hand side field averaged over its panel by the quadrature rule,
-                          near-singular inner integrals exact.  Product, RHS, solve, energy and
-                          BIBEE; the transposed product and the gradients return
-                          BEM_EUNSUPPORTED in this form. */
+                          near-singular inner integrals exact.  Product, RHS, solve, energy,
+                          BIBEE, the transposed product and the gradients (their transposes
+                          place the dipoles at the quadrature points). */
 } bem_options;
 
 #define BEM_M2L_AUTO 0

@@ -10,6 +10,9 @@
 // potential of the charges at the quadrature points summed over each panel.
 // The products between charges and surface are direct sums here; K'^T is a
 // fast multipole pass (fmm_pass_t) plus the transposed near-singular table.
+// In the Galerkin form K' and B are K'_G and B_G (every row averaged over its
+// panel by the rule): their transposes place the dipoles lam_i w_q n_i at the
+// quadrature points of panel i instead of lam_i n_i at its centroid.
 #include <algorithm>
 
 #include "bem_internal.cuh"
@@ -128,7 +131,10 @@ template <class T>
 static void direct_adj(Mesh &m, AdjSrc sk, AdjTgt tk, const double *dens, double *out) {
     cudaStream_t s = m.stream;
     const int64_t ntgt = (tk == AT_CHG_GRAD) ? m.nc : m.nqp;
-    const int64_t nsrc = (sk == AS_QUAD) ? m.nqp : (sk == AS_CHARGE ? m.nc : m.np);
+    // Galerkin: the dipoles of B_G^T sit at every quadrature point, their
+    // moments lam_j w_q in m.lamq (galerkin_moments)
+    const bool gq = sk == AS_DIPOLE && m.opt.galerkin;
+    const int64_t nsrc = (sk == AS_QUAD) ? m.nqp : (sk == AS_CHARGE ? m.nc : (gq ? m.nqp : m.np));
     if (ntgt == 0) return;
     if (nsrc == 0) {
         BEM_CUDA(cudaMemsetAsync(out, 0, ntgt * 4 * sizeof(double), s));
@@ -151,7 +157,8 @@ static void direct_adj(Mesh &m, AdjSrc sk, AdjTgt tk, const double *dens, double
             ntgt, nsrc, chunk, tpos, m.qpg64.p, m.qw64.p, nullptr, m.qp_panel.p, dens, ox, oy, oz, part.p);
     else if (sk == AS_DIPOLE && tk == AT_CHG_GRAD)
         k_direct_adj<T, AS_DIPOLE, AT_CHG_GRAD><<<grid, ADJ_THREADS, 0, s>>>(
-            ntgt, nsrc, chunk, tpos, m.cen64.p, nullptr, m.nrm64.p, nullptr, dens, ox, oy, oz, part.p);
+            ntgt, nsrc, chunk, tpos, gq ? m.qpg64.p : m.cen64.p, nullptr, gq ? m.nrmq64.p : m.nrm64.p, nullptr,
+            gq ? m.lamq.p : dens, ox, oy, oz, part.p);
     else if (sk == AS_CHARGE && tk == AT_QUAD_PHI)
         k_direct_adj<T, AS_CHARGE, AT_QUAD_PHI><<<grid, ADJ_THREADS, 0, s>>>(
             ntgt, nsrc, chunk, tpos, m.chgg64.p, m.q64.p, nullptr, nullptr, nullptr, ox, oy, oz, part.p);
@@ -183,7 +190,6 @@ __global__ void k_apply_At(const double *x, const double *ktx, const int *off, c
 }
 
 void matvec_t_sorted(Mesh &m, const double *xs, double *ys) {
-    if (m.opt.galerkin) throw Error(BEM_EUNSUPPORTED, "the transposed product is not built for the Galerkin form");
     const bool nt = m.nt_nnz > 0 && !(m.opt.flags & (BEM_FLAG_NO_NEARTAB | BEM_FLAG_NO_NEAR));
     if (nt) transpose_near_table(m);
     fmm_pass_t(m, xs, m.zs.p);
@@ -216,7 +222,6 @@ __global__ void k_gradients(const double *cs4, const double *bl4, const double *
 void build_qp_of_panel(Mesh &m);
 
 void adjoint_gradients(Mesh &m, double grad_out, double *dq_s, double *dx_s) {
-    if (m.opt.galerkin) throw Error(BEM_EUNSUPPORTED, "gradients are not built for the Galerkin form");
     cudaStream_t s = m.stream;
     build_qp_of_panel(m);
     const int64_t np = m.np, nc = m.nc;
@@ -239,6 +244,8 @@ void adjoint_gradients(Mesh &m, double grad_out, double *dq_s, double *dx_s) {
     bem_solve_stats st{};
     gmres_solve(m, rhs.p, lam.p, true, &st);
     // B^T lam and its gradient: dipoles lam_i n_i at the collocation points
+    // (Galerkin: lam_i w_q n_i at the quadrature points)
+    if (m.opt.galerkin) galerkin_moments(m, lam.p);
     direct_adjoint(m, AS_DIPOLE, AT_CHG_GRAD, lam.p, bl4.p);
     const double pref = grad_out * FOUR_PI * KCAL / (2.0 * m.eps_in);
     k_gradients<<<cdiv(nc, 256), 256, 0, s>>>(cs4.p, bl4.p, m.q64.p, m.ehat, pref, nc, dq_s, dx_s);

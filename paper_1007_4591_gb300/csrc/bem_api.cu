@@ -136,7 +136,7 @@ size_t Mesh::bytes() const {
     if (tab) b += tab->bytes();
     if (tab2) b += tab2->bytes();
     b += Mf.bytes() + Lf.bytes() + Md.bytes() + Ld.bytes();
-    b += pan64.bytes() + cn_off.bytes() + cn_col.bytes() + cn_val.bytes() + cnT_off.bytes() + cnT_row.bytes() +
+    b += lamq.bytes() + pan64.bytes() + cn_off.bytes() + cn_col.bytes() + cn_val.bytes() + cnT_off.bytes() + cnT_row.bytes() +
          cnT_val.bytes();
     b += Mtc.bytes() + ctq.bytes() + str32.bytes() + str64.bytes() + near64.bytes() + dpart_f.bytes() +
          dpart_d.bytes();

@@ -776,13 +776,13 @@ k_p2p(P2PList wl, const typename V4T<T>::t *tgt, const typename V4T<T>::t *nrm,
 //   M_n^m = sum_{l=-1..1} conj(R_{n-1}^{m-l}(c - z)) D_1^l,
 // accumulated here while the recurrence emits R_k^l (scaled by 1/h).
 template <class T>
-__global__ void k_p2m_dipole(TreeView tv, const typename V4T<T>::t *rec,
+__global__ void k_p2m_dipole(TreeView tv, const int *dbeg, const typename V4T<T>::t *rec,
                              const typename V4T<T>::t *nrm, const double *lam, int p, int cs,
                              T inv_h, T *M) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sh = reinterpret_cast<T *>(smraw);
     const int leaf = blockIdx.x;
-    const int b = tv.cen_beg[leaf], e = tv.cen_beg[leaf + 1];
+    const int b = dbeg[leaf], e = dbeg[leaf + 1];
     const int nc = (p + 1) * (p + 1);
     constexpr int MAXACC = 10;
     T acc[MAXACC];
@@ -849,14 +849,14 @@ __global__ void k_p2m_dipole(TreeView tv, const typename V4T<T>::t *rec,
 // per point and CTA.
 template <class T>
 __global__ void __launch_bounds__(P2P_THREADS)
-k_p2p_t(TreeView tv, const typename V4T<T>::t *cen, const typename V4T<T>::t *nrm,
+k_p2p_t(TreeView tv, const int *dbeg, const typename V4T<T>::t *cen, const typename V4T<T>::t *nrm,
         const double *lam, const typename V4T<T>::t *qrec, T h, T *outq) {
     using V4 = typename V4T<T>::t;
     __shared__ V4 sc[P2P_THREADS], sn[P2P_THREADS];
     __shared__ int s_beg[28], s_cum[28];
     __shared__ T s_off[27][3];
     const int leaf = tv.p2p_order[blockIdx.x];
-    const int tb = tv.cen_beg[leaf], te = tv.cen_beg[leaf + 1];
+    const int tb = dbeg[leaf], te = dbeg[leaf + 1];
     if (tb == te) return;
     const int nb0 = tv.nbr_off[leaf], nn = tv.nbr_off[leaf + 1] - nb0;
     const int4 ct = tv.ijk[tv.leaf0 + leaf];
@@ -2492,6 +2492,22 @@ static void m2l_dense(Mesh &m, const Tree &t, const T *Oop, int nc, int cs, int 
     BEM_CHECK_LAUNCH();
 }
 
+// Galerkin dipole moments per quadrature point: lam of its panel times the
+// rule's weight on that panel, w_q = qw / A
+__global__ void k_lam_quad(const double *lam, const int *qp_panel, const double *qw, const double *area, int64_t nqp,
+                           double *out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nqp) return;
+    const int j = qp_panel[i];
+    out[i] = lam[j] * (qw[i] / area[j]);
+}
+
+void galerkin_moments(Mesh &m, const double *lam) {
+    if (m.lamq.n < (size_t)m.nqp) m.lamq.alloc(m.nqp);
+    k_lam_quad<<<cdiv(m.nqp, 256), 256, 0, m.stream>>>(lam, m.qp_panel.p, m.qw64.p, m.area64.p, m.nqp, m.lamq.p);
+    BEM_CHECK_LAUNCH();
+}
+
 template <class T>
 static void run_pass_t(Mesh &m, const double *lam, double *out) {
     using B = PassBufs<T>;
@@ -2509,9 +2525,22 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
     T *far_b = B::far(m), *near_b = B::near(m);
     build_qp_of_panel(m);
     const bool conc = near && m.stream2;
+    // the dipoles: lam_i n_i at the collocation points, or for the Galerkin
+    // rows lam_i w_q n_i at every quadrature point of panel i
+    const int *dbeg = tv.cen_beg;
+    const typename V4T<T>::t *drec = B::cen(m), *dnrm = B::nrm(m);
+    const double *dlam = lam;
+    if (m.opt.galerkin) {
+        if (!B::nrmq(m)) throw Error(BEM_ECUDA, "quadrature-point normals not built");
+        galerkin_moments(m, lam);
+        dbeg = tv.qp_beg;
+        drec = B::qp(m);
+        dnrm = B::nrmq(m);
+        dlam = m.lamq.p;
+    }
     auto launch_near = [&](cudaStream_t ss) {
         BEM_CUDA(cudaMemsetAsync(near_b, 0, m.nqp * sizeof(T), ss));
-        k_p2p_t<T><<<t.nleaf, P2P_THREADS, 0, ss>>>(tv, B::cen(m), B::nrm(m), lam, B::qp(m), (T)h, near_b);
+        k_p2p_t<T><<<t.nleaf, P2P_THREADS, 0, ss>>>(tv, dbeg, drec, dnrm, dlam, B::qp(m), (T)h, near_b);
         BEM_CHECK_LAUNCH();
     };
     if (conc) {
@@ -2529,7 +2558,7 @@ static void run_pass_t(Mesh &m, const double *lam, double *out) {
             const int th = std::max(32, p2m_threads(p, sizeof(T)));
             const size_t sm = (size_t)th * nc * sizeof(T);
             set_smem<T>(k_p2m_dipole<T>, sm);
-            k_p2m_dipole<T><<<t.nleaf, th, sm, s>>>(tv, B::cen(m), B::nrm(m), lam, p, cs, inv_h, M);
+            k_p2m_dipole<T><<<t.nleaf, th, sm, s>>>(tv, dbeg, drec, dnrm, dlam, p, cs, inv_h, M);
             BEM_CHECK_LAUNCH();
         }
         if (t.L >= 3)

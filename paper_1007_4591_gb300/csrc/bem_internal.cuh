@@ -252,6 +252,7 @@ struct Mesh {
     DArray<double4> nrmq64r;
     DArray<double> nrmq64;
     DArray<double> gq_tmp;             // [nqp] Galerkin scratch (direct sums at the quadrature points)
+    DArray<double> lamq;               // [nqp] Galerkin dipole moments of the transposed product / B_G^T
     DArray<double> ctq;                // [np] C^T q (sorted panels), valid when ctq_ok
     bool ctq_ok = false;
     DArray<uint64_t> cen_key;
@@ -335,6 +336,8 @@ void build_near_table(Mesh &m, const double *panels);
 // creation, the table built per charge set, and its application to the
 // potential (and gradient) at the charges (C s; stride / ncomp 1 / 1 or 4 / 4
 // for (phi, grad)) and to C^T u (per panel); no-ops unless the flag is set
+// Galerkin dipole moments lam_j w_q at every quadrature point (into m.lamq)
+void galerkin_moments(Mesh &m, const double *lam);
 bool charge_near_on(const Mesh &m);
 void keep_panel_vertices(Mesh &m, const double *d_panels);
 void build_charge_near(Mesh &m);

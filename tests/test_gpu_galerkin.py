@@ -1,7 +1,7 @@
 """The Galerkin form (galerkin = 1) on the GPU against the oracle's Galerkin
-rows, right-hand side and solve: every row of K' and of the right-hand side
-field averaged over its panel by the quadrature rule, near-singular inner
-integrals exact."""
+rows, right-hand side, solve, transposed product and adjoint gradients:
+every row of K' and of the right-hand side field averaged over its panel by
+the quadrature rule, near-singular inner integrals exact."""
 import numpy as np
 import pytest
 
@@ -72,9 +72,40 @@ def test_galerkin_born_ion(pkg):
     assert abs(dg - born) < 0.004 * abs(born), (dg, born)     # collocation: 1.25 % at this mesh
 
 
-def test_galerkin_transpose_and_gradients_unsupported(pkg):
-    m = synth.small_molecule(2)
-    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, galerkin=1) as g:
-        with pytest.raises(pkg.BemError) as ei:
-            g.matvec_t(torch.zeros(m.n_p, dtype=torch.float64, device="cuda"))
-        assert ei.value.code == pkg.BEM_EUNSUPPORTED
+@pytest.mark.parametrize("precision", [0, 1])
+def test_galerkin_transposed_product_matches_oracle(pkg, precision):
+    """A_G^T x = x + Ehat K'_G^T x: the dipoles lam_i w_q n_i at the quadrature
+    points of panel i, the transposed Galerkin near-singular table."""
+    m = synth.small_molecule(4)
+    P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+    x = np.random.default_rng(35).standard_normal(m.n_p)
+    ref = x + P.ehat * P.kprime_t_galerkin(x)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=12, precision=precision, galerkin=1) as g:
+        y = g.matvec_t(torch.from_numpy(x).cuda()).cpu().numpy()
+    close(y, ref, 1e-5)
+    # a different operator from the collocation transpose
+    col = x + P.ehat * P.kprime_t(x)
+    assert rel(col, ref) > 10 * rel(y, ref)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_galerkin_gradients_match_oracle(pkg, precision):
+    """d dG/dq and d dG/dx of the Galerkin form by the adjoint (A_G^T lam =
+    C^T q, B_G^T lam and its gradient with the dipoles at the quadrature
+    points) against the oracle's dense Galerkin adjoint."""
+    m = synth.small_molecule(3)
+    P = oracle.Problem(m.panels, m.charges, m.eps_in, m.eps_out)
+    dg_ref, dq_ref, dx_ref, sig_ref, _ = P.gradients_galerkin(tol=1e-12)
+    with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, p=12, tol=1e-11, precision=precision,
+                  galerkin=1) as g:
+        s, st = g.solve()
+        assert st["converged"] == 1
+        dg = g.energy(s)
+        dq, dx = g.energy_backward(1.0)
+    close(s.cpu().numpy(), sig_ref, 1e-5, what="sigma")
+    assert abs(dg - dg_ref) < 1e-5 * abs(dg_ref), (dg, dg_ref)
+    close(dq.cpu().numpy(), dq_ref, 1e-5, what="dq")
+    close(dx.cpu().numpy(), dx_ref, 1e-5, what="dx")
+    # not the collocation gradients
+    _, _, dx_col, _, _ = P.gradients(tol=1e-12)
+    assert rel(dx_col, dx_ref) > 10 * rel(dx.cpu().numpy(), dx_ref)
