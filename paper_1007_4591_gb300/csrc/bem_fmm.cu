@@ -1380,12 +1380,10 @@ static std::shared_ptr<Tables> make_tables(int p, int prec, int ws) {
         }, &ol2l[(size_t)o * osz]);
     }
     if (prec == BEM_MIXED && nc <= 128) {
-        std::vector<float> hi, lo;
-        build_tc_tables(p, om2l, NOFFSET, hi, lo);
-        t->Tc_hi.alloc(hi.size());
-        t->Tc_lo.alloc(lo.size());
-        BEM_CUDA(cudaMemcpy(t->Tc_hi.p, hi.data(), hi.size() * sizeof(float), cudaMemcpyHostToDevice));
-        BEM_CUDA(cudaMemcpy(t->Tc_lo.p, lo.data(), lo.size() * sizeof(float), cudaMemcpyHostToDevice));
+        std::vector<float> op;
+        build_tc_tables(p, om2l, NOFFSET, op);
+        t->Tc_f.alloc(op.size());
+        BEM_CUDA(cudaMemcpy(t->Tc_f.p, op.data(), op.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
     // translation operators with each [in] row padded to the cell stride, so
     // that k_translate stages them with 16-byte copies

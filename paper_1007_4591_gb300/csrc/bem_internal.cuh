@@ -201,9 +201,10 @@ struct Tables {
     int ws = 1;                   // the M2L operators cover the offset classes of this separation
     DArray<float> Rm2m_f, If_f, Om2l_f, Om2m_f, Ol2l_f;
     DArray<double> Rm2m_d, If_d, Om2l_d, Om2m_d, Ol2l_d;
-    DArray<float> Tc_hi, Tc_lo;   // M2L operators split for 3xTF32, tensor-core tile order
+    DArray<float> Tc_f;           // M2L operators in FP32, tensor-core tile order (the kernel
+                                  // splits them into their TF32 hi / lo parts as it loads them)
     size_t bytes() const {
-        return Tc_hi.bytes() + Tc_lo.bytes() + Rm2m_f.bytes() + If_f.bytes() + Om2l_f.bytes() + Om2m_f.bytes() + Ol2l_f.bytes() +
+        return Tc_f.bytes() + Rm2m_f.bytes() + If_f.bytes() + Om2l_f.bytes() + Om2m_f.bytes() + Ol2l_f.bytes() +
                Rm2m_d.bytes() + If_d.bytes() + Om2l_d.bytes() + Om2m_d.bytes() + Ol2l_d.bytes();
     }
 };
@@ -368,8 +369,7 @@ int64_t unique_sorted_u64(const uint64_t *in, uint64_t *out, int64_t n, cudaStre
 void build_translation_groups(Mesh &m, Tree &t);
 // tensor-core M2L (bem_tc.cu)
 bool tc_m2l_available(const Mesh &m);
-void build_tc_tables(int p, const std::vector<double> &om2l, int nops, std::vector<float> &hi,
-                     std::vector<float> &lo);
+void build_tc_tables(int p, const std::vector<double> &om2l, int nops, std::vector<float> &op);
 void build_tc_super(Tree &t, const std::vector<int4> &chunks_m2l, cudaStream_t s);
 void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed = false);
 bool use_tc_m2l(const Mesh &m);

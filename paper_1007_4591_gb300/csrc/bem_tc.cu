@@ -129,8 +129,8 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *g, uint32_t bytes) 
 //    g % TC_NS (cp.async: a warp instruction moves four 128-byte rows,
 //    written in the 128-byte swizzle; mbarrier fullB).  After the first tile
 //    of an item they wait for the last MMA of the previous item (its fullD
-//    commit) and write the item's operator (hi | lo TF32 parts) into tensor
-//    memory (aReady).
+//    commit) and write the item's operator into tensor memory (aReady),
+//    split from FP32 into its TF32 hi and lo parts on the way.
 //  * MMA (warp 0, lane 0): per item waits aReady; per tile waits a free
 //    accumulator (emptyD), per K-block its stage (fullB), issues 4 K-steps x
 //    3 products with A from tensor memory and commits to emptyB; after the
@@ -140,7 +140,7 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *g, uint32_t bytes) 
 //    expansion row of cs floats per pair), then the 128 threads add the rows
 //    into their target cells of `out`, four coefficients per reduction.
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
+k_m2l_tc(const float *__restrict__ A_all,
          const int4 *__restrict__ items, int nitems, int *__restrict__ next_item,
          const int *__restrict__ p_out, const int *__restrict__ p_in, int cs,
          const float *__restrict__ Mtc, float *__restrict__ out, int *__restrict__ err,
@@ -202,8 +202,7 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                 const int idx = atomicAdd(next_item, 1);
                 const int4 it = idx < nitems ? items[idx] : make_int4(-1, 0, 0, 0);
                 if (it.x >= 0) {
-                    bulk_prefetch_l2(Ahi_all + (size_t)it.x * TC_K * TC_K, TC_K * TC_K * 4);
-                    bulk_prefetch_l2(Alo_all + (size_t)it.x * TC_K * TC_K, TC_K * TC_K * 4);
+                    bulk_prefetch_l2(A_all + (size_t)it.x * TC_K * TC_K, TC_K * TC_K * 4);
                 }
                 s_item[slot] = it;
                 mbar_arrive(smem_u32(&itemFull[slot]));
@@ -263,35 +262,37 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     // operator layout [k / 4][row][k % 4]: the warp's rows read 512
-                    // contiguous bytes per load
-                    const float4 *gh = reinterpret_cast<const float4 *>(Ahi_all + (size_t)sc.x * TC_K * TC_K) + row;
-                    const float4 *gl = reinterpret_cast<const float4 *>(Alo_all + (size_t)sc.x * TC_K * TC_K) + row;
+                    // contiguous bytes per load; 32 coefficients at a time, each
+                    // split into its TF32 hi part and the TF32 rest (the 3xTF32
+                    // operands) and stored to both halves of the operator's columns
+                    const float4 *ga = reinterpret_cast<const float4 *>(A_all + (size_t)sc.x * TC_K * TC_K) + row;
 #pragma unroll 1
                     for (int part = 0; part < 4; ++part) {
-                        const float4 *gp = (part < 2 ? gh : gl) + (part & 1) * 16 * TC_K;
-                        const uint32_t col = (part < 2 ? TC_A_HI : TC_A_LO) + (part & 1) * 64;
-                        uint32_t v[64];
+                        const float4 *gp = ga + part * 8 * TC_K;
+                        uint32_t vh[32], vl[32];
 #pragma unroll
-                        for (int q = 0; q < 64; q += 4) {
+                        for (int q = 0; q < 32; q += 4) {
                             const float4 f = __ldg(gp + (q >> 2) * TC_K);
-                            v[q] = __float_as_uint(f.x);
-                            v[q + 1] = __float_as_uint(f.y);
-                            v[q + 2] = __float_as_uint(f.z);
-                            v[q + 3] = __float_as_uint(f.w);
+                            const float x[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                vh[q + e] = to_tf32(x[e]);
+                                vl[q + e] = to_tf32(x[e] - __uint_as_float(vh[q + e]));
+                            }
                         }
 #pragma unroll
-                        for (int h = 0; h < 64; h += 32) {
+                        for (int hl = 0; hl < 2; ++hl) {
+                            const uint32_t *v = hl ? vl : vh;
                             asm volatile(
                                 "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
                                 "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(
-                                    tm + ((uint32_t)(32 * quad) << 16) + col + (uint32_t)h),
-                                "r"(v[h + 0]), "r"(v[h + 1]), "r"(v[h + 2]), "r"(v[h + 3]), "r"(v[h + 4]),
-                                "r"(v[h + 5]), "r"(v[h + 6]), "r"(v[h + 7]), "r"(v[h + 8]), "r"(v[h + 9]),
-                                "r"(v[h + 10]), "r"(v[h + 11]), "r"(v[h + 12]), "r"(v[h + 13]), "r"(v[h + 14]),
-                                "r"(v[h + 15]), "r"(v[h + 16]), "r"(v[h + 17]), "r"(v[h + 18]), "r"(v[h + 19]),
-                                "r"(v[h + 20]), "r"(v[h + 21]), "r"(v[h + 22]), "r"(v[h + 23]), "r"(v[h + 24]),
-                                "r"(v[h + 25]), "r"(v[h + 26]), "r"(v[h + 27]), "r"(v[h + 28]), "r"(v[h + 29]),
-                                "r"(v[h + 30]), "r"(v[h + 31]));
+                                    tm + ((uint32_t)(32 * quad) << 16) + (uint32_t)(hl ? TC_A_LO : TC_A_HI) +
+                                    (uint32_t)(32 * part)),
+                                "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+                                "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]),
+                                "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]),
+                                "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+                                "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]));
                         }
                     }
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -466,37 +467,19 @@ k_m2l_tc(const float *__restrict__ Ahi_all, const float *__restrict__ Alo_all,
 }
 
 // ---------------------------------------------------------------- host side
-static inline float host_tf32(float x) {
-    // round to nearest (ties away from zero) keeping 10 explicit mantissa bits
-    uint32_t u;
-    std::memcpy(&u, &x, 4);
-    if ((u & 0x7F800000u) == 0x7F800000u) return x;
-    u = (u + 0x1000u) & 0xFFFFE000u;
-    float r;
-    std::memcpy(&r, &u, 4);
-    return r;
-}
-
-// hi/lo TF32 parts of the M2L operators, [offset][k / 4][row = output
-// coefficient][k % 4] (k = input coefficient), zero-padded to 128 x 128: the
-// kernel writes row r into tensor-memory lane r, and the 32 rows of a warp
-// read 4 consecutive coefficients each from 512 contiguous bytes
-void build_tc_tables(int p, const std::vector<double> &om2l, int nops, std::vector<float> &hi,
-                     std::vector<float> &lo) {
+// The M2L operators in FP32, [offset][k / 4][row = output coefficient][k % 4]
+// (k = input coefficient), zero-padded to 128 x 128: the kernel writes row r
+// into tensor-memory lane r (its TF32 hi and lo parts), and the 32 rows of a
+// warp read 4 consecutive coefficients each from 512 contiguous bytes
+void build_tc_tables(int p, const std::vector<double> &om2l, int nops, std::vector<float> &op) {
     const int nc = (p + 1) * (p + 1);
-    hi.assign((size_t)nops * TC_K * TC_K, 0.f);
-    lo.assign((size_t)nops * TC_K * TC_K, 0.f);
+    op.assign((size_t)nops * TC_K * TC_K, 0.f);
     for (int o = 0; o < nops; ++o) {
         const double *T = &om2l[(size_t)o * nc * nc];
-        float *H = &hi[(size_t)o * TC_K * TC_K], *L = &lo[(size_t)o * TC_K * TC_K];
+        float *A = &op[(size_t)o * TC_K * TC_K];
         for (int row = 0; row < nc; ++row)
-            for (int k = 0; k < nc; ++k) {
-                const float x = (float)T[(size_t)k * nc + row];
-                const float h = host_tf32(x);
-                const size_t at = ((size_t)(k >> 2) * TC_K + row) * 4 + (k & 3);
-                H[at] = h;
-                L[at] = host_tf32(x - h);
-            }
+            for (int k = 0; k < nc; ++k)
+                A[((size_t)(k >> 2) * TC_K + row) * 4 + (k & 3)] = (float)T[(size_t)k * nc + row];
     }
 }
 
@@ -529,16 +512,28 @@ void build_tc_super(Tree &t, const std::vector<int4> &chunks_m2l, cudaStream_t s
 }
 
 // hi/lo TF32 split of the multipoles of the M2L sources (cells of levels
-// >= 2), rows of 2 x 128 floats: hi | lo, zero beyond (p+1)^2
+// >= 2), rows of 2 x 128 floats: hi | lo, zero beyond (p+1)^2.  One thread
+// per 4 coefficients of a cell (16-byte loads and stores; cs is a multiple
+// of 4, and a group at or past cs is not read).
 __global__ void k_split_m(const float *M, int first, int ncell, int nc, int cs, float *Mtc) {
-    const int c = first + blockIdx.x;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t c = first + (i >> 5);
+    const int k0 = 4 * (int)(i & 31);
     if (c >= ncell) return;
-    for (int k = threadIdx.x; k < TC_K; k += blockDim.x) {
-        const float x = k < nc ? M[(size_t)c * cs + k] : 0.f;
-        const uint32_t h = to_tf32(x);
-        Mtc[(size_t)c * 2 * TC_K + k] = __uint_as_float(h);
-        Mtc[(size_t)c * 2 * TC_K + TC_K + k] = __uint_as_float(to_tf32(x - __uint_as_float(h)));
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k0 < cs) x = *reinterpret_cast<const float4 *>(M + c * cs + k0);
+    float v[4] = {x.x, x.y, x.z, x.w};
+    float h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (k0 + e >= nc) v[e] = 0.f;
+        const uint32_t t = to_tf32(v[e]);
+        h[e] = __uint_as_float(t);
+        l[e] = __uint_as_float(to_tf32(v[e] - h[e]));
     }
+    float *row = Mtc + c * 2 * TC_K;
+    *reinterpret_cast<float4 *>(row + k0) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4 *>(row + TC_K + k0) = make_float4(l[0], l[1], l[2], l[3]);
 }
 
 // L (levels >= 2) = sum over the M2L pairs of T_o M_s: L cleared, the
@@ -557,7 +552,8 @@ void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed) {
         if (tk) BEM_CUDA(cudaEventRecord(m.tm.kev[k], m.stream));
     };
     kev(0);
-    k_split_m<<<t.ncell - first, 128, 0, m.stream>>>(M, first, t.ncell, nc, cs, m.Mtc.p);
+    if (cs % 4 != 0) throw Error(BEM_ECUDA, "tensor-core staging: cell stride not a multiple of 4");
+    k_split_m<<<cdiv((int64_t)(t.ncell - first) * 32, 256), 256, 0, m.stream>>>(M, first, t.ncell, nc, cs, m.Mtc.p);
     BEM_CHECK_LAUNCH();
     const size_t sm = tc_smem_bytes();
     int dev = 0, nsm = 0;
@@ -567,7 +563,7 @@ void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed) {
     BEM_CUDA(cudaMemsetAsync(m.dev_err.p + 1, 0, sizeof(int), m.stream));  // work-item counter
     kev(1);
     ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc), sm);
-    k_m2l_tc<<<grid, TC_THREADS, sm, m.stream>>>(tb.Tc_hi.p, tb.Tc_lo.p, t.tc_super.p, t.tc_nsuper, m.dev_err.p + 1,
+    k_m2l_tc<<<grid, TC_THREADS, sm, m.stream>>>(tb.Tc_f.p, t.tc_super.p, t.tc_nsuper, m.dev_err.p + 1,
                                                  t.g_out.p, t.g_in.p, cs, m.Mtc.p, L, m.dev_err.p, m.wait_budget);
     BEM_CHECK_LAUNCH();
     kev(2);
