@@ -42,14 +42,25 @@ k_direct_adj(int64_t ntgt, int64_t nsrc, int64_t chunk, const double *tpos, cons
              const double *sw, const double *snrm, const int *qpanel, const double *dens, double ox,
              double oy, double oz, T *part) {
     using V4 = typename V4A<T>::t;
+    // FP32: coordinates as hi + lo pairs, differences (hi - hi) + (lo - lo)
+    // (exact first term for nearby points; see k_direct)
+    constexpr bool SPLIT = sizeof(T) == 4;
     __shared__ V4 sa[ADJ_THREADS], sb[ADJ_THREADS];
+    __shared__ float4 sl[SPLIT ? ADJ_THREADS : 1];
     const int64_t i = blockIdx.x * (int64_t)ADJ_THREADS + threadIdx.x;
     const int64_t s0 = (int64_t)blockIdx.y * chunk, s1 = min(nsrc, s0 + chunk);
     T x = 0, y = 0, z = 0;
+    float lx = 0.f, ly = 0.f, lz = 0.f;
     if (i < ntgt) {
-        x = (T)(tpos[3 * i] - ox);
-        y = (T)(tpos[3 * i + 1] - oy);
-        z = (T)(tpos[3 * i + 2] - oz);
+        const double px = tpos[3 * i] - ox, py = tpos[3 * i + 1] - oy, pz = tpos[3 * i + 2] - oz;
+        x = (T)px;
+        y = (T)py;
+        z = (T)pz;
+        if (SPLIT) {
+            lx = (float)(px - (double)x);
+            ly = (float)(py - (double)y);
+            lz = (float)(pz - (double)z);
+        }
     }
     T o0 = 0, o1 = 0, o2 = 0, o3 = 0;
     for (int64_t b = s0; b < s1; b += ADJ_THREADS) {
@@ -58,10 +69,13 @@ k_direct_adj(int64_t ntgt, int64_t nsrc, int64_t chunk, const double *tpos, cons
         V4 a, c;
         a.x = a.y = a.z = a.w = 0;
         c.x = c.y = c.z = c.w = 0;
+        float4 al = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k < s1) {
-            a.x = (T)(spos[3 * k] - ox);
-            a.y = (T)(spos[3 * k + 1] - oy);
-            a.z = (T)(spos[3 * k + 2] - oz);
+            const double px = spos[3 * k] - ox, py = spos[3 * k + 1] - oy, pz = spos[3 * k + 2] - oz;
+            a.x = (T)px;
+            a.y = (T)py;
+            a.z = (T)pz;
+            if (SPLIT) al = make_float4((float)(px - (double)a.x), (float)(py - (double)a.y), (float)(pz - (double)a.z), 0.f);
             if (SK == AS_QUAD) a.w = (T)(sw[k] * dens[qpanel[k]]);
             else if (SK == AS_CHARGE) a.w = (T)sw[k];
             else {
@@ -73,12 +87,19 @@ k_direct_adj(int64_t ntgt, int64_t nsrc, int64_t chunk, const double *tpos, cons
         }
         sa[threadIdx.x] = a;
         sb[threadIdx.x] = c;
+        if (SPLIT) sl[threadIdx.x] = al;
         __syncthreads();
         const int cnt = (int)min((int64_t)ADJ_THREADS, s1 - b);
         T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         for (int j = 0; j < cnt; ++j) {
             const V4 sp = sa[j];
-            const T dx = x - sp.x, dy = y - sp.y, dz = z - sp.z;
+            T dx = x - sp.x, dy = y - sp.y, dz = z - sp.z;
+            if (SPLIT) {
+                const float4 q = sl[j];
+                dx += (T)(lx - q.x);
+                dy += (T)(ly - q.y);
+                dz += (T)(lz - q.z);
+            }
             const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
             if (r2 == (T)0) continue;  // a dummy slot or a coincident point
             const T ri = rsqa(r2), ri3 = ri * ri * ri;

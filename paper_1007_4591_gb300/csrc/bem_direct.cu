@@ -8,10 +8,15 @@
 // whose truncation error converges only like (sqrt(3)/2)^p.  Large systems
 // (many molecules) use the fast multipole pass; opt.charge_mode selects.
 //
-// Coordinates are taken relative to the root-cube centre and rounded to the
-// kernel precision when a source tile is staged; each thread sums one tile
-// in a short accumulator and adds the tile total to a second one, and the
-// partial sums of the source splits are reduced in FP64.
+// Coordinates are taken relative to the root-cube centre; in FP32 each one is
+// carried as a pair hi + lo (hi = the FP32 rounding, lo = the FP32 rounding of
+// the rest) and a difference is formed as (hi_t - hi_s) + (lo_t - lo_s): the
+// first term is exact for nearby points, so a pair's difference keeps about
+// 2^-24 of its own length instead of 2^-24 of the distance from the centre
+// (charges a few hundredths of an A from a quadrature or collocation point).
+// Each thread sums one tile in a short accumulator and adds the tile total
+// to a second one, and the partial sums of the source splits are reduced in
+// FP64.
 #include "bem_internal.cuh"
 
 namespace bem {
@@ -32,16 +37,25 @@ k_direct(int64_t ntgt, int64_t nsrc, int64_t chunk, const double *tpos, const do
          const double *spos, const double *sw, const int *qpanel, const double *dens, double ox,
          double oy, double oz, T *part) {
     using V4 = typename V4D<T>::t;
+    constexpr bool SPLIT = sizeof(T) == 4;  // coordinates as hi + lo pairs
     __shared__ V4 sh[DIRECT_THREADS];
+    __shared__ float4 shl[SPLIT ? DIRECT_THREADS : 1];
     const int64_t i = blockIdx.x * (int64_t)DIRECT_THREADS + threadIdx.x;
     const int64_t sb = (int64_t)blockIdx.y * chunk;
     const int64_t se = min(nsrc, sb + chunk);
     constexpr bool DN = TGT == TGT_CEN_DN || TGT == TGT_QUAD_DN;  // normal field, else potential
     T cx = 0, cy = 0, cz = 0, nx = 0, ny = 0, nz = 0;
+    float lx = 0.f, ly = 0.f, lz = 0.f;
     if (i < ntgt) {
-        cx = (T)(tpos[3 * i] - ox);
-        cy = (T)(tpos[3 * i + 1] - oy);
-        cz = (T)(tpos[3 * i + 2] - oz);
+        const double px = tpos[3 * i] - ox, py = tpos[3 * i + 1] - oy, pz = tpos[3 * i + 2] - oz;
+        cx = (T)px;
+        cy = (T)py;
+        cz = (T)pz;
+        if (SPLIT) {
+            lx = (float)(px - (double)cx);
+            ly = (float)(py - (double)cy);
+            lz = (float)(pz - (double)cz);
+        }
         if (DN) {
             nx = (T)tnrm[3 * i];
             ny = (T)tnrm[3 * i + 1];
@@ -54,23 +68,33 @@ k_direct(int64_t ntgt, int64_t nsrc, int64_t chunk, const double *tpos, const do
         const int64_t k = b + threadIdx.x;
         V4 r;
         r.x = r.y = r.z = r.w = 0;
+        float4 rl = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k < se) {
-            r.x = (T)(spos[3 * k] - ox);
-            r.y = (T)(spos[3 * k + 1] - oy);
-            r.z = (T)(spos[3 * k + 2] - oz);
+            const double px = spos[3 * k] - ox, py = spos[3 * k + 1] - oy, pz = spos[3 * k + 2] - oz;
+            r.x = (T)px;
+            r.y = (T)py;
+            r.z = (T)pz;
+            if (SPLIT) rl = make_float4((float)(px - (double)r.x), (float)(py - (double)r.y), (float)(pz - (double)r.z), 0.f);
             double w;
             if (SRC == SRC_QUAD) w = sw[k] * dens[qpanel[k]];
             else w = dens ? dens[k] : sw[k];
             r.w = (T)w;
         }
         sh[threadIdx.x] = r;
+        if (SPLIT) shl[threadIdx.x] = rl;
         __syncthreads();
         const int cnt = (int)min((int64_t)DIRECT_THREADS, se - b);
         T acc = 0;
 #pragma unroll 4
         for (int j = 0; j < cnt; ++j) {
             const V4 y = sh[j];
-            const T dx = cx - y.x, dy = cy - y.y, dz = cz - y.z;
+            T dx = cx - y.x, dy = cy - y.y, dz = cz - y.z;
+            if (SPLIT) {
+                const float4 yl = shl[j];
+                dx += (T)(lx - yl.x);
+                dy += (T)(ly - yl.y);
+                dz += (T)(lz - yl.z);
+            }
             const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
             const T ri = rsqd(r2);
             if (DN) {

@@ -3,8 +3,8 @@ C s, C^T q and grad_x C s with every charge-panel pair closer than
 2.5 sqrt(A_j) integrated exactly over the flat panel (Sec. 2.1), against the
 oracle's Problem(exact_charge_near=True).
 
-The molecules carry charges 0.02 A (FP64 form) or 0.15 A (mixed form)
-under panel centroids, where the 7-point rule errs visibly: each test also checks that the quadrature-only oracle is
+The molecules carry charges 0.02 A under panel centroids, where the 7-point
+rule errs visibly: each test also checks that the quadrature-only oracle is
 farther from the exact one than the gate, so the comparison means something.
 Both the direct charge sums and the fast multipole charge passes are
 covered, in both precisions; the Born-sphere case finds its pairs over all
@@ -48,17 +48,15 @@ CASES = {
     "small4": (lambda: synth.small_molecule(4), 8, 2),
 }
 
-# Depth of the near charges under the surface, per precision.  Mixed
-# precision forms the pair terms in FP32 from coordinates about a frame
-# origin (the root cube's centre for the direct sums, the leaf for the
-# multipole passes), so a charge at distance r from a quadrature or
-# collocation point carries a relative error of about |x| 2^-24 / r on each
-# such term of C, B and B^T; at 0.02 A that reaches 4e-5 to 6e-5 in dq and
-# dx on the 6 A sphere (measured), at 0.15 A it is several times smaller.
-# The FP64 form takes the 0.02 A case; both are held to the 1e-5 gates, and
-# at both depths the 7-point rule misses the exact pairs by 8e-4 or more in
-# the energy.
-DEPTH = {0: 0.15, 1: 0.02}
+# Depth of the near charges under the surface, both precisions.  The
+# mixed-precision direct sums carry each coordinate as an FP32 hi + lo pair
+# about the root cube's centre (a difference (hi - hi) + (lo - lo) keeps
+# 2^-24 of its own length; with a single FP32 coordinate a charge 0.02 A
+# from a point lost |x| 2^-24 / 0.02 A ~ 1e-5 per pair term, measured up to
+# 6e-5 in dx on the 6 A sphere); the multipole charge passes work in leaf
+# frames.  At this depth the 7-point rule misses the exact pairs by 0.3 or
+# more in the energy.
+DEPTH = {0: 0.02, 1: 0.02}
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
