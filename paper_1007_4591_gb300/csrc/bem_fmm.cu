@@ -1601,6 +1601,9 @@ __device__ __forceinline__ void tree_translate_block(const T *__restrict__ ops, 
     // different banks and its operator loads one 128-byte span
     static_assert(NTX % 8 == 0, "tree translate thread map");
     const int tid = threadIdx.x, rest = tid >> 3, ty = rest % NTY, tx = (tid & 7) + 8 * (rest / NTY);
+    // The next level's launch may start now (programmatic dependent launch):
+    // its operator rows and pair lists do not depend on this level.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (tid < BN) {
         s_in[tid] = tid < ch.z ? p_in[ch.y + tid] : -1;
         s_out[tid] = tid < ch.z ? p_out[ch.y + tid] : -1;
@@ -1611,6 +1614,10 @@ __device__ __forceinline__ void tree_translate_block(const T *__restrict__ ops, 
         const bool ok = rb + r < cs;  // cs % VEC == 0: a copy never crosses a row
         cp_async_16(As + (size_t)k * TR_BM + r, ok ? Tt + (size_t)k * cs + rb + r : Tt, ok);
     }
+    // everything the previous kernels of the stream wrote (this level's input
+    // expansions, the cleared outputs) is complete and visible after this
+    // wait; nothing above reads or writes it
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int cv = cs / VEC;
     for (int e = tid; e < BN * cv; e += NTH) {
         const int j = e / cv, q = (e - j * cv) * VEC;
@@ -1969,9 +1976,25 @@ static void tree_translate(const T *ops, int nc, int cs, int rblocks, const Tree
     const size_t sm = tree_translate_smem<T>(nc, cs);
     if (sm <= TREE_SMEM_MAX) {
         dim3 gt(nchunk, cdiv(nc, TREE_BM));
-        set_smem<T>(k_tree_translate<T, TR_BN_TREE, TR_THREADS_TREE, TREE_BM>, sm);
-        k_tree_translate<T, TR_BN_TREE, TR_THREADS_TREE, TREE_BM><<<gt, TR_THREADS_TREE, sm, s>>>(
-            ops, nc, cs, tree_ldb<T>(cs), t.g_chunk.p + chunk0, t.g_out.p, t.g_in.p, in, out);
+        auto kern = k_tree_translate<T, TR_BN_TREE, TR_THREADS_TREE, TREE_BM>;
+        set_smem<T>(kern, sm);
+        // programmatic dependent launch: the CTAs may start while the previous
+        // kernel of the stream finishes (the kernel waits before it reads its
+        // input or writes its output)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = gt;
+        cfg.blockDim = dim3(TR_THREADS_TREE);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const int ldb = tree_ldb<T>(cs);
+        const int4 *chunks = t.g_chunk.p + chunk0;
+        const int *po = t.g_out.p, *pi = t.g_in.p;
+        BEM_CUDA(cudaLaunchKernelEx(&cfg, kern, ops, nc, cs, ldb, chunks, po, pi, in, out));
     } else {
         const size_t trsm_t = translate_smem<T, TR_BN_TREE>();
         set_smem<T>(k_translate<T, TR_BN_TREE, TR_THREADS_TREE>, trsm_t);

@@ -49,6 +49,9 @@ k_p2m_c(TreeView tv, const typename V4T<T>::t *rec, const int *qpanel, const dou
     constexpr int KC = (NC + 31) / 32;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sm = reinterpret_cast<T *>(smraw);
+    // the first upward translation may start now (it waits for this grid's
+    // results before it reads them)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     T *buf = sm + (size_t)w * 32 * P2M_RS;
     T *row = buf + lane * P2M_RS;
