@@ -176,6 +176,10 @@ k_m2l_tc(const float *__restrict__ A_all,
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tm = s_tmem;
+    // launched as a programmatic dependent of the multipole split: the set-up
+    // above overlaps it; the split multipoles, the cleared local expansions
+    // and the work counter are read only after this wait
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int ntile_done = 0;  // tiles whose MMAs were all issued (MMA thread)
     int nstage_done = 0; // K-block stages whose MMAs were issued and committed (MMA thread)
 
@@ -516,6 +520,7 @@ void build_tc_super(Tree &t, const std::vector<int4> &chunks_m2l, cudaStream_t s
 // per 4 coefficients of a cell (16-byte loads and stores; cs is a multiple
 // of 4, and a group at or past cs is not read).
 __global__ void k_split_m(const float *M, int first, int ncell, int nc, int cs, float *Mtc) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the M2L kernel may start its set-up
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t c = first + (i >> 5);
     const int k0 = 4 * (int)(i & 31);
@@ -551,6 +556,7 @@ void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed) {
     auto kev = [&](int k) {
         if (tk) BEM_CUDA(cudaEventRecord(m.tm.kev[k], m.stream));
     };
+    BEM_CUDA(cudaMemsetAsync(m.dev_err.p + 1, 0, sizeof(int), m.stream));  // work-item counter
     kev(0);
     if (cs % 4 != 0) throw Error(BEM_ECUDA, "tensor-core staging: cell stride not a multiple of 4");
     k_split_m<<<cdiv((int64_t)(t.ncell - first) * 32, 256), 256, 0, m.stream>>>(M, first, t.ncell, nc, cs, m.Mtc.p);
@@ -560,12 +566,30 @@ void m2l_tc(Mesh &m, const Tree &t, const float *M, float *L, bool timed) {
     BEM_CUDA(cudaGetDevice(&dev));
     BEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int grid = std::max(1, std::min(t.tc_nsuper, nsm));
-    BEM_CUDA(cudaMemsetAsync(m.dev_err.p + 1, 0, sizeof(int), m.stream));  // work-item counter
     kev(1);
     ensure_smem_attr(reinterpret_cast<const void *>(k_m2l_tc), sm);
-    k_m2l_tc<<<grid, TC_THREADS, sm, m.stream>>>(tb.Tc_f.p, t.tc_super.p, t.tc_nsuper, m.dev_err.p + 1,
-                                                 t.g_out.p, t.g_in.p, cs, m.Mtc.p, L, m.dev_err.p, m.wait_budget);
-    BEM_CHECK_LAUNCH();
+    {
+        // programmatic dependent launch after the split (the kernel waits
+        // before it reads anything the split or earlier work wrote)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = m.stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const float *A = tb.Tc_f.p;
+        const int4 *items = t.tc_super.p;
+        const int nitems = t.tc_nsuper;
+        int *counter = m.dev_err.p + 1, *err = m.dev_err.p;
+        const int *po = t.g_out.p, *pi = t.g_in.p;
+        const float *Mtc = m.Mtc.p;
+        const long long budget = m.wait_budget;
+        BEM_CUDA(cudaLaunchKernelEx(&cfg, k_m2l_tc, A, items, nitems, counter, po, pi, cs, Mtc, L, err, budget));
+    }
     kev(2);
     kev(3);
 }
