@@ -84,6 +84,10 @@ extern "C" {
                                      are kept on the device (72 bytes per panel).  Returns
                                      BEM_EUNSUPPORTED if a panel is wider than the charge tree's
                                      neighbour reach. */
+#define BEM_FLAG_P2M_FROM_POINTS 64u /* P2M of the quadrature points evaluated from the points
+                                     on every product instead of from the per-panel moments
+                                     built at mesh creation (the two agree to FP32 rounding;
+                                     this form needs no moment storage) */
 
 /* bem_options.near_table */
 #define BEM_NEAR_QUADRATURE 1
@@ -154,6 +158,8 @@ typedef struct bem_mesh_info {
     double root_side;      /* root cube side (A) */
     size_t device_bytes;   /* device memory held by the mesh */
     double ms_build;       /* time spent in bem_mesh_create (tree, lists, tables) */
+    int64_t p2m_segments;  /* (leaf, panel) segments whose P2M moments were built at mesh
+                              creation; 0: P2M works from the quadrature points */
 } bem_mesh_info;
 
 typedef struct bem_mesh bem_mesh; /* opaque: owns geometry, trees, lists, scratch */

@@ -41,6 +41,7 @@ BEM_FLAG_NO_NEARTAB = 4
 BEM_FLAG_CHECK_CHARGES = 8
 BEM_FLAG_M2L_REDUCE = 16
 BEM_FLAG_CHARGE_NEAR_EXACT = 32
+BEM_FLAG_P2M_FROM_POINTS = 64
 BEM_CHARGE_AUTO = 0
 BEM_CHARGE_FMM = 1
 BEM_CHARGE_DIRECT = 2
@@ -76,7 +77,7 @@ class bem_mesh_info(ctypes.Structure):
                 ("m2l_pairs", ctypes.c_int64), ("m2m_pairs", ctypes.c_int64),
                 ("source_points", ctypes.c_int64), ("near_table_nnz", ctypes.c_int64),
                 ("root_side", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("ms_build", ctypes.c_double)]
+                ("ms_build", ctypes.c_double), ("p2m_segments", ctypes.c_int64)]
 
 
 _vp = ctypes.c_void_p

@@ -302,6 +302,9 @@ int bem_mesh_create(const double *panels, int64_t n_p, const double *charges, in
         build_ctq(*m);
         sync(*m);
         st.mark("C^T q");
+        // last, so that its memory check sees everything else the mesh holds
+        build_p2m_moments(*m, m->tp);
+        st.mark("P2M panel moments");
         m->ms_build = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     });
     if (rc != BEM_OK) {
@@ -580,6 +583,7 @@ int bem_mesh_info_get(const bem_mesh *m, bem_mesh_info *info) {
     info->root_side = m->side;
     info->device_bytes = m->bytes();
     info->ms_build = m->ms_build;
+    info->p2m_segments = m->tp.p2m_seg_p >= 0 ? (int64_t)m->tp.p2m_seg_panel.n : 0;
     return BEM_OK;
 }
 

@@ -160,6 +160,16 @@ struct Tree {
     DArray<int4> p2p_hdr[2];
     DArray<int2> p2p_rec[2];
     int p2p_nb = 27;              // records per CTA (the most neighbour leaves)
+    // P2M of the quadrature points as a product with fixed moments: the
+    // points of each leaf grouped by panel into segments, and each segment's
+    // multipole with unit density (its points' weights times their regular
+    // solid harmonics) computed once; a product's P2M is then
+    // M_leaf = sum over the leaf's segments of sigma(panel) x moment.
+    DArray<int> p2m_seg_beg;      // [nleaf+1] the segments of each leaf (CSR)
+    DArray<int> p2m_seg_panel;    // [nseg] panel of each segment
+    DArray<float> p2m_seg_f;      // [nseg x cell stride] moments (mixed precision)
+    DArray<double> p2m_seg_d;     // [nseg x cell stride] moments (FP64)
+    int p2m_seg_p = -1;           // expansion order of the moments (-1: none built)
     DArray<int4> tc_super;        // tensor-core M2L work items (offset, first chunk, chunks)
     int tc_nsuper = 0;
     int m2l_chunk0 = 0, m2l_nchunk = 0;
@@ -176,6 +186,11 @@ struct TreeView {
     const int *nbr_off, *nbr;
     const int *m2l_off, *m2l_src, *m2l_ofs;
     const int *p2p_order;
+    // per-panel P2M moments of the quadrature points (null: none)
+    const int *seg_beg, *seg_panel;
+    const float *seg_f;
+    const double *seg_d;
+    int seg_p;
 };
 
 TreeView view(const Tree &t);
@@ -366,6 +381,11 @@ void radix_sort_u32(const uint32_t *k_in, const int *v_in, uint32_t *k_out, int 
 void scan_exclusive_i32(const int *in, int *out, int64_t n, cudaStream_t s);
 void scan_inclusive_i32(const int *in, int *out, int64_t n, cudaStream_t s);
 int64_t unique_sorted_u64(const uint64_t *in, uint64_t *out, int64_t n, cudaStream_t s);
+// the per-panel P2M moments of a tree's quadrature points (bem_leaf.cu);
+// nothing is built when BEM_FLAG_P2M_FROM_POINTS is set, when the tree has no
+// far field or no quadrature points, or when the moments would take more than
+// half of the free device memory (P2M then works from the points)
+void build_p2m_moments(Mesh &m, Tree &t);
 void build_translation_groups(Mesh &m, Tree &t);
 // tensor-core M2L (bem_tc.cu)
 bool tc_m2l_available(const Mesh &m);

@@ -144,10 +144,229 @@ static void p2m_dispatch(const TreeView &tv, int nleaf, SrcKind sk, const typena
     }
 }
 
+// ------------------------------------------------- P2M from panel moments
+// The quadrature points' strengths are s_i = w_i sigma(panel_i), so a leaf's
+// multipole is sum over the panels j with points in the leaf of
+// sigma_j (sum over those points of w_i conj R(y_i - z) / h^n): the inner sum
+// (the segment's moment) depends on the geometry only.  The moments are
+// built once per mesh with the point P2M above (every segment a CTA, unit
+// density); a product's P2M then reads them (HBM bound) instead of running
+// the recurrence for every point.
+
+constexpr int P2M_SEG_MAXNC = 384;  // (p+1)^2 for p <= 18: three coefficients per thread
+
+// one CTA per leaf: coefficient k of the leaf's multipole is the sum over its
+// segments, in segment order, of sigma(panel) x moment_k.  A thread keeps
+// P2M_SEG_BATCH moment loads in flight (a leaf has ~26 segments: about two
+// batches), and the first batch is issued before the densities are gathered
+// (two dependent loads), so the latencies overlap.
+constexpr int P2M_SEG_BATCH = 16;
+
+template <class T>
+__global__ void __launch_bounds__(128)
+k_p2m_seg(TreeView tv, const T *__restrict__ mom, const double *__restrict__ dens, int nc, int cs, T *M) {
+    // the first upward translation may start now (it waits for this grid's
+    // results before it reads them)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    constexpr int NJ = P2M_SEG_MAXNC / 128, B = P2M_SEG_BATCH;
+    __shared__ T s_sig[128];
+    const int leaf = blockIdx.x;
+    const int b = tv.seg_beg[leaf], e = tv.seg_beg[leaf + 1];
+    T acc[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[j] = 0;
+    for (int s0 = b; s0 < e; s0 += 128) {
+        const int ns = min(128, e - s0);
+        const T *base = mom + (size_t)s0 * cs + threadIdx.x;
+        T v[B];
+        auto load = [&](int j, int q0) {
+            const bool ok = (int)threadIdx.x + 128 * j < nc;
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                v[u] = (ok && q0 + u < ns) ? __ldg(base + 128 * j + (size_t)(q0 + u) * cs) : (T)0;
+        };
+        load(0, 0);
+        __syncthreads();
+        if ((int)threadIdx.x < ns) s_sig[threadIdx.x] = dens ? (T)dens[tv.seg_panel[s0 + threadIdx.x]] : (T)1;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            if ((int)threadIdx.x + 128 * j >= nc) continue;
+            T a = acc[j];
+            for (int q0 = 0; q0 < ns; q0 += B) {
+                if (j > 0 || q0 > 0) load(j, q0);
+#pragma unroll
+                for (int u = 0; u < B; ++u)
+                    if (q0 + u < ns) a = fma(s_sig[q0 + u], v[u], a);
+            }
+            acc[j] = a;
+        }
+    }
+    T *out = M + (size_t)(tv.leaf0 + leaf) * cs;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int k = threadIdx.x + 128 * j;
+        if (k < nc) out[k] = acc[j];
+    }
+}
+
+// (leaf, panel) key of every quadrature point, and its index
+__global__ void k_seg_keys(TreeView tv, const int *qpanel, uint64_t *key, int *idx) {
+    const int leaf = blockIdx.x;
+    for (int i = tv.qp_beg[leaf] + threadIdx.x; i < tv.qp_beg[leaf + 1]; i += blockDim.x) {
+        key[i] = ((uint64_t)leaf << 32) | (uint32_t)qpanel[i];
+        idx[i] = i;
+    }
+}
+
+__global__ void k_seg_flags(const uint64_t *key, int64_t n, int *flag) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+}
+
+// segment g = pos[i] starts at sorted point i: its first point, leaf, panel
+__global__ void k_seg_write(const uint64_t *key, const int *flag, const int *pos, int64_t n, int nseg,
+                            int *pt_beg, int *seg_leaf, int *seg_panel) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (flag[i]) {
+        const int g = pos[i];
+        pt_beg[g] = (int)i;
+        seg_leaf[g] = (int)(key[i] >> 32);
+        seg_panel[g] = (int)(uint32_t)(key[i] & 0xffffffffu);
+    }
+    if (i == n - 1) pt_beg[nseg] = (int)n;
+}
+
+// seg_beg[l] = the first segment of a leaf >= l (segments sorted by leaf)
+__global__ void k_seg_leaf_beg(const int *seg_leaf, int nseg, int nleaf, int *seg_beg) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l > nleaf) return;
+    int lo = 0, hi = nseg;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (seg_leaf[mid] < l) lo = mid + 1;
+        else hi = mid;
+    }
+    seg_beg[l] = lo;
+}
+
+template <class V>
+__global__ void k_seg_gather(const V *rec, const int *idx, int64_t n, V *out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = rec[idx[i]];
+}
+
+template <class T>
+static bool build_p2m_moments_t(Mesh &m, Tree &t, const typename V4T<T>::t *rec, DArray<T> &mom) {
+    using V4 = typename V4T<T>::t;
+    cudaStream_t s = m.stream;
+    const int64_t n = m.nqp;
+    const int p = m.opt.p, cs = cell_stride(p);
+    if ((p + 1) * (p + 1) > P2M_SEG_MAXNC || n <= 0 || n >= ((int64_t)1 << 31) || t.nleaf <= 0) return false;
+    // the points' (leaf, panel) keys, sorted stably: points already come in
+    // leaf order, so each leaf's points end up grouped by panel
+    DArray<uint64_t> key, key_s;
+    DArray<int> idx, idx_s;
+    key.alloc(n);
+    key_s.alloc(n);
+    idx.alloc(n);
+    idx_s.alloc(n);
+    const TreeView tv = view(t);
+    k_seg_keys<<<t.nleaf, 128, 0, s>>>(tv, m.qp_panel.p, key.p, idx.p);
+    BEM_CHECK_LAUNCH();
+    int lb = 1;
+    while (((int64_t)1 << lb) < (int64_t)t.nleaf) ++lb;
+    radix_sort_u64(key.p, idx.p, key_s.p, idx_s.p, n, 32 + lb, s);
+    key.release();
+    idx.release();
+    DArray<int> flag, pos;
+    flag.alloc(n);
+    pos.alloc(n);
+    k_seg_flags<<<cdiv(n, 256), 256, 0, s>>>(key_s.p, n, flag.p);
+    BEM_CHECK_LAUNCH();
+    scan_exclusive_i32(flag.p, pos.p, n, s);
+    int last_pos = 0, last_flag = 0;
+    BEM_CUDA(cudaMemcpyAsync(&last_pos, pos.p + n - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(&last_flag, flag.p + n - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    const int nseg = last_pos + last_flag;
+    // the moments may take at most half of the free device memory
+    const size_t bytes = (size_t)nseg * cs * sizeof(T);
+    size_t fr = 0, tot = 0;
+    BEM_CUDA(cudaMemGetInfo(&fr, &tot));
+    if (nseg <= 0 || bytes > fr / 2) return false;
+    DArray<int> pt_beg, seg_leaf;
+    pt_beg.alloc((size_t)nseg + 1);
+    seg_leaf.alloc(nseg);
+    t.p2m_seg_panel.alloc(nseg);
+    k_seg_write<<<cdiv(n, 256), 256, 0, s>>>(key_s.p, flag.p, pos.p, n, nseg, pt_beg.p, seg_leaf.p,
+                                             t.p2m_seg_panel.p);
+    BEM_CHECK_LAUNCH();
+    t.p2m_seg_beg.alloc((size_t)t.nleaf + 1);
+    k_seg_leaf_beg<<<cdiv((int64_t)t.nleaf + 1, 256), 256, 0, s>>>(seg_leaf.p, nseg, t.nleaf, t.p2m_seg_beg.p);
+    BEM_CHECK_LAUNCH();
+    // the points' records in segment order, then the point P2M with every
+    // segment as a leaf of its own and unit density
+    DArray<V4> rp;
+    rp.alloc(n);
+    k_seg_gather<V4><<<cdiv(n, 256), 256, 0, s>>>(rec, idx_s.p, n, rp.p);
+    BEM_CHECK_LAUNCH();
+    mom.alloc((size_t)nseg * cs);
+    BEM_CUDA(cudaMemsetAsync(mom.p, 0, bytes, s));
+    TreeView sv = tv;
+    sv.qp_beg = pt_beg.p;
+    sv.leaf0 = 0;
+    sv.nleaf = nseg;
+    const T inv_h = (T)(1.0 / (m.side / (double)(1 << t.L)));
+    p2m_dispatch<T>(sv, nseg, SRC_QUAD, rp.p, nullptr, nullptr, p, cs, inv_h, mom.p, s);
+    BEM_CUDA(cudaStreamSynchronize(s));  // the temporaries are released on return
+    return true;
+}
+
+void build_p2m_moments(Mesh &m, Tree &t) {
+    auto drop = [&]() {
+        t.p2m_seg_p = -1;
+        t.p2m_seg_beg.release();
+        t.p2m_seg_panel.release();
+        t.p2m_seg_f.release();
+        t.p2m_seg_d.release();
+    };
+    drop();
+    if ((m.opt.flags & (BEM_FLAG_P2M_FROM_POINTS | BEM_FLAG_NO_FAR)) || !t.has_qp || t.L < 2) return;
+    bool ok = false;
+    try {
+        if (m.opt.precision == BEM_MIXED) ok = build_p2m_moments_t<float>(m, t, m.qp32.p, t.p2m_seg_f);
+        else ok = build_p2m_moments_t<double>(m, t, m.qp64r.p, t.p2m_seg_d);
+    } catch (const Error &e) {
+        // out of device memory (or over the process's cap): P2M works from
+        // the points, as with BEM_FLAG_P2M_FROM_POINTS
+        if (e.code != BEM_ENOMEM) throw;
+        BEM_CUDA(cudaStreamSynchronize(m.stream));
+        ok = false;
+    }
+    if (ok) t.p2m_seg_p = m.opt.p;
+    else drop();
+}
+
+template <class T>
+static const T *seg_moments(const TreeView &tv);
+template <>
+const float *seg_moments<float>(const TreeView &tv) { return tv.seg_f; }
+template <>
+const double *seg_moments<double>(const TreeView &tv) { return tv.seg_d; }
+
 template <class T>
 void p2m_leaves(const TreeView &tv, int nleaf, SrcKind sk, const typename V4T<T>::t *src, const int *qpanel,
                 const double *dens, int p, int cs, T inv_h, T *M, cudaStream_t s) {
-    if (nleaf > 0) p2m_dispatch<T>(tv, nleaf, sk, src, qpanel, dens, p, cs, inv_h, M, s);
+    if (nleaf <= 0) return;
+    const T *mom = seg_moments<T>(tv);
+    if (sk == SRC_QUAD && tv.seg_beg && mom && tv.seg_p == p) {
+        k_p2m_seg<T><<<nleaf, 128, 0, s>>>(tv, mom, dens, (p + 1) * (p + 1), cs, M);
+        BEM_CHECK_LAUNCH();
+        return;
+    }
+    p2m_dispatch<T>(tv, nleaf, sk, src, qpanel, dens, p, cs, inv_h, M, s);
 }
 
 // ------------------------------------------------------------------- L2P

@@ -652,7 +652,8 @@ size_t Tree::bytes() const {
            p2p_hdr[0].bytes() + p2p_hdr[1].bytes() + p2p_rec[0].bytes() + p2p_rec[1].bytes() +
            key.bytes() + ijk.bytes() + parent.bytes() + child_beg.bytes() + child_end.bytes() +
            cen_beg.bytes() + qp_beg.bytes() + chg_beg.bytes() + nbr_off.bytes() + nbr.bytes() +
-           m2l_off.bytes() + m2l_src.bytes() + m2l_ofs.bytes();
+           m2l_off.bytes() + m2l_src.bytes() + m2l_ofs.bytes() + p2m_seg_beg.bytes() + p2m_seg_panel.bytes() +
+           p2m_seg_f.bytes() + p2m_seg_d.bytes();
 }
 
 TreeView view(const Tree &t) {
@@ -674,6 +675,11 @@ TreeView view(const Tree &t) {
     v.m2l_src = t.m2l_src.p;
     v.m2l_ofs = t.m2l_ofs.p;
     v.p2p_order = t.p2p_order.p;
+    v.seg_beg = t.p2m_seg_p >= 0 ? t.p2m_seg_beg.p : nullptr;
+    v.seg_panel = t.p2m_seg_panel.p;
+    v.seg_f = t.p2m_seg_f.p;
+    v.seg_d = t.p2m_seg_d.p;
+    v.seg_p = t.p2m_seg_p;
     return v;
 }
 

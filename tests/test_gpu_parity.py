@@ -64,6 +64,35 @@ def test_fmm_matvec_matches_dense(pkg, small4, depth, p, m2l_mode):
         close(y, ref, 1e-5)
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 2e-6), (1, 1e-11)])
+@pytest.mark.parametrize("depth,p", [(3, 10), (4, 16)])
+def test_p2m_from_panel_moments_matches_points(pkg, small4, precision, tol, depth, p):
+    """P2M of the quadrature points from the per-panel moments built at mesh
+    creation (the default) against the point P2M on every product
+    (BEM_FLAG_P2M_FROM_POINTS): the far field alone (no near field) agrees to
+    the precision's rounding, and both full products match the oracle."""
+    m, P = small4
+    x = _x(m.n_p, 3)
+    far, full = [], []
+    for flags in (0, pkg.BEM_FLAG_P2M_FROM_POINTS):
+        with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=depth, p=p, precision=precision,
+                      flags=flags | pkg.BEM_FLAG_NO_NEAR) as g:
+            nseg = g.info()["p2m_segments"]
+            if flags:
+                assert nseg == 0
+            else:
+                # every panel has its points in one or a few leaves
+                assert m.n_p <= nseg <= 7 * m.n_p, nseg
+            far.append(g.matvec(torch.from_numpy(x).cuda()).cpu().numpy() - x)
+        with pkg.Mesh(m.panels, m.charges, m.eps_in, m.eps_out, depth=depth, p=p, precision=precision,
+                      flags=flags) as g:
+            full.append(g.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
+    close(far[0], far[1], tol)
+    ref = P.A(x)
+    for y in full:
+        close(y, ref, 1e-5)
+
+
 def test_tensor_core_m2l_matches_simt(pkg, small4):
     """M2L on the tensor cores (3xTF32) against the SIMT FP32 operators."""
     m, P = small4
