@@ -173,8 +173,10 @@ int bem_options_default(bem_options *opt);
  *   eps_in, eps_out > 0.
  *   opt may be NULL (defaults).  stream: a cudaStream_t (NULL = legacy default).
  * Computes panel geometry and quadrature points, Morton keys and sort, the
- * octree, neighbour and interaction lists, translation tables and the FP64
- * near-singular table, all on the device.  Errors: BEM_EINVAL for NaN/Inf
+ * octree, neighbour and interaction lists, translation tables, the FP64
+ * near-singular table and the P2M moments of the panels (per leaf and panel,
+ * unit density; skipped with BEM_FLAG_P2M_FROM_POINTS or when they would take
+ * more than half of the free device memory), all on the device.  Errors: BEM_EINVAL for NaN/Inf
  * coordinates, zero-area panels, eps <= 0, n_p <= 0, bad options.  With the
  * environment variable BEM_TIMING=1 the build steps' wall times are printed
  * to stderr (diagnostics). */
