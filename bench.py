@@ -552,6 +552,7 @@ def run_ours(args):
                            form="galerkin" if args.galerkin else "collocation"),
             "phases_ms": {k: round(v, 4) for k, v in ph.items()},
             "tree_build_s": round(tree_s, 4),
+            "p2m_segments": int(info.get("p2m_segments", 0)),
             "solve_s": round(solve_s, 4), "solve_s_runs": [round(t, 4) for t in solve_ts],
             "solve_iters": st["iterations"], "dG_kcal": dg,
             "roofline": roofline,
@@ -690,6 +691,7 @@ def run_lattice(args):
         "solve_s": round(solve_s, 3), "solve_iters": st["iterations"], "dG_kcal": dg,
         "mesh_build_s": round(build_s, 2), "generate_s": round(gen_s, 2),
         "device_bytes": int(info["device_bytes"]), "m2l_pairs": int(info["m2l_pairs"]),
+        "p2m_segments": int(info.get("p2m_segments", 0)),
         "p2p_pairs": int(info["p2p_pairs"])}), flush=True)
     mesh.close()
 
