@@ -49,6 +49,7 @@ BEM_M2L_AUTO = 0
 BEM_M2L_DENSE = 1
 BEM_M2L_DIRECT = 2
 BEM_M2L_TC = 3
+BEM_NOALLOC_SCRATCH_FLOATS = 1 << 21  # the allocation-free entry point's largest n_t
 
 ERROR_NAMES = {0: "BEM_OK", -1: "BEM_EINVAL", -2: "BEM_ENOMEM", -3: "BEM_ECUDA",
                -4: "BEM_ENOCONV", -5: "BEM_ETIMEOUT", -6: "BEM_EUNSUPPORTED"}

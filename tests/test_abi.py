@@ -33,6 +33,23 @@ def lib():
     return pkg.load_library()
 
 
+def test_python_constants_match_the_header():
+    """Every integer constant the header defines (status codes, precisions,
+    BIBEE lambdas, flags, option values) has a Python constant of the same
+    name and value in the binding."""
+    import paper_1007_4591_gb300 as pkg
+    txt = open(HEADER).read()
+    defs = []
+    for name, body in re.findall(r"^#define\s+(BEM_\w+)\s+([^/\n]+)", txt, re.M):
+        expr = re.sub(r"(\d)u\b", r"\1", body.strip())
+        if re.fullmatch(r"[\d\s()<>+\-]+", expr):  # integer literals and shifts only
+            defs.append((name, eval(expr)))
+    assert len(defs) >= 20
+    for name, val in defs:
+        assert hasattr(pkg, name), name
+        assert getattr(pkg, name) == val, (name, getattr(pkg, name), val)
+
+
 def test_header_declares_the_call_list():
     names = _declared()
     for want in ("bem_mesh_create", "bem_mesh_destroy", "bem_matvec", "bem_solve", "bem_bibee",
